@@ -1,0 +1,335 @@
+"""Benchmark: batched deep-unfolded precoding throughput on GB300.
+
+Workload (the headline): 65,536 independent channels H in C^{8x64} (K=8 users,
+M=64 antennas), CN(0,1) entries with 8 dB log-normal per-user gains, unit
+targets, T=10 projected layers with per-layer steps mu_t drawn once from
+U[0.01, 0.1] (seed 2).  One step = one pass of the whole hot path over the
+batch: channel load, Gram + equilibrated Cholesky + G^{-1} + ZF start, 10
+layers (shrink, residual, projection), objective, residual, W write-back.  It is
+one persistent kernel launch.  Inputs stay resident in HBM (268 MB of H, larger
+than the 129 MB L2; W is another 268 MB), so no L2 flush is needed between steps.
+
+Lines printed (rank 0, one JSON line):
+  value      precoders/s from CUDA events over the timed steps (device buffers)
+  e2e        the same through precode_solve_host with pinned host buffers
+             (host->device, solve, device->host inside the timed region)
+  roofline   FP32 FMA-pipe roofline of the solve kernel (the path is
+             arithmetic-bound: ~86 flop per HBM byte)
+  cpu_baseline  the FP64 oracle on this host's cores, bounded sample
+  pa_gap     relative PA-consumption (||W||_{2,1}) difference GPU vs oracle on
+             that sample, and the mean PCG of the GPU output
+  --impl reference runs the FP64 oracle alone (the CPU comparison arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2304_12745_gb300 import channels as ch  # noqa: E402
+
+METRIC = ("precoders/s at M=64,K=8,T=10 (fraction of FP32 roofline); PA-power gap vs FP64 "
+          "oracle; p99 latency")
+UNIT = "precoders/s"
+
+
+def flops_per_instance(K: int, M: int, T: int, mode: int) -> float:
+    """Algorithmic flops of one instance (8 flop per complex multiply-add).
+
+    Paper layer: 2 K^2 M CMAC per layer (residual W H^T and update E H^*).
+    Projected layer as computed here: 2 K^2 M per layer (residual and E Q) plus
+    setup K^2 M / 2 (Hermitian Gram) + K^3 / 6 (factorisation) + K^2 M (Q)."""
+    per_layer = 2 * K * K * M
+    setup = 0.0 if mode == 0 else K * K * M / 2 + K ** 3 / 6 + K * K * M
+    return 8.0 * (T * per_layer + setup)
+
+
+def fp32_peak_tflops() -> float:
+    """152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (maximum SM clock)."""
+    return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                             parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r[2] > 200.0] or rows
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median([r[0] for r in load])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(H, t, mu, budget_s: float = 10.0):
+    """FP64 oracle throughput on this host's cores over a bounded sample."""
+    import oracle
+    oracle.build()
+    nthreads = os.cpu_count() or 1
+    # calibrate on a small slice, then size the sample to ~budget_s of wall time
+    n0 = min(len(H), 4 * nthreads)
+    t0 = time.perf_counter()
+    oracle.batch_forward(1, H[:n0].astype(np.complex128), t[:n0].astype(np.float64),
+                         mu.astype(np.float64), nthreads=nthreads)
+    dt0 = time.perf_counter() - t0
+    n = int(min(len(H), max(n0, n0 * budget_s / max(dt0, 1e-6))))
+    Hs = H[:n].astype(np.complex128)
+    ts = t[:n].astype(np.float64)
+    t0 = time.perf_counter()
+    W, obj, res, st = oracle.batch_forward(1, Hs, ts, mu.astype(np.float64), nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"first {n} instances of the workload, FP64 projected layers, "
+                      f"{nthreads} threads over contiguous ranges, {dt:.2f} s"}, obj, n
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = ch.WORKLOADS["fixed"]
+    nthreads = os.cpu_count() or 1
+    n = min(wl.B, max(64, 24 * nthreads))
+    H = ch.lognormal(n, wl.K, wl.M, seed=wl.seed).astype(np.complex128)
+    t = ch.targets(n, wl.K).astype(np.float64)
+    mu = ch.fixed_workload_steps(wl.T).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.batch_forward(1, H[:nthreads], t[:nthreads], mu, nthreads=nthreads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.batch_forward(1, H, t, mu, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "fixed: 65,536 x C^{8x64}, 8 dB log-normal Rayleigh, T=10 "
+                                   "projected layers, mu_t ~ U[0.01,0.1]",
+                       "sample_per_step": n, "layer": "projected"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": f"{n} instances of the workload per step (FP64 oracle, "
+                                       f"{nthreads} threads)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    wl = ch.WORKLOADS["fixed"]
+    B, K, M, T = wl.B, wl.K, wl.M, wl.T
+    # weak scaling: each rank solves its own 65,536-instance shard
+    H = ch.lognormal(B, K, M, seed=wl.seed + 1000 * rank)
+    t = ch.targets(B, K)
+    mu = ch.fixed_workload_steps(T)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B)
+    Hd = torch.from_numpy(H).cuda()
+    td = torch.from_numpy(t).cuda()
+    md = torch.from_numpy(mu).cuda()
+    W = torch.empty_like(Hd)
+    obj = torch.empty(B, device="cuda")
+    res = torch.empty(B, device="cuda")
+    fl = torch.empty(B, device="cuda", dtype=torch.int32)
+    out = (W, obj, res, fl)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        plan.solve(Hd, td, md, out=out)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            plan.solve(Hd, td, md, out=out)
+            evs[i][1].record(stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = start.elapsed_time(stop)
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * B / (ms_per_step / 1e3)
+    clocks = clk.summary()
+    flags_np = fl.cpu().numpy()
+    obj_np = obj.cpu().numpy()
+    res_np = res.cpu().numpy()
+    Wnp = W.cpu().numpy()
+
+    # roofline of the solve kernel (FP32 FMA pipe)
+    fpi = flops_per_instance(K, M, T, 1)
+    achieved = fpi * B / (kern_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    hbm_bytes = B * K * M * 8 * 2 + B * (K + 3) * 4
+    peaks = measured_peaks()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.070 GHz",
+            "kernel": "solve_kernel<proj,K=8,M=64>", "kernel_ms": kern_ms,
+            "flop_per_instance": fpi,
+            "hbm": {"achieved_gbs": hbm_bytes / (kern_ms / 1e3) / 1e9,
+                    "peak_gbs": peaks.get("hbm_gbs"), "algorithmic_bytes": hbm_bytes}}
+    prof = os.path.join(ROOT, "profiles", "solve_proj_k8_m64_fixed.traffic.json")
+    if os.path.exists(prof):
+        try:
+            roof["traffic"] = json.load(open(prof)).get("traffic_bytes_per_launch")
+        except Exception:
+            pass
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "fixed: 65,536 x C^{8x64} per GPU, CN(0,1) with 8 dB log-normal "
+                                   "user gains, unit targets, T=10 projected layers, "
+                                   "mu_t ~ U[0.01,0.1] (seed 2)",
+                       "B_per_gpu": B, "K": K, "M": M, "T": T, "layer": "projected",
+                       "l2": "inputs larger than L2 (268 MB of H per step), no flush",
+                       "parallelism": f"independent shards x{world}"},
+            "gpu_launches": args.steps, "roofline": roof, "clocks": clocks,
+            "flags_nonzero": int((flags_np != 0).sum())}
+
+    # end to end through the C ABI with pinned host buffers
+    Hh = torch.from_numpy(H).pin_memory()
+    th = torch.from_numpy(t).pin_memory()
+    mh = torch.from_numpy(mu)
+    Wh = torch.empty_like(Hh).pin_memory()
+    oh = torch.empty(B).pin_memory()
+    rh = torch.empty(B).pin_memory()
+    fh = torch.empty(B, dtype=torch.int32).pin_memory()
+    plan.solve_host(Hh, th, mh, None, W=Wh, obj=oh, resid=rh, flags=fh)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.solve_host(Hh, th, mh, None, W=Wh, obj=oh, resid=rh, flags=fh)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    line["e2e"] = {"value": world * B / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(H.nbytes + t.nbytes + 4 * T),
+                   "d2h_bytes_per_step": int(H.nbytes + 3 * 4 * B),
+                   "api": "precode_solve_host (pinned host buffers, chunked copy/compute overlap)"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, oobj, n = cpu_baseline(H, t, mu)
+        line["cpu_baseline"] = cb
+        gap = np.abs(obj_np[:n] - oobj) / oobj
+        import oracle
+        pcg = [oracle.pcg(H[b].astype(np.complex128), t[b].astype(np.float64),
+                          Wnp[b].astype(np.complex128)) for b in range(min(n, 256))]
+        line["pa_gap"] = {"rel_obj_diff_gpu_vs_oracle_max": float(gap.max()),
+                          "rel_obj_diff_gpu_vs_oracle_mean": float(gap.mean()),
+                          "instances": n, "mean_pcg_gpu": float(np.mean(pcg))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * precode.h -- C ABI of the GB300 deep-unfolded PA-consumption precoder.
+ *
+ * Method: Feys, Mestre, Peschiera, Rottenberg, "Deep Unfolding for Fast Linear
+ * Massive MIMO Precoders under a PA Consumption Model" (VTC2023-Spring,
+ * arXiv 2304.12745).
+ *
+ * Problem (Sec. III, Eq. optim1): for a channel H in C^{K x M} (K users, M
+ * antennas) and user targets t_k = sigma_nu sqrt(gamma_k) > 0, find the linear
+ * precoder W in C^{K x M} that minimises the PA consumed power
+ *     alpha ||W||_{2,1} = alpha sum_m sqrt(sum_k |w_{k,m}|^2)        (Eq. effmodel)
+ * subject to H W^T = diag(t).  The library runs T unfolded layers per instance:
+ *
+ *   PRECODE_LAYER_PGD  (Sec. V, Eq. unfoldednet) -- the paper's layer
+ *       V = W - eta_l (W H^T - S) H^*;  W <- prox_{lam_l eta_l ||.||_{2,1}}(V),
+ *       prox per antenna column: w_m <- max(0, 1 - tau/||v_m||) v_m (Sec. IV),
+ *       W^(0) = H^* (Sec. VI-C).  Constraint enforced only through the penalty.
+ *   PRECODE_LAYER_PROJ -- projected layer on the same problem
+ *       X = prox_{mu_l ||.||_{2,1}}(W);  W <- P_A(X) = X - (X H^T - S) G^{-T} H^*,
+ *       G = H H^H (K x K Gram), W^(0) = S G^{-T} H^* (the ZF precoder).
+ *       Every output satisfies H W^T = S up to rounding.
+ *
+ * Data layout (all buffers caller-owned unless stated):
+ *   H, W   complex64 interleaved (re, im) float pairs, instance-major
+ *          [B][K][M], row k = user k, column m = antenna m; base 16-byte aligned.
+ *   t      float [B][K] (t_stride = K) or one shared [K] vector (t_stride = 0).
+ *   step   float [T] device: eta_l (PGD) or mu_l (PROJ).  lam: float [T] device
+ *          (PGD only; NULL for PROJ).
+ *   obj    float [B] = ||W_T||_{2,1}; resid float [B] = ||H W_T^T - S||_F;
+ *   flags  int32 [B] per-instance PRECODE_F_* bits.  obj/resid/flags may be NULL.
+ *
+ * Conventions: every call is asynchronous on the given stream (cudaStream_t,
+ * NULL = legacy default stream); argument errors return PRECODE_EINVAL before
+ * any launch; numerical trouble is reported per instance in flags, never as a
+ * call failure; no C++ exception crosses this interface; the last error
+ * message of the calling thread is available from precode_last_error().
+ * A plan may be used from one host thread / stream at a time.
+ */
+#ifndef PRECODE_H_
+#define PRECODE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* precode_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  PRECODE_OK = 0,
+  PRECODE_EINVAL = 1,    /* bad argument, shape, alignment or size; nothing launched */
+  PRECODE_ENOMEM = 2,    /* device or pinned host allocation failed */
+  PRECODE_ECUDA = 3,     /* CUDA runtime error (message in precode_last_error) */
+  PRECODE_ETIMEDOUT = 4, /* a bounded wait ran out (host wait, or device copy wait) */
+  PRECODE_EBUSY = 5,     /* object in use (serving: no slot / memory for the job) */
+  PRECODE_PENDING = 6,   /* serving: job not finished yet */
+  PRECODE_ENOTFOUND = 7  /* serving: unknown ticket or channel handle */
+} precode_status_t;
+
+typedef enum {
+  PRECODE_LAYER_PGD = 0,  /* paper layer, Eq. (unfoldednet) */
+  PRECODE_LAYER_PROJ = 1  /* shrink + projection onto {H W^T = S} */
+} precode_layer_t;
+
+/* per-instance flag bits (int32 flags[b]) */
+#define PRECODE_F_FP64_CHOL 1   /* PROJ: equilibrated Gram condition estimate above the
+                                   threshold (or FP32 pivot failed): Gram, Cholesky and
+                                   G^{-1} were redone in FP64 */
+#define PRECODE_F_SINGULAR 2    /* PROJ: Gram not positive definite even in FP64
+                                   (rank(H) < K): W set to 0, obj 0, resid ||S||_F */
+#define PRECODE_F_NONFINITE 4   /* NaN/Inf met in the input or the output objective */
+#define PRECODE_F_TIMEOUT 8     /* the device-side wait for this instance's channel copy
+                                   ran out (about 1 s); W not written */
+
+/* plan flags (precode_desc_t.flags) */
+#define PRECODE_PLAN_AUTOTUNE 1u        /* time the kernel variants of each shape at plan
+                                           time and keep the fastest (cached in tune_cache) */
+#define PRECODE_PLAN_STEP_NORMALISED 2u /* PGD only: use eta_l / L_b with the per-instance
+                                           Gershgorin bound L_b = max_k sum_j |G_kj| >=
+                                           lambda_max(H H^H) instead of eta_l */
+
+#define PRECODE_MAX_K 32
+#define PRECODE_MAX_M 256
+#define PRECODE_MAX_T 65536
+
+typedef struct {
+  int32_t M, K;
+} precode_shape_t;
+
+typedef struct {
+  int32_t mode;                  /* precode_layer_t */
+  int32_t T;                     /* layers, 1..PRECODE_MAX_T */
+  int32_t n_shapes;              /* shapes the plan prepares (buckets); >= 1 */
+  const precode_shape_t* shapes; /* host array [n_shapes]; 1 <= K <= 32, K <= M <= 256, M even */
+  int64_t max_instances;         /* largest B any call will pass (sizes plan workspace) */
+  double cond_threshold;         /* PROJ: FP64 fallback when max(d)/min(d) of the
+                                    equilibrated Cholesky pivots exceeds it; <= 0 -> 1e3 */
+  uint32_t flags;                /* PRECODE_PLAN_* */
+  int32_t device;                /* CUDA device ordinal the plan lives on */
+  const char* tune_cache;        /* autotune cache file (read/written), NULL = none */
+} precode_desc_t;
+
+typedef struct precode_plan_s* precode_plan_t;
+
+/* Create a plan: validates the descriptor, picks a kernel variant per shape
+ * (autotuned when PRECODE_PLAN_AUTOTUNE is set, which launches kernels on the
+ * device and synchronises), allocates its workspace.  Returns EINVAL on a bad
+ * descriptor, ENOMEM / ECUDA on allocation or launch failure. */
+precode_status_t precode_plan(const precode_desc_t* desc, precode_plan_t* out);
+precode_status_t precode_plan_destroy(precode_plan_t plan);
+
+/* Uniform batch: B instances of one (M, K) (must be one of the plan's shapes or
+ * fit one: K <= K_bucket, M <= M_bucket).  All pointers are DEVICE pointers.
+ * Runs setup (PROJ: Gram, equilibrated Cholesky, G^{-1}, ZF start) and the T
+ * layers of each instance in one persistent kernel, then writes W, obj, resid,
+ * flags.  B = 0 is a no-op.  EINVAL: B > max_instances, unaligned pointer,
+ * lam == NULL in PGD mode, shape not covered by the plan. */
+precode_status_t precode_solve(precode_plan_t plan, int32_t M, int32_t K, int64_t B,
+                               const void* H, const float* t, int64_t t_stride,
+                               const float* step, const float* lam, void* W, float* obj,
+                               float* resid, int32_t* flags, precode_stream_t stream);
+
+/* Same computation from HOST buffers (pinned memory recommended): the batch is
+ * split in chunks whose host->device copy, solve and device->host copy are
+ * pipelined over the plan's internal streams.  step/lam are HOST arrays [T].
+ * Returns after the results are in the host buffers (synchronous). */
+precode_status_t precode_solve_host(precode_plan_t plan, int32_t M, int32_t K, int64_t B,
+                                    const void* H, const float* t, int64_t t_stride,
+                                    const float* step, const float* lam, void* W, float* obj,
+                                    float* resid, int32_t* flags);
+
+/* Number of device-side wait timeouts recorded by the plan's kernels since the
+ * plan was created (synchronises the plan's device).  0 in normal operation. */
+precode_status_t precode_plan_errors(precode_plan_t plan, uint64_t* count);
+
+const char* precode_status_str(precode_status_t status);
+/* Message of the last failing call on this host thread ("" if none). */
+const char* precode_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRECODE_H_ */

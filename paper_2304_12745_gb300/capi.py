@@ -1,0 +1,115 @@
+"""ctypes binding of ``libprecode.so`` -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards
+plain pointers and sizes; the computation runs in the library's CUDA kernels.
+There is no CPU fallback: if the library is missing or fails to load, the
+import raises.  Tensors are torch tensors used only as device (or pinned host)
+memory; their ``data_ptr()`` is what crosses the boundary.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libprecode.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, PENDING, ENOTFOUND = range(8)
+LAYER_PGD, LAYER_PROJ = 0, 1
+F_FP64_CHOL, F_SINGULAR, F_NONFINITE, F_TIMEOUT = 1, 2, 4, 8
+PLAN_AUTOTUNE, PLAN_STEP_NORMALISED = 1, 2
+MAX_K, MAX_M, MAX_T = 32, 256, 65536
+
+
+class PrecodeError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("K", ctypes.c_int32)]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("T", ctypes.c_int32), ("n_shapes", ctypes.c_int32),
+                ("shapes", ctypes.POINTER(Shape)), ("max_instances", ctypes.c_int64),
+                ("cond_threshold", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("device", ctypes.c_int32), ("tune_cache", ctypes.c_char_p)]
+
+
+_vp = ctypes.c_void_p
+_i32, _i64, _u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+
+_SIGS = {
+    "precode_plan": [ctypes.POINTER(Desc), ctypes.POINTER(_vp)],
+    "precode_plan_destroy": [_vp],
+    "precode_solve": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "precode_solve_host": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
+    "precode_plan_errors": [_vp, ctypes.POINTER(ctypes.c_uint64)],
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_2304_12745_gb300.build` "
+            "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.precode_status_str.argtypes = [ctypes.c_int]
+    lib.precode_status_str.restype = ctypes.c_char_p
+    lib.precode_last_error.argtypes = []
+    lib.precode_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+LIB = _load()
+
+
+def check(status: int, where: str):
+    if status != OK:
+        raise PrecodeError(status, where, LIB.precode_last_error().decode(errors="replace")
+                           or LIB.precode_status_str(status).decode())
+
+
+def ptr(x) -> int | None:
+    """Device (or host) address of a tensor / numpy array, None for None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def precode_plan(mode: int, T: int, shapes, max_instances: int, cond_threshold: float = 0.0,
+                 flags: int = 0, device: int = 0, tune_cache: str | None = None) -> int:
+    arr = (Shape * len(shapes))(*[Shape(int(m), int(k)) for (m, k) in shapes])
+    d = Desc(mode, T, len(shapes), arr, max_instances, cond_threshold, flags, device,
+             tune_cache.encode() if tune_cache else None)
+    h = _vp()
+    check(LIB.precode_plan(ctypes.byref(d), ctypes.byref(h)), "precode_plan")
+    return h.value
+
+
+def precode_plan_destroy(plan: int):
+    check(LIB.precode_plan_destroy(plan), "precode_plan_destroy")
+
+
+def precode_solve(plan, M, K, B, H, t, t_stride, step, lam, W, obj, resid, flags, stream):
+    check(LIB.precode_solve(plan, M, K, B, ptr(H), ptr(t), t_stride, ptr(step), ptr(lam), ptr(W),
+                            ptr(obj), ptr(resid), ptr(flags), stream), "precode_solve")
+
+
+def precode_solve_host(plan, M, K, B, H, t, t_stride, step, lam, W, obj, resid, flags):
+    check(LIB.precode_solve_host(plan, M, K, B, ptr(H), ptr(t), t_stride, ptr(step), ptr(lam),
+                                 ptr(W), ptr(obj), ptr(resid), ptr(flags)), "precode_solve_host")
+
+
+def precode_plan_errors(plan) -> int:
+    n = ctypes.c_uint64(0)
+    check(LIB.precode_plan_errors(plan, ctypes.byref(n)), "precode_plan_errors")
+    return n.value

@@ -1,0 +1,409 @@
+// Host side of the C ABI: plans, argument validation, kernel-variant choice,
+// launches, the host-buffer pipeline and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+#include "precode.h"
+#include "registry.h"
+
+namespace precode {
+
+static thread_local std::string g_last_error;
+
+precode_status_t fail(precode_status_t st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+precode_status_t cuda_fail(cudaError_t e, const char* what) {
+  return fail(PRECODE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+const std::vector<Variant>& variants() {
+  static std::vector<Variant> v = [] {
+    std::vector<Variant> r;
+    register_solve_pgd(r);
+    register_solve_proj(r);
+    return r;
+  }();
+  return v;
+}
+
+// Blocks per SM a variant reaches on the current device (shared memory attribute set once).
+int variant_occupancy(const Variant& v, int device) {
+  static std::mutex mu;
+  static std::vector<std::vector<int>> cache;  // [device][variant index]
+  std::lock_guard<std::mutex> lk(mu);
+  const auto& all = variants();
+  const size_t idx = &v - all.data();
+  if ((int)cache.size() <= device) cache.resize(device + 1);
+  auto& c = cache[device];
+  if (c.empty()) c.assign(all.size(), -1);
+  if (c[idx] < 0) {
+    if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem) !=
+        cudaSuccess)
+      return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v.fn, v.threads, v.smem) != cudaSuccess)
+      return 0;
+    c[idx] = n;
+  }
+  return c[idx];
+}
+
+// Default choice: the first exact variant of (mode, K, M), else the smallest
+// generic bucket that holds (K, M).
+const Variant* pick_variant(int mode, int M, int K) {
+  const Variant* best = nullptr;
+  for (const auto& v : variants())
+    if (v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
+  for (const auto& v : variants()) {
+    if (v.mode != mode || v.exact || v.KB < K || v.MB < M) continue;
+    if (!best || v.KB * v.MB < best->KB * best->MB) best = &v;
+  }
+  return best;
+}
+
+std::vector<const Variant*> eligible_variants(int mode, int M, int K) {
+  std::vector<const Variant*> r;
+  for (const auto& v : variants()) {
+    if (v.mode != mode) continue;
+    if (v.exact ? (v.KB == K && v.MB == M) : (v.KB >= K && v.MB >= M)) r.push_back(&v);
+  }
+  return r;
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+  cudaGetDevice(&prev_);
+  if (prev_ != dev) cudaSetDevice(dev);
+}
+DeviceGuard::~DeviceGuard() {
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != prev_) cudaSetDevice(prev_);
+}
+
+precode_status_t launch_variant(const Variant& v, int device, int num_sms, const SolveArgs& A,
+                                int64_t n_hint, cudaStream_t stream) {
+  const int occ = variant_occupancy(v, device);
+  if (occ <= 0) return fail(PRECODE_ECUDA, "kernel variant cannot be resident on this device");
+  int64_t grid = (int64_t)occ * num_sms;
+  if (n_hint >= 0) grid = std::min<int64_t>(grid, (n_hint + v.groups - 1) / v.groups);
+  if (grid < 1) grid = 1;
+  SolveArgs a = A;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.threads), args,
+                                   (size_t)v.smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
+  return PRECODE_OK;
+}
+
+bool shape_ok(int mode, int M, int K) {
+  if (K < 1 || K > PRECODE_MAX_K || M < 2 || M > PRECODE_MAX_M || (M & 1)) return false;
+  if (mode == PRECODE_LAYER_PROJ && K > M) return false;
+  return true;
+}
+
+}  // namespace precode
+
+using namespace precode;
+
+struct precode_plan_s {
+  int mode = 0, T = 0, device = 0, num_sms = 0;
+  std::vector<precode_shape_t> shapes;
+  std::vector<const Variant*> chosen;
+  int64_t max_instances = 0;
+  float cond_thr = 1e3f;
+  uint32_t flags = 0;
+  unsigned long long* d_err = nullptr;
+  // host-buffer pipeline
+  static constexpr int kPipe = 2;
+  cudaStream_t hstream[kPipe] = {nullptr, nullptr};
+  int64_t chunk = 0;
+  size_t chunk_elems = 0;  // complex elements per chunk buffer
+  void* dH[kPipe] = {};
+  void* dW[kPipe] = {};
+  float* dt[kPipe] = {};
+  float* dobj[kPipe] = {};
+  float* dres[kPipe] = {};
+  int32_t* dfl[kPipe] = {};
+  float* dparams = nullptr;  // [2][T]
+  std::mutex mu;
+
+  const Variant* variant_for(int M, int K) const {
+    for (size_t i = 0; i < shapes.size(); ++i)
+      if (shapes[i].M == M && shapes[i].K == K) return chosen[i];
+    // not a plan shape: any prepared variant whose bucket holds it
+    const Variant* best = nullptr;
+    for (auto* v : chosen)
+      if (!v->exact && v->KB >= K && v->MB >= M && (!best || v->KB * v->MB < best->KB * best->MB))
+        best = v;
+    return best;
+  }
+};
+
+static void plan_free(precode_plan_t p) {
+  if (!p) return;
+  DeviceGuard g(p->device);
+  if (p->d_err) cudaFree(p->d_err);
+  for (int i = 0; i < precode_plan_s::kPipe; ++i) {
+    if (p->hstream[i]) cudaStreamDestroy(p->hstream[i]);
+    cudaFree(p->dH[i]);
+    cudaFree(p->dW[i]);
+    cudaFree(p->dt[i]);
+    cudaFree(p->dobj[i]);
+    cudaFree(p->dres[i]);
+    cudaFree(p->dfl[i]);
+  }
+  cudaFree(p->dparams);
+  delete p;
+}
+
+namespace precode {
+precode_status_t autotune_plan(precode_plan_t p, const char* cache_path);
+int plan_mode(precode_plan_t p) { return p->mode; }
+int plan_T(precode_plan_t p) { return p->T; }
+int plan_device(precode_plan_t p) { return p->device; }
+int plan_num_sms(precode_plan_t p) { return p->num_sms; }
+float plan_cond(precode_plan_t p) { return p->cond_thr; }
+uint32_t plan_flags(precode_plan_t p) { return p->flags; }
+unsigned long long* plan_err(precode_plan_t p) { return p->d_err; }
+int64_t plan_max_instances(precode_plan_t p) { return p->max_instances; }
+std::vector<precode_shape_t>& plan_shapes(precode_plan_t p) { return p->shapes; }
+std::vector<const Variant*>& plan_chosen(precode_plan_t p) { return p->chosen; }
+const Variant* plan_variant_for(precode_plan_t p, int M, int K) { return p->variant_for(M, K); }
+}  // namespace precode
+
+extern "C" {
+
+const char* precode_status_str(precode_status_t s) {
+  switch (s) {
+    case PRECODE_OK: return "ok";
+    case PRECODE_EINVAL: return "invalid argument";
+    case PRECODE_ENOMEM: return "out of memory";
+    case PRECODE_ECUDA: return "CUDA error";
+    case PRECODE_ETIMEDOUT: return "timed out";
+    case PRECODE_EBUSY: return "busy";
+    case PRECODE_PENDING: return "pending";
+    case PRECODE_ENOTFOUND: return "not found";
+  }
+  return "unknown status";
+}
+
+const char* precode_last_error(void) { return g_last_error.c_str(); }
+
+precode_status_t precode_plan(const precode_desc_t* d, precode_plan_t* out) {
+  try {
+    if (!d || !out) return fail(PRECODE_EINVAL, "precode_plan: NULL argument");
+    *out = nullptr;
+    if (d->mode != PRECODE_LAYER_PGD && d->mode != PRECODE_LAYER_PROJ)
+      return fail(PRECODE_EINVAL, "precode_plan: unknown layer mode");
+    if (d->T < 1 || d->T > PRECODE_MAX_T) return fail(PRECODE_EINVAL, "precode_plan: T out of range");
+    if (d->n_shapes < 1 || !d->shapes) return fail(PRECODE_EINVAL, "precode_plan: no shapes");
+    if (d->max_instances < 1) return fail(PRECODE_EINVAL, "precode_plan: max_instances < 1");
+    if ((d->flags & PRECODE_PLAN_STEP_NORMALISED) && d->mode != PRECODE_LAYER_PGD)
+      return fail(PRECODE_EINVAL, "precode_plan: step normalisation applies to the paper layer");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "precode_plan: no CUDA device");
+    if (d->device < 0 || d->device >= ndev) return fail(PRECODE_EINVAL, "precode_plan: bad device");
+    std::unique_ptr<precode_plan_s, void (*)(precode_plan_t)> p(new precode_plan_s, plan_free);
+    p->mode = d->mode;
+    p->T = d->T;
+    p->device = d->device;
+    p->max_instances = d->max_instances;
+    p->cond_thr = d->cond_threshold > 0 ? (float)d->cond_threshold : 1e3f;
+    p->flags = d->flags;
+    DeviceGuard g(p->device);
+    e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "precode_plan: device query");
+    for (int i = 0; i < d->n_shapes; ++i) {
+      const auto s = d->shapes[i];
+      if (!shape_ok(d->mode, s.M, s.K))
+        return fail(PRECODE_EINVAL, "precode_plan: shape (M=" + std::to_string(s.M) + ", K=" +
+                                        std::to_string(s.K) + ") unsupported");
+      const Variant* v = pick_variant(d->mode, s.M, s.K);
+      if (!v) return fail(PRECODE_EINVAL, "precode_plan: no kernel bucket holds the shape");
+      if (variant_occupancy(*v, p->device) <= 0)
+        return fail(PRECODE_ECUDA, "precode_plan: kernel variant cannot run on this device");
+      p->shapes.push_back(s);
+      p->chosen.push_back(v);
+    }
+    e = cudaMalloc(&p->d_err, sizeof(unsigned long long));
+    if (e != cudaSuccess) return fail(PRECODE_ENOMEM, "precode_plan: device allocation");
+    e = cudaMemset(p->d_err, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e, "precode_plan: memset");
+    if (d->flags & PRECODE_PLAN_AUTOTUNE) {
+      precode_status_t st = autotune_plan(p.get(), d->tune_cache);
+      if (st != PRECODE_OK) return st;
+    }
+    *out = p.release();
+    return PRECODE_OK;
+  } catch (const std::exception& ex) {
+    return fail(PRECODE_ENOMEM, std::string("precode_plan: ") + ex.what());
+  }
+}
+
+precode_status_t precode_plan_destroy(precode_plan_t plan) {
+  if (!plan) return fail(PRECODE_EINVAL, "precode_plan_destroy: NULL plan");
+  plan_free(plan);
+  return PRECODE_OK;
+}
+
+precode_status_t precode_solve(precode_plan_t p, int32_t M, int32_t K, int64_t B, const void* H,
+                               const float* t, int64_t t_stride, const float* step,
+                               const float* lam, void* W, float* obj, float* resid,
+                               int32_t* flags, precode_stream_t stream) {
+  if (!p) return fail(PRECODE_EINVAL, "precode_solve: NULL plan");
+  if (B < 0 || B > p->max_instances)
+    return fail(PRECODE_EINVAL, "precode_solve: B outside [0, max_instances]");
+  if (!shape_ok(p->mode, M, K)) return fail(PRECODE_EINVAL, "precode_solve: unsupported shape");
+  if (B == 0) return PRECODE_OK;
+  if (!H || !t || !step || !W) return fail(PRECODE_EINVAL, "precode_solve: NULL buffer");
+  if (p->mode == PRECODE_LAYER_PGD && !lam)
+    return fail(PRECODE_EINVAL, "precode_solve: lam required for the paper layer");
+  if (((uintptr_t)H & 15) || ((uintptr_t)W & 15))
+    return fail(PRECODE_EINVAL, "precode_solve: H and W must be 16-byte aligned");
+  if (t_stride != 0 && t_stride < K) return fail(PRECODE_EINVAL, "precode_solve: t_stride < K");
+  const Variant* v = p->variant_for(M, K);
+  if (!v) return fail(PRECODE_EINVAL, "precode_solve: shape not covered by the plan");
+  DeviceGuard g(p->device);
+  SolveArgs A{};
+  A.H = static_cast<const float2*>(H);
+  A.t = t;
+  A.t_stride = t_stride;
+  A.step = step;
+  A.lam = lam ? lam : step;
+  A.W = static_cast<float2*>(W);
+  A.obj = obj;
+  A.resid = resid;
+  A.flags = flags;
+  A.B = B;
+  A.K = K;
+  A.M = M;
+  A.T = p->T;
+  A.cond_thr = p->cond_thr;
+  A.opts = (p->flags & PRECODE_PLAN_STEP_NORMALISED) ? OPT_STEP_NORMALISED : 0u;
+  A.err = p->d_err;
+  return launch_variant(*v, p->device, p->num_sms, A, B, (cudaStream_t)stream);
+}
+
+precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int64_t B,
+                                    const void* H, const float* t, int64_t t_stride,
+                                    const float* step, const float* lam, void* W, float* obj,
+                                    float* resid, int32_t* flags) {
+  if (!p) return fail(PRECODE_EINVAL, "precode_solve_host: NULL plan");
+  if (B < 0 || B > p->max_instances)
+    return fail(PRECODE_EINVAL, "precode_solve_host: B outside [0, max_instances]");
+  if (!shape_ok(p->mode, M, K)) return fail(PRECODE_EINVAL, "precode_solve_host: bad shape");
+  if (B == 0) return PRECODE_OK;
+  if (!H || !t || !step || !W) return fail(PRECODE_EINVAL, "precode_solve_host: NULL buffer");
+  if (p->mode == PRECODE_LAYER_PGD && !lam)
+    return fail(PRECODE_EINVAL, "precode_solve_host: lam required for the paper layer");
+  if (t_stride != 0 && t_stride < K)
+    return fail(PRECODE_EINVAL, "precode_solve_host: t_stride < K");
+  if (!p->variant_for(M, K)) return fail(PRECODE_EINVAL, "precode_solve_host: shape not in plan");
+  std::lock_guard<std::mutex> lk(p->mu);
+  DeviceGuard g(p->device);
+  cudaError_t e;
+  const size_t n = (size_t)K * M;
+  // chunk: at least 8 waves of work per chunk boundary, at most 8 chunks
+  int64_t chunk = std::max<int64_t>(std::min<int64_t>(B, 8192), (B + 7) / 8);
+  if (!p->dparams) {
+    e = cudaMalloc(&p->dparams, sizeof(float) * 2 * p->T);
+    if (e != cudaSuccess) return fail(PRECODE_ENOMEM, "precode_solve_host: params buffer");
+  }
+  if ((size_t)chunk * n > p->chunk_elems || chunk > p->chunk) {
+    for (int i = 0; i < precode_plan_s::kPipe; ++i) {
+      cudaFree(p->dH[i]);
+      cudaFree(p->dW[i]);
+      cudaFree(p->dt[i]);
+      cudaFree(p->dobj[i]);
+      cudaFree(p->dres[i]);
+      cudaFree(p->dfl[i]);
+      p->dH[i] = p->dW[i] = nullptr;
+      p->dt[i] = p->dobj[i] = p->dres[i] = nullptr;
+      p->dfl[i] = nullptr;
+    }
+    p->chunk = std::max<int64_t>(chunk, p->chunk);
+    p->chunk_elems = std::max<size_t>((size_t)chunk * n, p->chunk_elems);
+    for (int i = 0; i < precode_plan_s::kPipe; ++i) {
+      if (cudaMalloc(&p->dH[i], p->chunk_elems * 8) != cudaSuccess ||
+          cudaMalloc(&p->dW[i], p->chunk_elems * 8) != cudaSuccess ||
+          cudaMalloc(&p->dt[i], (size_t)p->chunk * PRECODE_MAX_K * 4) != cudaSuccess ||
+          cudaMalloc(&p->dobj[i], (size_t)p->chunk * 4) != cudaSuccess ||
+          cudaMalloc(&p->dres[i], (size_t)p->chunk * 4) != cudaSuccess ||
+          cudaMalloc(&p->dfl[i], (size_t)p->chunk * 4) != cudaSuccess)
+        return fail(PRECODE_ENOMEM, "precode_solve_host: staging buffers");
+      if (!p->hstream[i] &&
+          cudaStreamCreateWithFlags(&p->hstream[i], cudaStreamNonBlocking) != cudaSuccess)
+        return fail(PRECODE_ECUDA, "precode_solve_host: stream");
+    }
+  }
+  e = cudaMemcpy(p->dparams, step, sizeof(float) * p->T, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && lam)
+    e = cudaMemcpy(p->dparams + p->T, lam, sizeof(float) * p->T, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "precode_solve_host: params copy");
+  const char* Hc = static_cast<const char*>(H);
+  char* Wc = static_cast<char*>(W);
+  precode_status_t st = PRECODE_OK;
+  for (int64_t c0 = 0, ci = 0; c0 < B; c0 += chunk, ++ci) {
+    const int s = (int)(ci % precode_plan_s::kPipe);
+    cudaStream_t S = p->hstream[s];
+    const int64_t nb = std::min<int64_t>(chunk, B - c0);
+    e = cudaMemcpyAsync(p->dH[s], Hc + (size_t)c0 * n * 8, (size_t)nb * n * 8,
+                        cudaMemcpyHostToDevice, S);
+    const size_t tbytes = t_stride ? (size_t)nb * t_stride * 4 : (size_t)K * 4;
+    const float* tsrc = t_stride ? t + (size_t)c0 * t_stride : t;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->dt[s], tsrc, tbytes, cudaMemcpyHostToDevice, S);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "precode_solve_host: copy in");
+      break;
+    }
+    if (t_stride > PRECODE_MAX_K && (size_t)nb * t_stride > (size_t)p->chunk * PRECODE_MAX_K) {
+      st = fail(PRECODE_EINVAL, "precode_solve_host: t_stride too large for staging");
+      break;
+    }
+    st = precode_solve(p, M, K, nb, p->dH[s], p->dt[s], t_stride, p->dparams,
+                       lam ? p->dparams + p->T : nullptr, p->dW[s], obj ? p->dobj[s] : nullptr,
+                       resid ? p->dres[s] : nullptr, flags ? p->dfl[s] : nullptr, S);
+    if (st != PRECODE_OK) break;
+    e = cudaMemcpyAsync(Wc + (size_t)c0 * n * 8, p->dW[s], (size_t)nb * n * 8,
+                        cudaMemcpyDeviceToHost, S);
+    if (e == cudaSuccess && obj)
+      e = cudaMemcpyAsync(obj + c0, p->dobj[s], nb * 4, cudaMemcpyDeviceToHost, S);
+    if (e == cudaSuccess && resid)
+      e = cudaMemcpyAsync(resid + c0, p->dres[s], nb * 4, cudaMemcpyDeviceToHost, S);
+    if (e == cudaSuccess && flags)
+      e = cudaMemcpyAsync(flags + c0, p->dfl[s], nb * 4, cudaMemcpyDeviceToHost, S);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "precode_solve_host: copy out");
+      break;
+    }
+  }
+  for (int i = 0; i < precode_plan_s::kPipe; ++i) {
+    e = cudaStreamSynchronize(p->hstream[i]);
+    if (e != cudaSuccess && st == PRECODE_OK) st = cuda_fail(e, "precode_solve_host: sync");
+  }
+  return st;
+}
+
+precode_status_t precode_plan_errors(precode_plan_t p, uint64_t* count) {
+  if (!p || !count) return fail(PRECODE_EINVAL, "precode_plan_errors: NULL argument");
+  DeviceGuard g(p->device);
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpy(&v, p->d_err, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "precode_plan_errors");
+  *count = v;
+  return PRECODE_OK;
+}
+
+}  // extern "C"

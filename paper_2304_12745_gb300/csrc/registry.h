@@ -1,0 +1,27 @@
+// Kernel variant table: one entry per compiled instantiation of the solve kernel.
+#pragma once
+
+#include <vector>
+
+#include "kernel_args.h"
+
+namespace precode {
+
+struct Variant {
+  int mode;      // 0 paper layer, 1 projected layer
+  int KB, MB;    // bucket: users and antennas the register/shared layout is built for
+  int GK, GM;    // thread grid per instance (user rows x antenna columns)
+  int JC;        // residual columns per reduction pass
+  int NW;        // warps per block
+  bool exact;    // compiled for K == KB and M == MB only
+  const void* fn;
+  int smem;      // dynamic shared memory per block (bytes)
+  int threads;   // threads per block
+  int groups;    // instances resident per block
+};
+
+void register_solve_pgd(std::vector<Variant>& v);
+void register_solve_proj(std::vector<Variant>& v);
+const std::vector<Variant>& variants();
+
+}  // namespace precode

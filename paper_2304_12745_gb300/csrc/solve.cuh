@@ -1,0 +1,758 @@
+// Persistent deep-unfolded precoder kernel (both layer maps), FP32 complex.
+//
+// One "instance group" of TPI = GK*GM threads owns one problem instance at a
+// time and keeps it on chip for all T layers:
+//   * H (and, for the projected layer, Q = G^{-T} H^*) in shared memory, loaded
+//     by one bulk async copy per instance (TMA engine, completion on an mbarrier);
+//   * W in registers: thread (a, b) owns users k = a + GK*u (u < KB/GK) and
+//     antenna pairs p = b + GM*i (i < MB/(2 GM)), i.e. antennas 2p and 2p+1.
+// Per layer the only cross-antenna reduction is E = W H^T - S (K x K): every
+// thread sums its antennas' share, then the GM threads of one user row reduce
+// it through a bank-swizzled shared buffer into the K x K matrix Es.  Column
+// norms (per antenna, over users) reduce over the GK user rows with warp
+// shuffles (plus shared memory when a group spans several warps).
+//
+// Paper layer (Sec. V, Eq. unfoldednet):    E = W H^T - S;  V = W - eta E H^*;
+//                                           W = prox_{lam eta ||.||_{2,1}}(V);  W^(0) = H^*.
+// Projected layer (constraint of Eq. optim1): X = prox_{mu ||.||_{2,1}}(W);
+//                                           W = X - (X H^T - S) Q,  Q = G^{-T} H^*;
+//                                           W^(0) = S Q (the ZF precoder).
+// Q is computed once per instance from the equilibrated Gram factorisation
+// D G D = L' diag(d) L'^H (D = diag(G)^{-1/2}, L' unit lower): FP32, or FP64 when
+// a pivot fails or max(d)/min(d) exceeds the threshold.  A projected layer then
+// costs the same two K x K x M contractions as a paper layer.
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+#include "device.cuh"
+#include "kernel_args.h"
+#include "precode.h"
+
+namespace precode {
+
+constexpr int kModePGD = 0;
+constexpr int kModeProj = 1;
+constexpr uint64_t kCopyWaitNs = 1000000000ull;  // 1 s bound on one channel copy
+
+__host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+template <int MODE, int KB, int MB, int GK, int GM, int JC_, int NW>
+struct SolveCfg {
+  static constexpr int TPI = GK * GM;            // threads per instance
+  static constexpr int UPT = KB / GK;            // users per thread
+  static constexpr int PPT = MB / (2 * GM);      // antenna pairs per thread
+  static constexpr int NA = 2 * PPT;             // antennas per thread
+  static constexpr int JC = JC_;                 // residual columns per reduction pass
+  static constexpr int NJC = KB / JC;
+  static constexpr int THREADS = NW * 32;
+  static constexpr int GROUPS = THREADS / TPI;   // instances resident per block
+  static constexpr int WPG = TPI >= 32 ? TPI / 32 : 1;
+  static constexpr int LPW = TPI >= 32 ? 32 : TPI;  // lanes of a group inside one warp
+  static constexpr int PF = 2 * UPT * JC;        // partial floats per thread per pass
+  static constexpr int SEG = PF / GM;            // reduced floats per thread per pass
+  static_assert(KB % GK == 0 && MB % (2 * GM) == 0, "lane grid must tile the bucket");
+  static_assert(KB % JC == 0, "reduction passes tile the residual columns");
+  static_assert((GM & (GM - 1)) == 0 && GM <= 32 && (GK & (GK - 1)) == 0, "powers of two");
+  static_assert(TPI <= 32 ? (32 % TPI == 0) : (TPI % 32 == 0), "groups tile warps");
+  static_assert(THREADS % TPI == 0 && THREADS <= 1024, "block holds whole groups");
+  static_assert(PF % GM == 0 && (SEG == 1 || SEG == 2 || SEG % 4 == 0), "segment size");
+  static_assert(SEG < 4 || (2 * JC) % SEG == 0, "a 4-float segment stays inside one user row");
+  static_assert(TPI >= KB, "one thread per Gram column");
+  static_assert(TPI <= 32 || GROUPS <= 15, "one named barrier per group");
+  static_assert(MODE == kModePGD || MB >= 5 * KB, "FP64 scratch lives in the Q area");
+  // per-group shared memory (bytes)
+  static constexpr int H_OFF = 0;
+  static constexpr int H_BYTES = KB * MB * 8;
+  static constexpr int Q_OFF = H_OFF + H_BYTES;
+  static constexpr int Q_BYTES = MODE == kModeProj ? KB * MB * 8 : 0;
+  static constexpr int RED_OFF = Q_OFF + Q_BYTES;
+  static constexpr int RED_BYTES = align_up(TPI * PF * 4, 16);
+  static constexpr int E_OFF = RED_OFF + RED_BYTES;
+  static constexpr int E_BYTES = KB * KB * 8;
+  static constexpr int NRM_OFF = E_OFF + E_BYTES;
+  static constexpr int NRM_BYTES = WPG > 1 ? WPG * GM * NA * 4 : 0;
+  static constexpr int SC_OFF = NRM_OFF + NRM_BYTES;  // t[KB] dsc[KB] piv[KB] misc[8] wsum[WPG]
+  static constexpr int SC_BYTES = align_up((3 * KB + 8 + WPG) * 4, 16);
+  static constexpr int BAR_OFF = SC_OFF + SC_BYTES;
+  static constexpr int GROUP_BYTES = align_up(BAR_OFF + 8, 16);
+  static constexpr int SMEM_BYTES = GROUPS * GROUP_BYTES;
+  static_assert(RED_BYTES >= KB * KB * 8, "unit-lower inverse lives in the reduction buffer");
+  static_assert(MODE == kModePGD || RED_BYTES >= KB * KB * 16, "FP64 inverse in reduction buffer");
+};
+
+template <int MODE, int KB, int MB, int GK, int GM, int JC_, bool EXACT, int NW>
+struct SolveKernel {
+  using C = SolveCfg<MODE, KB, MB, GK, GM, JC_, NW>;
+  static constexpr int TPI = C::TPI, UPT = C::UPT, PPT = C::PPT, NA = C::NA, JC = C::JC,
+                       NJC = C::NJC, PF = C::PF, SEG = C::SEG, WPG = C::WPG, LPW = C::LPW;
+
+  struct Ctx {
+    float2* Hs;
+    float2* Qs;
+    float* red;
+    float2* Es;
+    float* nrm;
+    float* tks;
+    float* dsc;
+    float* piv;
+    int* misc;
+    float* wsum;
+    uint64_t* bar;
+    int g, a, b, lane, wig, gid;
+    unsigned wmask;
+    int K, M;
+  };
+
+  using WReg = float2[UPT][NA];
+  using EReg = float2[UPT][JC];
+
+  __device__ __forceinline__ static int Kd(const Ctx& c) { return EXACT ? KB : c.K; }
+  __device__ __forceinline__ static int Md(const Ctx& c) { return EXACT ? MB : c.M; }
+  __device__ __forceinline__ static int user(const Ctx& c, int u) { return c.a + GK * u; }
+  __device__ __forceinline__ static int pair(const Ctx& c, int i) { return c.b + GM * i; }
+  __device__ __forceinline__ static bool uok(const Ctx& c, int u) {
+    return EXACT || user(c, u) < c.K;
+  }
+  __device__ __forceinline__ static bool pok(const Ctx& c, int i) {
+    return EXACT || 2 * pair(c, i) < c.M;
+  }
+
+  __device__ __forceinline__ static void gsync(const Ctx& c) {
+    if constexpr (TPI <= 32) {
+      __syncwarp(c.wmask);
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(c.gid + 1), "r"(TPI) : "memory");
+    }
+  }
+
+  // w <- rows k_u of X (shared [K][M]) restricted to this thread's antennas.
+  __device__ __forceinline__ static void load_rows(const Ctx& c, WReg& w, const float2* X) {
+    const int M = Md(c);
+#pragma unroll
+    for (int u = 0; u < UPT; ++u)
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        if (uok(c, u) && pok(c, i)) {
+          const float4 v = *reinterpret_cast<const float4*>(X + user(c, u) * M + 2 * pair(c, i));
+          w[u][2 * i] = make_float2(v.x, v.y);
+          w[u][2 * i + 1] = make_float2(v.z, v.w);
+        } else {
+          w[u][2 * i] = make_float2(0.f, 0.f);
+          w[u][2 * i + 1] = make_float2(0.f, 0.f);
+        }
+      }
+  }
+
+  // e[u][jj] = sum over own antennas m of w[u][m] * X[j][m] (CJ: * conj(X[j][m])),
+  // j = jc*JC + jj.
+  template <bool CJ>
+  __device__ __forceinline__ static void partials(const Ctx& c, const WReg& w, const float2* X,
+                                                  int jc, EReg& e) {
+    const int K = Kd(c), M = Md(c);
+#pragma unroll
+    for (int u = 0; u < UPT; ++u)
+#pragma unroll
+      for (int jj = 0; jj < JC; ++jj) e[u][jj] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int jj = 0; jj < JC; ++jj) {
+      const int j = jc * JC + jj;
+      if (!EXACT && j >= K) continue;
+      const float2* row = X + j * M;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        if (!pok(c, i)) continue;
+        const float4 v = *reinterpret_cast<const float4*>(row + 2 * pair(c, i));
+        const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+          if (CJ) {
+            cmac_conj(e[u][jj], w[u][2 * i], x0);
+            cmac_conj(e[u][jj], w[u][2 * i + 1], x1);
+          } else {
+            cmac(e[u][jj], w[u][2 * i], x0);
+            cmac(e[u][jj], w[u][2 * i + 1], x1);
+          }
+        }
+      }
+    }
+  }
+
+  __device__ __forceinline__ static float pf(const EReg& e, int f) {
+    return (f & 1) ? e[f / (2 * JC)][(f >> 1) % JC].y : e[f / (2 * JC)][(f >> 1) % JC].x;
+  }
+
+  // Sum the partials of the GM threads of this user row; the reduced entries
+  // (minus S on the diagonal when SUB_S, times `scale`) go to Es[k][j].
+  // Returns the sum of squares of the entries this thread wrote.
+  template <bool SUB_S>
+  __device__ __forceinline__ static float reduce(const Ctx& c, const EReg& e, int jc,
+                                                 float scale) {
+    float* row = c.red + (c.a * GM + c.b) * PF;
+#pragma unroll
+    for (int s = 0; s < GM; ++s) {
+      float* dst = row + (s ^ c.b) * SEG;
+      if constexpr (SEG % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < SEG; q += 4)
+          *reinterpret_cast<float4*>(dst + q) =
+              make_float4(pf(e, s * SEG + q), pf(e, s * SEG + q + 1), pf(e, s * SEG + q + 2),
+                          pf(e, s * SEG + q + 3));
+      } else if constexpr (SEG == 2) {
+        *reinterpret_cast<float2*>(dst) = make_float2(pf(e, s * SEG), pf(e, s * SEG + 1));
+      } else {
+        *dst = pf(e, s);
+      }
+    }
+    __syncwarp(c.wmask);
+    float acc[SEG];
+#pragma unroll
+    for (int q = 0; q < SEG; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int bb = 0; bb < GM; ++bb) {
+      const float* src = c.red + (c.a * GM + bb) * PF + (c.b ^ bb) * SEG;
+      if constexpr (SEG % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < SEG; q += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(src + q);
+          acc[q] += v.x;
+          acc[q + 1] += v.y;
+          acc[q + 2] += v.z;
+          acc[q + 3] += v.w;
+        }
+      } else if constexpr (SEG == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(src);
+        acc[0] += v.x;
+        acc[1] += v.y;
+      } else {
+        acc[0] += *src;
+      }
+    }
+    float ssq = 0.f;
+    float* Ef = reinterpret_cast<float*>(c.Es);
+#pragma unroll
+    for (int q = 0; q < SEG; ++q) {
+      const int f = c.b * SEG + q;
+      const int u = f / (2 * JC);
+      const int jj = (f >> 1) % JC;
+      const int k = user(c, u);
+      const int j = jc * JC + jj;
+      float v = acc[q];
+      if (SUB_S && (f & 1) == 0 && j == k && k < Kd(c)) v -= c.tks[k];
+      v *= scale;
+      ssq = fmaf(v, v, ssq);
+      acc[q] = v;
+      if constexpr (SEG < 4) Ef[(k * KB + j) * 2 + (f & 1)] = v;
+    }
+    if constexpr (SEG % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < SEG; q += 4) {
+        const int f = c.b * SEG + q;
+        const int k = user(c, f / (2 * JC));
+        const int j = jc * JC + ((f >> 1) % JC);
+        *reinterpret_cast<float4*>(Ef + (k * KB + j) * 2) =
+            make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
+      }
+    }
+    __syncwarp(c.wmask);
+    return ssq;
+  }
+
+  // Squared column norms over all users, identical in every thread of a column.
+  __device__ __forceinline__ static void colnorm2(const Ctx& c, const WReg& w, float (&r2)[NA]) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      float s = 0.f;
+#pragma unroll
+      for (int u = 0; u < UPT; ++u) s = fmaf(w[u][q].x, w[u][q].x, fmaf(w[u][q].y, w[u][q].y, s));
+      r2[q] = s;
+    }
+#pragma unroll
+    for (int msk = GM; msk < LPW; msk <<= 1)
+#pragma unroll
+      for (int q = 0; q < NA; ++q) r2[q] += __shfl_xor_sync(c.wmask, r2[q], msk);
+    if constexpr (WPG > 1) {
+      float* buf = c.nrm;
+      if (c.lane < GM)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) buf[(c.wig * GM + c.b) * NA + q] = r2[q];
+      gsync(c);
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
+        float s = 0.f;
+        for (int ww = 0; ww < WPG; ++ww) s += buf[(ww * GM + c.b) * NA + q];
+        r2[q] = s;
+      }
+      gsync(c);  // buffer free for the next call
+    }
+  }
+
+  // Group soft threshold per antenna column: w_m <- max(0, 1 - tau/||w_m||) w_m.
+  __device__ __forceinline__ static void shrink(WReg& w, const float (&r2)[NA], float tau) {
+    const float tau2 = tau * tau;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const float s = (r2[q] > tau2) ? (1.f - tau * rsqrtf(r2[q])) : 0.f;
+#pragma unroll
+      for (int u = 0; u < UPT; ++u) {
+        w[u][q].x *= s;
+        w[u][q].y *= s;
+      }
+    }
+  }
+
+  // w -= Es[k_u][:] * X  (CJ: X conjugated), X shared [K][M].
+  template <bool CJ>
+  __device__ __forceinline__ static void update(const Ctx& c, WReg& w, const float2* X) {
+    const int K = Kd(c), M = Md(c);
+#pragma unroll 4
+    for (int j = 0; j < KB; ++j) {
+      if (!EXACT && j >= K) break;
+      float2 ej[UPT];
+#pragma unroll
+      for (int u = 0; u < UPT; ++u) ej[u] = c.Es[user(c, u) * KB + j];
+      const float2* row = X + j * M;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        if (!pok(c, i)) continue;
+        const float4 v = *reinterpret_cast<const float4*>(row + 2 * pair(c, i));
+        const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+          if (CJ) {
+            cmsub_conj(w[u][2 * i], ej[u], x0);
+            cmsub_conj(w[u][2 * i + 1], ej[u], x1);
+          } else {
+            cmsub(w[u][2 * i], ej[u], x0);
+            cmsub(w[u][2 * i + 1], ej[u], x1);
+          }
+        }
+      }
+    }
+  }
+
+  // Es <- G = H H^H (full K x K), from w = own rows of H.
+  __device__ __forceinline__ static void gram(Ctx& c, WReg& w, EReg& e) {
+    load_rows(c, w, c.Hs);
+#pragma unroll 1
+    for (int jc = 0; jc < NJC; ++jc) {
+      partials<true>(c, w, c.Hs, jc, e);
+      reduce<false>(c, e, jc, 1.f);
+    }
+    gsync(c);
+  }
+
+  // Projected-layer setup.  Writes Q to Qs and W^(0) = S Q into w.  Returns the
+  // instance flags (FP64 fallback, singular, non-finite).
+  __device__ static int setup_proj(Ctx& c, WReg& w, EReg& e, float cond_thr) {
+    const int K = Kd(c), M = Md(c);
+    gram(c, w, e);
+    // equilibration D = diag(G)^{-1/2}
+    if (c.g < K) c.dsc[c.g] = rsqrtf(c.Es[c.g * KB + c.g].x);
+    gsync(c);
+    for (int idx = c.g; idx < K * K; idx += TPI) {
+      const int i = idx / K, j = idx - i * K;
+      if (j <= i) {
+        const float s = c.dsc[i] * c.dsc[j];
+        float2 v = c.Es[i * KB + j];
+        c.Es[i * KB + j] = make_float2(v.x * s, v.y * s);
+      }
+    }
+    gsync(c);
+    // LDL^H elimination of the equilibrated Gram, lower triangle in place
+    bool fail = false;
+    float dmin = FLT_MAX, dmax = 0.f;
+    for (int j = 0; j < K; ++j) {
+      const float d = c.Es[j * KB + j].x;
+      if (!(d > 0.f) || !(d < FLT_MAX)) {
+        fail = true;
+        break;
+      }
+      dmin = fminf(dmin, d);
+      dmax = fmaxf(dmax, d);
+      const float inv = 1.f / d;
+      const int R = K - 1 - j;
+      for (int idx = c.g; idx < R * R; idx += TPI) {
+        const int i = j + 1 + idx / R, l = j + 1 + idx % R;
+        if (l > i) continue;
+        const float2 aij = c.Es[i * KB + j], alj = c.Es[l * KB + j];
+        float2 v = c.Es[i * KB + l];
+        cmsub_conj(v, make_float2(aij.x * inv, aij.y * inv), alj);
+        c.Es[i * KB + l] = v;
+      }
+      gsync(c);
+    }
+    if (!fail && !(dmax > cond_thr * dmin)) {
+      // U = L'^{-1} (unit lower), one column per thread; L'_ip = A_ip / d_p
+      float2* U = reinterpret_cast<float2*>(c.red);
+      if (c.g < K) c.piv[c.g] = 1.f / c.Es[c.g * KB + c.g].x;
+      gsync(c);
+      if (c.g < K) {
+        const int col = c.g;
+        U[col * KB + col] = make_float2(1.f, 0.f);
+        for (int i = col + 1; i < K; ++i) {
+          float2 s = make_float2(0.f, 0.f);
+          for (int p = col; p < i; ++p) {
+            const float2 a = c.Es[i * KB + p];
+            const float ip = c.piv[p];
+            cmac(s, make_float2(a.x * ip, a.y * ip), U[p * KB + col]);
+          }
+          U[i * KB + col] = make_float2(-s.x, -s.y);
+        }
+      }
+      gsync(c);
+      // G^{-1}_ij = dsc_i dsc_j sum_{p >= max(i,j)} conj(U_pi) U_pj / d_p  -> Es
+      for (int idx = c.g; idx < K * K; idx += TPI) {
+        const int i = idx / K, j = idx - i * K;
+        float2 s = make_float2(0.f, 0.f);
+        for (int p = (i > j ? i : j); p < K; ++p) {
+          const float2 upi = U[p * KB + i];
+          const float ip = c.piv[p];
+          cmac_conj(s, U[p * KB + j], make_float2(upi.x * ip, upi.y * ip));
+        }
+        const float sc = c.dsc[i] * c.dsc[j];
+        c.Es[i * KB + j] = make_float2(s.x * sc, s.y * sc);
+      }
+      gsync(c);
+      // Q = conj(G^{-1} H) on own entries; W^(0) = t_k Q
+#pragma unroll
+      for (int u = 0; u < UPT; ++u)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) w[u][q] = make_float2(0.f, 0.f);
+      for (int l = 0; l < K; ++l) {
+        float2 gl[UPT];
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) gl[u] = c.Es[user(c, u) * KB + l];
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          if (!pok(c, i)) continue;
+          const float4 v = *reinterpret_cast<const float4*>(c.Hs + l * M + 2 * pair(c, i));
+#pragma unroll
+          for (int u = 0; u < UPT; ++u) {
+            cmac(w[u][2 * i], gl[u], make_float2(v.x, v.y));
+            cmac(w[u][2 * i + 1], gl[u], make_float2(v.z, v.w));
+          }
+        }
+      }
+      store_q_and_start(c, w);
+      return 0;
+    }
+    return setup_proj_fp64(c, w);
+  }
+
+  // Q = conj(w) into Qs for own entries, then w <- t_k Q.
+  __device__ __forceinline__ static void store_q_and_start(Ctx& c, WReg& w) {
+    const int M = Md(c);
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+      const float tk = uok(c, u) ? c.tks[user(c, u)] : 0.f;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        const float2 q0 = make_float2(w[u][2 * i].x, -w[u][2 * i].y);
+        const float2 q1 = make_float2(w[u][2 * i + 1].x, -w[u][2 * i + 1].y);
+        if (uok(c, u) && pok(c, i))
+          *reinterpret_cast<float4*>(c.Qs + user(c, u) * M + 2 * pair(c, i)) =
+              make_float4(q0.x, q0.y, q1.x, q1.y);
+        w[u][2 * i] = make_float2(tk * q0.x, tk * q0.y);
+        w[u][2 * i + 1] = make_float2(tk * q1.x, tk * q1.y);
+      }
+    }
+    gsync(c);
+  }
+
+  // FP64 Gram, LDL^H and inverse (no equilibration; a pivot below 1e-12 times
+  // its Gram diagonal entry means rank(H) < K).
+  __device__ static int setup_proj_fp64(Ctx& c, WReg& w) {
+    const int K = Kd(c), M = Md(c);
+    double2* G = reinterpret_cast<double2*>(c.Qs);
+    double2* U = G + KB * KB;
+    double* orig = reinterpret_cast<double*>(U + KB * KB);
+    double* pv = orig + KB;
+    double2* Gi = reinterpret_cast<double2*>(c.red);
+    for (int idx = c.g; idx < K * K; idx += TPI) {
+      const int i = idx / K, j = idx - i * K;
+      if (j > i) continue;
+      double sr = 0.0, si = 0.0;
+      for (int m = 0; m < M; ++m) {
+        const float2 x = c.Hs[i * M + m], y = c.Hs[j * M + m];
+        sr += (double)x.x * y.x + (double)x.y * y.y;
+        si += (double)x.y * y.x - (double)x.x * y.y;
+      }
+      G[i * KB + j] = make_double2(sr, si);
+    }
+    gsync(c);
+    if (c.g < K) orig[c.g] = G[c.g * KB + c.g].x;
+    gsync(c);
+    int fl = PRECODE_F_FP64_CHOL;
+    bool singular = false;
+    for (int j = 0; j < K; ++j) {
+      const double d = G[j * KB + j].x;
+      if (!(d > 1e-12 * orig[j]) || !(d < DBL_MAX)) {
+        singular = true;
+        if (!(orig[j] < DBL_MAX) || orig[j] != orig[j]) fl |= PRECODE_F_NONFINITE;
+        break;
+      }
+      const double inv = 1.0 / d;
+      const int R = K - 1 - j;
+      for (int idx = c.g; idx < R * R; idx += TPI) {
+        const int i = j + 1 + idx / R, l = j + 1 + idx % R;
+        if (l > i) continue;
+        const double2 aij = G[i * KB + j], alj = G[l * KB + j];
+        const double ar = aij.x * inv, ai = aij.y * inv;
+        double2 v = G[i * KB + l];
+        v.x -= ar * alj.x + ai * alj.y;  // a * conj(b)
+        v.y -= ai * alj.x - ar * alj.y;
+        G[i * KB + l] = v;
+      }
+      gsync(c);
+    }
+    if (singular) {
+      gsync(c);
+#pragma unroll
+      for (int u = 0; u < UPT; ++u)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) w[u][q] = make_float2(0.f, 0.f);
+      return fl | PRECODE_F_SINGULAR;
+    }
+    if (c.g < K) pv[c.g] = 1.0 / G[c.g * KB + c.g].x;
+    gsync(c);
+    if (c.g < K) {
+      const int col = c.g;
+      U[col * KB + col] = make_double2(1.0, 0.0);
+      for (int i = col + 1; i < K; ++i) {
+        double sr = 0.0, si = 0.0;
+        for (int p = col; p < i; ++p) {
+          const double2 a = G[i * KB + p], x = U[p * KB + col];
+          const double ar = a.x * pv[p], ai = a.y * pv[p];
+          sr += ar * x.x - ai * x.y;
+          si += ar * x.y + ai * x.x;
+        }
+        U[i * KB + col] = make_double2(-sr, -si);
+      }
+    }
+    gsync(c);
+    for (int idx = c.g; idx < K * K; idx += TPI) {
+      const int i = idx / K, j = idx - i * K;
+      double sr = 0.0, si = 0.0;
+      for (int p = (i > j ? i : j); p < K; ++p) {
+        const double2 upi = U[p * KB + i], upj = U[p * KB + j];
+        // conj(U_pi) U_pj / d_p
+        sr += (upi.x * upj.x + upi.y * upj.y) * pv[p];
+        si += (upi.x * upj.y - upi.y * upj.x) * pv[p];
+      }
+      Gi[i * KB + j] = make_double2(sr, si);
+    }
+    gsync(c);
+    // own entries of conj(G^{-1} H) in FP64, rounded once
+#pragma unroll
+    for (int u = 0; u < UPT; ++u)
+#pragma unroll
+      for (int i = 0; i < PPT; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          double zr = 0.0, zi = 0.0;
+          if (uok(c, u) && pok(c, i)) {
+            const int k = user(c, u), m = 2 * pair(c, i) + h;
+            for (int l = 0; l < K; ++l) {
+              const double2 gkl = Gi[k * KB + l];
+              const float2 x = c.Hs[l * M + m];
+              zr += gkl.x * x.x - gkl.y * x.y;
+              zi += gkl.x * x.y + gkl.y * x.x;
+            }
+          }
+          w[u][2 * i + h] = make_float2((float)zr, (float)zi);
+        }
+    gsync(c);  // every thread is done with the FP64 scratch before Q overwrites it
+    store_q_and_start(c, w);
+    return fl;
+  }
+
+  // Paper-layer per-instance step normalisation: 1 / max_k sum_j |G_kj|.
+  __device__ static float inv_gershgorin(Ctx& c, WReg& w, EReg& e) {
+    const int K = Kd(c);
+    gram(c, w, e);
+    if (c.g < K) {
+      float s = 0.f;
+      for (int j = 0; j < K; ++j) {
+        const float2 v = c.Es[c.g * KB + j];
+        s += sqrtf(v.x * v.x + v.y * v.y);
+      }
+      c.dsc[c.g] = s;
+    }
+    gsync(c);
+    float L = 0.f;
+    for (int k = 0; k < K; ++k) L = fmaxf(L, c.dsc[k]);
+    gsync(c);
+    return 1.f / L;
+  }
+
+  __device__ static void run(const SolveArgs& A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Ctx c;
+    const int tid = threadIdx.x;
+    c.gid = tid / TPI;
+    c.g = tid - c.gid * TPI;
+    c.b = c.g % GM;
+    c.a = c.g / GM;
+    c.lane = tid & 31;
+    c.wig = c.g >> 5;
+    c.wmask = TPI >= 32 ? 0xffffffffu : (((1u << (TPI & 31)) - 1u) << ((c.lane / TPI) * TPI));
+    unsigned char* gs = smem + c.gid * C::GROUP_BYTES;
+    c.Hs = reinterpret_cast<float2*>(gs + C::H_OFF);
+    c.Qs = reinterpret_cast<float2*>(gs + C::Q_OFF);
+    c.red = reinterpret_cast<float*>(gs + C::RED_OFF);
+    c.Es = reinterpret_cast<float2*>(gs + C::E_OFF);
+    c.nrm = reinterpret_cast<float*>(gs + C::NRM_OFF);
+    c.tks = reinterpret_cast<float*>(gs + C::SC_OFF);
+    c.dsc = c.tks + KB;
+    c.piv = c.dsc + KB;
+    c.misc = reinterpret_cast<int*>(c.piv + KB);
+    c.wsum = reinterpret_cast<float*>(c.misc + 8);
+    c.bar = reinterpret_cast<uint64_t*>(gs + C::BAR_OFF);
+
+    if (c.g == 0) mbar_init(c.bar, 1);
+    fence_mbar_init();
+    __syncthreads();
+
+    uint32_t phase = 0;
+    const int64_t n_inst = A.tbl ? (int64_t)(*A.count) : A.B;
+    WReg w;
+    EReg e;
+    float r2[NA];
+#pragma unroll 1
+    for (int64_t it = (int64_t)blockIdx.x * C::GROUPS + c.gid; it < n_inst;
+         it += (int64_t)gridDim.x * C::GROUPS) {
+      int64_t inst, h_off, w_off, t_off;
+      if (A.tbl) {
+        inst = A.index[it];
+        const InstDesc d = A.tbl[inst];
+        h_off = d.h_off;
+        w_off = d.w_off;
+        t_off = d.t_off;
+        c.K = d.K;
+        c.M = d.M;
+      } else {
+        inst = it;
+        c.K = A.K;
+        c.M = A.M;
+        h_off = it * (int64_t)A.K * A.M;
+        w_off = h_off;
+        t_off = it * A.t_stride;
+      }
+      const int K = Kd(c), M = Md(c);
+
+      // ---- channel copy into shared memory (one bulk async copy)
+      gsync(c);  // every thread of the group is done with the previous instance
+      if (c.g == 0) {
+        fence_proxy_async_smem();
+        const uint32_t bytes = (uint32_t)(K * M) * 8u;
+        mbar_arrive_expect_tx(c.bar, bytes);
+        bulk_g2s(c.Hs, A.H + h_off, bytes, c.bar);
+      }
+      if (c.g < K) c.tks[c.g] = A.t[t_off + c.g];
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+      gsync(c);
+      if (c.misc[0] == 0) {
+        // the copy did not land in time: report, then wait (bounded) for it
+        // before this group's buffers can be reused; give up the group if not.
+        if (c.g == 0) {
+          atomicAdd(A.err, 1ull);
+          if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
+          c.misc[1] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+        }
+        gsync(c);
+        if (c.misc[1] == 0) return;
+        phase ^= 1;
+        continue;
+      }
+      if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);  // already complete
+      phase ^= 1;
+
+      int fl = 0;
+      const int T = A.T;
+      if constexpr (MODE == kModeProj) {
+        fl = setup_proj(c, w, e, A.cond_thr);
+        if (!(fl & PRECODE_F_SINGULAR)) {
+#pragma unroll 1
+          for (int l = 0; l < T; ++l) {
+            const float mu = fmaxf(__ldg(A.step + l), 0.f);
+            colnorm2(c, w, r2);
+            shrink(w, r2, mu);
+#pragma unroll 1
+            for (int jc = 0; jc < NJC; ++jc) {
+              partials<false>(c, w, c.Hs, jc, e);
+              reduce<true>(c, e, jc, 1.f);
+            }
+            update<false>(c, w, c.Qs);
+          }
+        }
+      } else {
+        float invL = 1.f;
+        if (A.opts & OPT_STEP_NORMALISED) invL = inv_gershgorin(c, w, e);
+        load_rows(c, w, c.Hs);
+#pragma unroll
+        for (int u = 0; u < UPT; ++u)
+#pragma unroll
+          for (int q = 0; q < NA; ++q) w[u][q].y = -w[u][q].y;  // W^(0) = H^*
+#pragma unroll 1
+        for (int l = 0; l < T; ++l) {
+          const float eta = __ldg(A.step + l) * invL;
+          const float tau = fmaxf(__ldg(A.lam + l), 0.f) * eta;
+#pragma unroll 1
+          for (int jc = 0; jc < NJC; ++jc) {
+            partials<false>(c, w, c.Hs, jc, e);
+            reduce<true>(c, e, jc, eta);
+          }
+          update<true>(c, w, c.Hs);
+          colnorm2(c, w, r2);
+          shrink(w, r2, fmaxf(tau, 0.f));
+        }
+      }
+
+      // ---- epilogue: objective, residual, W
+      colnorm2(c, w, r2);
+      float o = 0.f;
+#pragma unroll
+      for (int q = 0; q < NA; ++q) o += sqrtf(r2[q]);
+#pragma unroll
+      for (int msk = 1; msk < GM; msk <<= 1) o += __shfl_xor_sync(c.wmask, o, msk);
+      float rs = 0.f;
+      if (A.resid) {
+#pragma unroll 1
+        for (int jc = 0; jc < NJC; ++jc) {
+          partials<false>(c, w, c.Hs, jc, e);
+          rs += reduce<true>(c, e, jc, 1.f);
+        }
+#pragma unroll
+        for (int msk = 1; msk < LPW; msk <<= 1) rs += __shfl_xor_sync(c.wmask, rs, msk);
+        if constexpr (WPG > 1) {
+          if (c.lane == 0) c.wsum[c.wig] = rs;
+          gsync(c);
+          rs = 0.f;
+          for (int ww = 0; ww < WPG; ++ww) rs += c.wsum[ww];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UPT; ++u)
+#pragma unroll
+        for (int i = 0; i < PPT; ++i)
+          if (uok(c, u) && pok(c, i))
+            *reinterpret_cast<float4*>(A.W + w_off + (int64_t)user(c, u) * M + 2 * pair(c, i)) =
+                make_float4(w[u][2 * i].x, w[u][2 * i].y, w[u][2 * i + 1].x, w[u][2 * i + 1].y);
+      if (c.g == 0) {
+        if (!(o < FLT_MAX) || !(rs < FLT_MAX)) fl |= PRECODE_F_NONFINITE;
+        if (A.obj) A.obj[inst] = o;
+        if (A.resid) A.resid[inst] = sqrtf(rs);
+        if (A.flags) A.flags[inst] = fl;
+      }
+    }
+  }
+};
+
+template <int MODE, int KB, int MB, int GK, int GM, int JC, bool EXACT, int NW>
+__global__ void __launch_bounds__(NW * 32) solve_kernel(SolveArgs A) {
+  SolveKernel<MODE, KB, MB, GK, GM, JC, EXACT, NW>::run(A);
+}
+
+}  // namespace precode

@@ -1,0 +1,17 @@
+// Instantiations of the solve kernel for the paper layer (Sec. V, Eq. unfoldednet).
+#include "registry.h"
+#include "solve.cuh"
+
+namespace precode {
+
+void register_solve_pgd(std::vector<Variant>& v) {
+#define X(KB, MB, GK, GM, JC, EXACT, NW)                                                  \
+  v.push_back(Variant{kModePGD, KB, MB, GK, GM, JC, NW, EXACT,                           \
+                      (const void*)&solve_kernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW>, \
+                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::SMEM_BYTES, NW * 32,      \
+                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::GROUPS});
+#include "solve_variants.inc"
+#undef X
+}
+
+}  // namespace precode

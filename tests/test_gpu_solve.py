@@ -1,0 +1,289 @@
+"""GPU parity of the batched solve (both layer maps) against the FP64 oracle.
+
+Bar (per instance): relative Frobenius error of W <= 1e-4 and relative error
+of the objective ||W||_{2,1} <= 1e-5, on the same seeded inputs; integer
+outputs (flags) exact.  Inputs follow the benchmark workloads: i.i.d. CN(0,1)
+and log-normal-scaled Rayleigh channels, Rician ULA channels for the larger
+buckets, unit targets or the paper's 10 dB targets.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2304_12745_gb300 import channels as ch
+
+pytestmark = pytest.mark.gpu
+
+W_TOL = 1e-4
+OBJ_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pc():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2304_12745_gb300 import capi, precoder
+    return capi, precoder
+
+
+def run_gpu(precoder, mode, H, t, step, lam=None, **plan_kw):
+    B, K, M = H.shape
+    plan = precoder.Plan(mode, len(step), [(M, K)], max(B, 1), **plan_kw)
+    Hd = torch.from_numpy(H).cuda()
+    td = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float32)).cuda()
+    sd = torch.tensor(step, dtype=torch.float32, device="cuda")
+    ld = torch.tensor(lam, dtype=torch.float32, device="cuda") if lam is not None else None
+    W, obj, res, fl = plan.solve(Hd, td, sd, ld)
+    torch.cuda.synchronize()
+    assert plan.errors() == 0
+    out = W.cpu().numpy(), obj.cpu().numpy(), res.cpu().numpy(), fl.cpu().numpy()
+    plan.close()
+    return out
+
+
+def oracle_ref(orc, mode, H, t, step, lam=None):
+    B, K, M = H.shape
+    tt = np.broadcast_to(np.asarray(t, np.float64), (B, K))
+    return orc.batch_forward(mode, H.astype(np.complex128), tt, np.asarray(step, np.float64),
+                             None if lam is None else np.asarray(lam, np.float64), nthreads=8)
+
+
+def rel_fro(A, B):
+    num = np.linalg.norm((A - B).reshape(len(A), -1), axis=1)
+    den = np.maximum(np.linalg.norm(B.reshape(len(B), -1), axis=1), 1e-30)
+    return num / den
+
+
+def assert_parity(gpu, ref, w_tol=W_TOL, obj_tol=OBJ_TOL, resid_abs=None):
+    Wg, og, rg, fg = gpu
+    Wo, oo, ro, so = ref
+    e = rel_fro(Wg, Wo)
+    assert e.max() <= w_tol, f"max rel-Fro error {e.max():.3e} at instance {e.argmax()}"
+    eo = np.abs(og - oo) / np.maximum(oo, 1e-30)
+    assert eo.max() <= obj_tol, f"max objective error {eo.max():.3e} at {eo.argmax()}"
+    if resid_abs is not None:
+        assert np.all(rg <= resid_abs)
+    return e, eo
+
+
+# ---------------------------------------------------------------- projected layer
+
+def test_proj_tiny_workload(pc, orc):
+    """128 x C^{4x32} CN(0,1), unit targets, T = 20, mu_t = 0.05."""
+    capi, precoder = pc
+    H = ch.rayleigh(128, 4, 32, seed=1)
+    t = ch.targets(128, 4)
+    mu = np.full(20, 0.05, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    assert_parity(gpu, ref, resid_abs=1e-4)
+    assert np.all(gpu[3] == 0)
+
+
+def test_proj_fixed_workload_sample(pc, orc):
+    """C^{8x64}, 8 dB log-normal user gains, T = 10, mu_t ~ U[0.01, 0.1] (seed 2);
+    a ragged batch of 1000 instances."""
+    capi, precoder = pc
+    H = ch.lognormal(1000, 8, 64, seed=2)
+    t = ch.targets(1000, 8)
+    mu = ch.fixed_workload_steps(10)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    assert_parity(gpu, ref)
+    # residual of a feasible output is rounding-level relative to ||S||_F
+    assert np.all(gpu[2] <= 1e-4 * math.sqrt(8))
+
+
+def test_proj_paper_targets_and_sum_rate(pc, orc):
+    """10 dB targets (t = sqrt(10)), K=8, M=64: every output is feasible, so the
+    sum rate equals the paper's 27.68 bits/symbol."""
+    capi, precoder = pc
+    H = ch.rayleigh(64, 8, 64, seed=3)
+    t = ch.targets(64, 8, gamma_db=10.0)
+    mu = np.full(10, 0.3, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    assert_parity(gpu, ref)
+    for b in range(0, 64, 9):
+        r = orc.sum_rate(H[b].astype(np.complex128), gpu[0][b].astype(np.complex128), 1.0)
+        assert abs(r - 8 * math.log2(1 + float(t[b, 0]) ** 2)) < 1e-3
+
+
+@pytest.mark.parametrize("K,M", [(16, 128), (32, 256)])
+def test_proj_large_buckets(pc, orc, K, M):
+    capi, precoder = pc
+    B = 96
+    H = ch.rician_ula(B, K, M, seed=5)
+    t = ch.targets(B, K)
+    mu = ch.uniform_steps(10, 0.01, 0.1, seed=7)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    assert_parity(gpu, ref)
+
+
+@pytest.mark.parametrize("K,M", [(3, 20), (4, 4), (5, 40), (8, 10), (11, 100), (32, 200)])
+def test_proj_generic_buckets(pc, orc, K, M):
+    """Shapes that only fit a larger bucket (runtime K, M); M = K leaves no freedom."""
+    capi, precoder = pc
+    B = 37
+    H = ch.rayleigh(B, K, M, seed=11 + K)
+    t = ch.targets(B, K)
+    mu = np.full(6, 0.05, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    assert_parity(gpu, ref, w_tol=(3e-4 if M == K else W_TOL), obj_tol=(3e-5 if M == K else OBJ_TOL))
+    if M == K:
+        for b in range(B):
+            Wstar = np.linalg.solve(H[b].astype(np.complex128), np.diag(t[b]).astype(np.complex128)).T
+            assert np.linalg.norm(gpu[0][b] - Wstar) / np.linalg.norm(Wstar) < 3e-4
+
+
+def test_proj_singular_and_nonfinite_flags(pc, orc):
+    capi, precoder = pc
+    H = ch.rayleigh(8, 4, 32, seed=21)
+    H[2, 3] = H[2, 1]          # rank 3: singular Gram
+    H[5, 0, 7] = np.nan        # non-finite input
+    t = ch.targets(8, 4)
+    mu = np.full(5, 0.05, np.float32)
+    W, obj, res, fl = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu)
+    assert fl[2] & capi.F_SINGULAR and fl[2] & capi.F_FP64_CHOL
+    assert not np.any(W[2]) and obj[2] == 0
+    assert res[2] == pytest.approx(2.0, rel=1e-6)  # ||S||_F with W = 0
+    assert fl[5] & capi.F_NONFINITE
+    ok = [0, 1, 3, 4, 6, 7]
+    assert np.all(fl[ok] == 0)
+    ref = oracle_ref(orc, 1, H[ok], t[ok], mu)
+    assert_parity((W[ok], obj[ok], res[ok], fl[ok]), ref)
+
+
+def test_proj_ill_conditioned_uses_fp64(pc, orc):
+    """Two almost collinear users push the equilibrated pivot ratio over the
+    threshold: the FP64 path runs and parity still holds."""
+    capi, precoder = pc
+    rs = np.random.default_rng(5)
+    H = ch.rayleigh(16, 4, 32, seed=22)
+    for b in range(0, 16, 2):
+        H[b, 1] = H[b, 0] + (1e-3 * (rs.standard_normal(32) + 1j * rs.standard_normal(32))).astype(np.complex64)
+    t = ch.targets(16, 4)
+    mu = np.full(4, 0.02, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, cond_threshold=1e3)
+    assert np.all(gpu[3][0::2] == capi.F_FP64_CHOL)
+    assert np.all(gpu[3][1::2] == 0)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    # the conditioning amplifies FP32 rounding of the layers themselves
+    assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
+
+
+# ---------------------------------------------------------------- paper layer
+
+def test_pgd_tiny_workload_paper_parameters(pc, orc):
+    """Paper layer on 128 x C^{4x32}: eta = 1/L~ (Marchenko-Pastur edge), lambda = 1/15, T = 20."""
+    capi, precoder = pc
+    H = ch.rayleigh(128, 4, 32, seed=1)
+    t = ch.targets(128, 4)
+    eta = np.full(20, ch.paper_eta(4, 32), np.float32)
+    lam = np.full(20, 1 / 15, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PGD, H, t, eta, lam)
+    ref = oracle_ref(orc, 0, H, t, eta, lam)
+    assert_parity(gpu, ref)
+    eo = np.abs(gpu[2] - ref[2]) / ref[2]
+    assert eo.max() < 1e-4
+
+
+def test_pgd_paper_setting_k8_m64(pc, orc):
+    """K=8, M=64, 10 dB targets, lambda = 1/15, learned-like per-layer eta in the clamp interval."""
+    capi, precoder = pc
+    H = ch.rayleigh(500, 8, 64, seed=9)
+    t = ch.targets(500, 8, gamma_db=10.0)
+    L = 1 / ch.paper_eta(8, 64)
+    eta = np.linspace(1 / L, 1 / (2 * L), 20).astype(np.float32)
+    lam = np.full(20, 1 / 15, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PGD, H, t, eta, lam)
+    ref = oracle_ref(orc, 0, H, t, eta, lam)
+    assert_parity(gpu, ref)
+
+
+def test_pgd_step_normalised_on_lognormal(pc, orc):
+    """Per-instance eta_l / L_b with the Gershgorin bound L_b = max_k sum_j |G_kj|."""
+    capi, precoder = pc
+    B, K, M = 200, 8, 64
+    H = ch.lognormal(B, K, M, seed=2)
+    t = ch.targets(B, K)
+    step = np.full(10, 0.9, np.float32)
+    lam = np.full(10, 0.5, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PGD, H, t, step, lam, step_normalised=True)
+    Wo = np.zeros_like(H, dtype=np.complex128)
+    for b in range(B):
+        Hb = H[b].astype(np.complex128)
+        Lb = np.abs(Hb @ Hb.conj().T).sum(1).max()
+        assert Lb >= orc.lambda_max(Hb) * (1 - 1e-12)
+        Wo[b] = orc.ufpgd_forward(Hb, t[b], step.astype(np.float64) / Lb, lam)
+    e = rel_fro(gpu[0], Wo)
+    assert e.max() <= W_TOL
+
+
+# ---------------------------------------------------------------- batch mechanics
+
+def test_empty_one_and_shared_targets(pc, orc):
+    capi, precoder = pc
+    plan = precoder.Plan(capi.LAYER_PROJ, 3, [(32, 4)], 64)
+    mu = torch.full((3,), 0.05, device="cuda")
+    H0 = torch.empty((0, 4, 32), dtype=torch.complex64, device="cuda")
+    t0 = torch.ones(4, device="cuda")
+    plan.solve(H0, t0, mu)  # B = 0: no-op
+    H = ch.rayleigh(33, 4, 32, seed=31)
+    t_shared = np.array([1.0, 2.0, 0.5, 1.5], np.float32)
+    W, obj, res, fl = plan.solve(torch.from_numpy(H).cuda(), torch.from_numpy(t_shared).cuda(), mu)
+    ref = oracle_ref(orc, 1, H, np.broadcast_to(t_shared, (33, 4)), [0.05] * 3)
+    assert_parity((W.cpu().numpy(), obj.cpu().numpy(), res.cpu().numpy(), fl.cpu().numpy()), ref)
+    W1 = plan.solve(torch.from_numpy(H[:1]).cuda(), torch.from_numpy(t_shared).cuda(), mu)[0]
+    assert torch.equal(W1[0], W[0])  # per-instance result independent of the batch
+    with pytest.raises(capi.PrecodeError):
+        plan.solve(torch.from_numpy(ch.rayleigh(65, 4, 32, seed=1)).cuda(), t0, mu)  # B > max
+    plan.close()
+
+
+def test_deterministic_and_host_path_identical(pc):
+    capi, precoder = pc
+    B = 3000
+    H = ch.lognormal(B, 8, 64, seed=41)
+    t = ch.targets(B, 8)
+    mu = ch.fixed_workload_steps(10)
+    plan = precoder.Plan(capi.LAYER_PROJ, 10, [(64, 8)], B)
+    Hd, td, md = torch.from_numpy(H).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(mu).cuda()
+    a = plan.solve(Hd, td, md)
+    b = plan.solve(Hd, td, md)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    Hh = torch.from_numpy(H).pin_memory()
+    th = torch.from_numpy(t).pin_memory()
+    Wh = torch.empty_like(Hh).pin_memory()
+    oh = torch.empty(B).pin_memory()
+    rh = torch.empty(B).pin_memory()
+    fh = torch.empty(B, dtype=torch.int32).pin_memory()
+    plan.solve_host(Hh, th, torch.from_numpy(mu), None, W=Wh, obj=oh, resid=rh, flags=fh)
+    assert torch.equal(Wh, a[0].cpu())
+    assert torch.equal(oh, a[1].cpu()) and torch.equal(fh, a[3].cpu())
+    plan.close()
+
+
+def test_fixed_workload_full_size_sampled(pc, orc):
+    """The full 65,536-instance batch in the benchmark's launch configuration;
+    256 sampled instances against the oracle, all flags clean, all outputs feasible."""
+    capi, precoder = pc
+    wl = ch.WORKLOADS["fixed"]
+    H = ch.lognormal(wl.B, wl.K, wl.M, seed=wl.seed)
+    t = ch.targets(wl.B, wl.K)
+    mu = ch.fixed_workload_steps(wl.T)
+    plan = precoder.Plan(capi.LAYER_PROJ, wl.T, [(wl.M, wl.K)], wl.B)
+    W, obj, res, fl = plan.solve(torch.from_numpy(H).cuda(), torch.from_numpy(t).cuda(),
+                                 torch.from_numpy(mu).cuda())
+    W, obj, res, fl = W.cpu().numpy(), obj.cpu().numpy(), res.cpu().numpy(), fl.cpu().numpy()
+    plan.close()
+    idx = np.sort(np.random.default_rng(0).choice(wl.B, 256, replace=False))
+    ref = oracle_ref(orc, 1, H[idx], t[idx], mu)
+    assert_parity((W[idx], obj[idx], res[idx], fl[idx]), ref)
+    assert np.all(np.isfinite(obj)) and np.all(res < 1e-4 * math.sqrt(wl.K))
+    assert (fl != 0).mean() < 0.01
