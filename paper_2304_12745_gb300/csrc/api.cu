@@ -51,6 +51,8 @@ int variant_occupancy(const Variant& v, int device) {
     if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem) !=
         cudaSuccess)
       return 0;
+    cudaFuncSetAttribute(v.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v.fn, v.threads, v.smem) != cudaSuccess)
       return 0;

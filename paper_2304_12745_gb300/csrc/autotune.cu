@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -41,7 +42,7 @@ __global__ void fill_const(float* p, int64_t n, float v) {
 std::string variant_key(const Variant& v) {
   std::ostringstream o;
   o << v.KB << "x" << v.MB << "/" << v.GK << "x" << v.GM << "/jc" << v.JC << "/w" << v.NW
-    << (v.exact ? "/exact" : "/generic");
+    << "/b" << v.minb << (v.exact ? "/exact" : "/generic");
   return o.str();
 }
 
@@ -121,6 +122,9 @@ precode_status_t autotune_plan(precode_plan_t p, const char* cache_path) {
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep > 0) ms_min = std::min(ms_min, ms);
       }
+      if (std::getenv("PRECODE_TUNE_LOG"))
+        std::fprintf(stderr, "[precode autotune] mode %d K=%d M=%d %s: %.4f ms\n", plan_mode(p), K,
+                     M, variant_key(*v).c_str(), ms_min);
       if (ms_min < best_ms) {
         best_ms = ms_min;
         best = v;

@@ -13,6 +13,7 @@ struct Variant {
   int GK, GM;    // thread grid per instance (user rows x antenna columns)
   int JC;        // residual columns per reduction pass
   int NW;        // warps per block
+  int minb;      // blocks per SM the register budget is built for
   bool exact;    // compiled for K == KB and M == MB only
   const void* fn;
   int smem;      // dynamic shared memory per block (bytes)

@@ -186,9 +186,8 @@ struct SolveKernel {
   // Sum the partials of the GM threads of this user row; the reduced entries
   // (minus S on the diagonal when SUB_S, times `scale`) go to Es[k][j].
   // Returns the sum of squares of the entries this thread wrote.
-  template <bool SUB_S>
   __device__ __forceinline__ static float reduce(const Ctx& c, const EReg& e, int jc,
-                                                 float scale) {
+                                                 float scale, bool sub_s) {
     float* row = c.red + (c.a * GM + c.b) * PF;
 #pragma unroll
     for (int s = 0; s < GM; ++s) {
@@ -239,7 +238,7 @@ struct SolveKernel {
       const int k = user(c, u);
       const int j = jc * JC + jj;
       float v = acc[q];
-      if (SUB_S && (f & 1) == 0 && j == k && k < Kd(c)) v -= c.tks[k];
+      if (sub_s && (f & 1) == 0 && j == k && k < Kd(c)) v -= c.tks[k];
       v *= scale;
       ssq = fmaf(v, v, ssq);
       acc[q] = v;
@@ -332,22 +331,12 @@ struct SolveKernel {
     }
   }
 
-  // Es <- G = H H^H (full K x K), from w = own rows of H.
-  __device__ __forceinline__ static void gram(Ctx& c, WReg& w, EReg& e) {
-    load_rows(c, w, c.Hs);
-#pragma unroll 1
-    for (int jc = 0; jc < NJC; ++jc) {
-      partials<true>(c, w, c.Hs, jc, e);
-      reduce<false>(c, e, jc, 1.f);
-    }
-    gsync(c);
-  }
-
-  // Projected-layer setup.  Writes Q to Qs and W^(0) = S Q into w.  Returns the
-  // instance flags (FP64 fallback, singular, non-finite).
-  __device__ static int setup_proj(Ctx& c, WReg& w, EReg& e, float cond_thr) {
+  // Projected-layer setup from Es = G^T = conj(H H^H) (Hermitian, same diagonal
+  // and conditioning as G).  Its inverse is G^{-T}, so Q = G^{-T} H^* is formed
+  // directly.  Writes Q to Qs and W^(0) = S Q into w.  Returns the instance
+  // flags (FP64 fallback, singular, non-finite).
+  __device__ static int setup_proj(Ctx& c, WReg& w, float cond_thr) {
     const int K = Kd(c), M = Md(c);
-    gram(c, w, e);
     // equilibration D = diag(G)^{-1/2}
     if (c.g < K) c.dsc[c.g] = rsqrtf(c.Es[c.g * KB + c.g].x);
     gsync(c);
@@ -402,7 +391,7 @@ struct SolveKernel {
         }
       }
       gsync(c);
-      // G^{-1}_ij = dsc_i dsc_j sum_{p >= max(i,j)} conj(U_pi) U_pj / d_p  -> Es
+      // (G^T)^{-1}_ij = dsc_i dsc_j sum_{p >= max(i,j)} conj(U_pi) U_pj / d_p  -> Es
       for (int idx = c.g; idx < K * K; idx += TPI) {
         const int i = idx / K, j = idx - i * K;
         float2 s = make_float2(0.f, 0.f);
@@ -415,7 +404,7 @@ struct SolveKernel {
         c.Es[i * KB + j] = make_float2(s.x * sc, s.y * sc);
       }
       gsync(c);
-      // Q = conj(G^{-1} H) on own entries; W^(0) = t_k Q
+      // Q = G^{-T} H^* on own entries; W^(0) = t_k Q
 #pragma unroll
       for (int u = 0; u < UPT; ++u)
 #pragma unroll
@@ -430,8 +419,8 @@ struct SolveKernel {
           const float4 v = *reinterpret_cast<const float4*>(c.Hs + l * M + 2 * pair(c, i));
 #pragma unroll
           for (int u = 0; u < UPT; ++u) {
-            cmac(w[u][2 * i], gl[u], make_float2(v.x, v.y));
-            cmac(w[u][2 * i + 1], gl[u], make_float2(v.z, v.w));
+            cmac_conj(w[u][2 * i], gl[u], make_float2(v.x, v.y));
+            cmac_conj(w[u][2 * i + 1], gl[u], make_float2(v.z, v.w));
           }
         }
       }
@@ -441,7 +430,7 @@ struct SolveKernel {
     return setup_proj_fp64(c, w);
   }
 
-  // Q = conj(w) into Qs for own entries, then w <- t_k Q.
+  // Q = w into Qs for own entries, then w <- t_k Q.
   __device__ __forceinline__ static void store_q_and_start(Ctx& c, WReg& w) {
     const int M = Md(c);
 #pragma unroll
@@ -449,8 +438,8 @@ struct SolveKernel {
       const float tk = uok(c, u) ? c.tks[user(c, u)] : 0.f;
 #pragma unroll
       for (int i = 0; i < PPT; ++i) {
-        const float2 q0 = make_float2(w[u][2 * i].x, -w[u][2 * i].y);
-        const float2 q1 = make_float2(w[u][2 * i + 1].x, -w[u][2 * i + 1].y);
+        const float2 q0 = w[u][2 * i];
+        const float2 q1 = w[u][2 * i + 1];
         if (uok(c, u) && pok(c, i))
           *reinterpret_cast<float4*>(c.Qs + user(c, u) * M + 2 * pair(c, i)) =
               make_float4(q0.x, q0.y, q1.x, q1.y);
@@ -561,17 +550,17 @@ struct SolveKernel {
               zi += gkl.x * x.y + gkl.y * x.x;
             }
           }
-          w[u][2 * i + h] = make_float2((float)zr, (float)zi);
+          w[u][2 * i + h] = make_float2((float)zr, (float)-zi);  // Q = conj(G^{-1} H)
         }
     gsync(c);  // every thread is done with the FP64 scratch before Q overwrites it
     store_q_and_start(c, w);
     return fl;
   }
 
-  // Paper-layer per-instance step normalisation: 1 / max_k sum_j |G_kj|.
-  __device__ static float inv_gershgorin(Ctx& c, WReg& w, EReg& e) {
+  // Paper-layer per-instance step normalisation 1 / max_k sum_j |G_kj|, from
+  // Es = G^T (the row sums of |G^T| and |G| agree).
+  __device__ static float inv_gershgorin(Ctx& c) {
     const int K = Kd(c);
-    gram(c, w, e);
     if (c.g < K) {
       float s = 0.f;
       for (int j = 0; j < K; ++j) {
@@ -669,45 +658,61 @@ struct SolveKernel {
       if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);  // already complete
       phase ^= 1;
 
+      // ---- steps -1 .. T of one instance.  Step -1 (Gram, when needed) and
+      // step T (final residual, when requested) share the residual code of the
+      // layers, so its unrolled body exists once in the kernel.
       int fl = 0;
       const int T = A.T;
-      if constexpr (MODE == kModeProj) {
-        fl = setup_proj(c, w, e, A.cond_thr);
-        if (!(fl & PRECODE_F_SINGULAR)) {
+      const bool need_gram = (MODE == kModeProj) || (A.opts & OPT_STEP_NORMALISED);
+      const int last = A.resid ? T : T - 1;
+      float invL = 1.f, rs = 0.f;
+      load_rows(c, w, c.Hs);
+#pragma unroll
+      for (int u = 0; u < UPT; ++u)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) w[u][q].y = -w[u][q].y;  // conj(H) rows
 #pragma unroll 1
-          for (int l = 0; l < T; ++l) {
-            const float mu = fmaxf(__ldg(A.step + l), 0.f);
+      for (int s = need_gram ? -1 : 0; s <= last; ++s) {
+        float scale = 1.f;
+        if (s >= 0 && s < T) {
+          if constexpr (MODE == kModeProj) {
             colnorm2(c, w, r2);
-            shrink(w, r2, mu);
-#pragma unroll 1
-            for (int jc = 0; jc < NJC; ++jc) {
-              partials<false>(c, w, c.Hs, jc, e);
-              reduce<true>(c, e, jc, 1.f);
-            }
-            update<false>(c, w, c.Qs);
+            shrink(w, r2, fmaxf(__ldg(A.step + s), 0.f));
+          } else {
+            scale = __ldg(A.step + s) * invL;
           }
         }
-      } else {
-        float invL = 1.f;
-        if (A.opts & OPT_STEP_NORMALISED) invL = inv_gershgorin(c, w, e);
-        load_rows(c, w, c.Hs);
-#pragma unroll
-        for (int u = 0; u < UPT; ++u)
-#pragma unroll
-          for (int q = 0; q < NA; ++q) w[u][q].y = -w[u][q].y;  // W^(0) = H^*
+        rs = 0.f;
 #pragma unroll 1
-        for (int l = 0; l < T; ++l) {
-          const float eta = __ldg(A.step + l) * invL;
-          const float tau = fmaxf(__ldg(A.lam + l), 0.f) * eta;
-#pragma unroll 1
-          for (int jc = 0; jc < NJC; ++jc) {
-            partials<false>(c, w, c.Hs, jc, e);
-            reduce<true>(c, e, jc, eta);
+        for (int jc = 0; jc < NJC; ++jc) {
+          partials<false>(c, w, c.Hs, jc, e);
+          rs += reduce(c, e, jc, scale, s >= 0);
+        }
+        if (s < 0) {
+          // Es = sum_m conj(H_km) H_jm = G^T
+          gsync(c);
+          if constexpr (MODE == kModeProj) {
+            fl = setup_proj(c, w, A.cond_thr);
+            if (fl & PRECODE_F_SINGULAR) break;
+          } else {
+            invL = inv_gershgorin(c);  // w still holds W^(0) = H^*
           }
+          continue;
+        }
+        if (s == T) break;  // final residual only
+        if constexpr (MODE == kModeProj) {
+          update<false>(c, w, c.Qs);
+        } else {
           update<true>(c, w, c.Hs);
           colnorm2(c, w, r2);
-          shrink(w, r2, fmaxf(tau, 0.f));
+          shrink(w, r2, fmaxf(fmaxf(__ldg(A.lam + s), 0.f) * scale, 0.f));
         }
+      }
+      if (fl & PRECODE_F_SINGULAR) {
+        // W = 0: objective 0, residual ||S||_F
+        rs = 0.f;
+        if (c.g == 0)
+          for (int k = 0; k < K; ++k) rs += c.tks[k] * c.tks[k];
       }
 
       // ---- epilogue: objective, residual, W
@@ -717,13 +722,7 @@ struct SolveKernel {
       for (int q = 0; q < NA; ++q) o += sqrtf(r2[q]);
 #pragma unroll
       for (int msk = 1; msk < GM; msk <<= 1) o += __shfl_xor_sync(c.wmask, o, msk);
-      float rs = 0.f;
-      if (A.resid) {
-#pragma unroll 1
-        for (int jc = 0; jc < NJC; ++jc) {
-          partials<false>(c, w, c.Hs, jc, e);
-          rs += reduce<true>(c, e, jc, 1.f);
-        }
+      if (A.resid && !(fl & PRECODE_F_SINGULAR)) {
 #pragma unroll
         for (int msk = 1; msk < LPW; msk <<= 1) rs += __shfl_xor_sync(c.wmask, rs, msk);
         if constexpr (WPG > 1) {
@@ -750,8 +749,8 @@ struct SolveKernel {
   }
 };
 
-template <int MODE, int KB, int MB, int GK, int GM, int JC, bool EXACT, int NW>
-__global__ void __launch_bounds__(NW * 32) solve_kernel(SolveArgs A) {
+template <int MODE, int KB, int MB, int GK, int GM, int JC, bool EXACT, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) solve_kernel(SolveArgs A) {
   SolveKernel<MODE, KB, MB, GK, GM, JC, EXACT, NW>::run(A);
 }
 

@@ -5,9 +5,9 @@
 namespace precode {
 
 void register_solve_pgd(std::vector<Variant>& v) {
-#define X(KB, MB, GK, GM, JC, EXACT, NW)                                                  \
-  v.push_back(Variant{kModePGD, KB, MB, GK, GM, JC, NW, EXACT,                           \
-                      (const void*)&solve_kernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW>, \
+#define X(KB, MB, GK, GM, JC, EXACT, NW, MINB)                                                 \
+  v.push_back(Variant{kModePGD, KB, MB, GK, GM, JC, NW, MINB, EXACT,                           \
+                      (const void*)&solve_kernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW, MINB>, \
                       SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::SMEM_BYTES, NW * 32,      \
                       SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::GROUPS});
 #include "solve_variants.inc"
