@@ -202,6 +202,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default kernel variant (no tuning launches; for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -222,7 +224,7 @@ def main():
     H = ch.lognormal(B, K, M, seed=wl.seed + 1000 * rank)
     t = ch.targets(B, K)
     mu = ch.fixed_workload_steps(T)
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=True)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=not args.no_autotune)
     Hd = torch.from_numpy(H).cuda()
     td = torch.from_numpy(t).cuda()
     md = torch.from_numpy(mu).cuda()

@@ -80,29 +80,47 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // ------------------------------------------------------------------ complex helpers
 
+// A complex value held as two independent scalars (no vector-register pairing,
+// so the register allocator may place the parts in any banks).
+struct cf {
+  float x, y;
+};
+
+template <class T>
+__device__ __forceinline__ T mkc(float x, float y) {
+  T r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+
 // acc += a * b
-__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
+template <class A, class P, class Q>
+__device__ __forceinline__ void cmac(A& acc, const P& a, const Q& b) {
   acc.x = fmaf(a.x, b.x, acc.x);
   acc.x = fmaf(-a.y, b.y, acc.x);
   acc.y = fmaf(a.x, b.y, acc.y);
   acc.y = fmaf(a.y, b.x, acc.y);
 }
 // acc += a * conj(b)
-__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {
+template <class A, class P, class Q>
+__device__ __forceinline__ void cmac_conj(A& acc, const P& a, const Q& b) {
   acc.x = fmaf(a.x, b.x, acc.x);
   acc.x = fmaf(a.y, b.y, acc.x);
   acc.y = fmaf(a.y, b.x, acc.y);
   acc.y = fmaf(-a.x, b.y, acc.y);
 }
 // acc -= a * b
-__device__ __forceinline__ void cmsub(float2& acc, float2 a, float2 b) {
+template <class A, class P, class Q>
+__device__ __forceinline__ void cmsub(A& acc, const P& a, const Q& b) {
   acc.x = fmaf(-a.x, b.x, acc.x);
   acc.x = fmaf(a.y, b.y, acc.x);
   acc.y = fmaf(-a.x, b.y, acc.y);
   acc.y = fmaf(-a.y, b.x, acc.y);
 }
 // acc -= a * conj(b)
-__device__ __forceinline__ void cmsub_conj(float2& acc, float2 a, float2 b) {
+template <class A, class P, class Q>
+__device__ __forceinline__ void cmsub_conj(A& acc, const P& a, const Q& b) {
   acc.x = fmaf(-a.x, b.x, acc.x);
   acc.x = fmaf(-a.y, b.y, acc.x);
   acc.y = fmaf(-a.y, b.x, acc.y);

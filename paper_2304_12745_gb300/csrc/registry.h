@@ -15,6 +15,8 @@ struct Variant {
   int NW;        // warps per block
   int minb;      // blocks per SM the register budget is built for
   bool exact;    // compiled for K == KB and M == MB only
+  bool split;    // complex registers as scalar pairs instead of float2
+  bool db;       // two channel buffers (next copy issued one instance ahead)
   const void* fn;
   int smem;      // dynamic shared memory per block (bytes)
   int threads;   // threads per block

@@ -25,6 +25,7 @@
 
 #include <cfloat>
 #include <cstdint>
+#include <type_traits>
 
 #include "device.cuh"
 #include "kernel_args.h"
@@ -38,7 +39,7 @@ constexpr uint64_t kCopyWaitNs = 1000000000ull;  // 1 s bound on one channel cop
 
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-template <int MODE, int KB, int MB, int GK, int GM, int JC_, int NW>
+template <int MODE, int KB, int MB, int GK, int GM, int JC_, int NW, bool DB = false>
 struct SolveCfg {
   static constexpr int TPI = GK * GM;            // threads per instance
   static constexpr int UPT = KB / GK;            // users per thread
@@ -52,6 +53,9 @@ struct SolveCfg {
   static constexpr int LPW = TPI >= 32 ? 32 : TPI;  // lanes of a group inside one warp
   static constexpr int PF = 2 * UPT * JC;        // partial floats per thread per pass
   static constexpr int SEG = PF / GM;            // reduced floats per thread per pass
+  // partial-buffer row stride: one extra segment (or 16 B) of padding makes the
+  // segment writes and the column reads bank-conflict free without index math
+  static constexpr int RS = PF + (SEG % 4 == 0 ? 4 : SEG);
   static_assert(KB % GK == 0 && MB % (2 * GM) == 0, "lane grid must tile the bucket");
   static_assert(KB % JC == 0, "reduction passes tile the residual columns");
   static_assert((GM & (GM - 1)) == 0 && GM <= 32 && (GK & (GK - 1)) == 0, "powers of two");
@@ -64,11 +68,12 @@ struct SolveCfg {
   static_assert(MODE == kModePGD || MB >= 5 * KB, "FP64 scratch lives in the Q area");
   // per-group shared memory (bytes)
   static constexpr int H_OFF = 0;
-  static constexpr int H_BYTES = KB * MB * 8;
-  static constexpr int Q_OFF = H_OFF + H_BYTES;
+  static constexpr int H_BYTES = KB * MB * 8;             // one channel buffer
+  static constexpr int NHB = DB ? 2 : 1;                  // channel buffers (DB: prefetch depth 2)
+  static constexpr int Q_OFF = H_OFF + NHB * H_BYTES;
   static constexpr int Q_BYTES = MODE == kModeProj ? KB * MB * 8 : 0;
   static constexpr int RED_OFF = Q_OFF + Q_BYTES;
-  static constexpr int RED_BYTES = align_up(TPI * PF * 4, 16);
+  static constexpr int RED_BYTES = align_up(TPI * RS * 4, 16);
   static constexpr int E_OFF = RED_OFF + RED_BYTES;
   static constexpr int E_BYTES = KB * KB * 8;
   static constexpr int NRM_OFF = E_OFF + E_BYTES;
@@ -76,17 +81,20 @@ struct SolveCfg {
   static constexpr int SC_OFF = NRM_OFF + NRM_BYTES;  // t[KB] dsc[KB] piv[KB] misc[8] wsum[WPG]
   static constexpr int SC_BYTES = align_up((3 * KB + 8 + WPG) * 4, 16);
   static constexpr int BAR_OFF = SC_OFF + SC_BYTES;
-  static constexpr int GROUP_BYTES = align_up(BAR_OFF + 8, 16);
+  static constexpr int GROUP_BYTES = align_up(BAR_OFF + 8 * NHB, 16);
   static constexpr int SMEM_BYTES = GROUPS * GROUP_BYTES;
-  static_assert(RED_BYTES >= KB * KB * 8, "unit-lower inverse lives in the reduction buffer");
+  static_assert(RED_BYTES >= 2 * KB * KB * 8, "Gauss-Jordan buffers live in the reduction buffer");
   static_assert(MODE == kModePGD || RED_BYTES >= KB * KB * 16, "FP64 inverse in reduction buffer");
 };
 
-template <int MODE, int KB, int MB, int GK, int GM, int JC_, bool EXACT, int NW>
+template <int MODE, int KB, int MB, int GK, int GM, int JC_, bool EXACT, int NW, bool SPLIT, bool DB>
 struct SolveKernel {
-  using C = SolveCfg<MODE, KB, MB, GK, GM, JC_, NW>;
+  using C = SolveCfg<MODE, KB, MB, GK, GM, JC_, NW, DB>;
+  // register form of complex W and partial sums: scalar pairs (SPLIT) or float2
+  using CT = typename std::conditional<SPLIT, cf, float2>::type;
   static constexpr int TPI = C::TPI, UPT = C::UPT, PPT = C::PPT, NA = C::NA, JC = C::JC,
-                       NJC = C::NJC, PF = C::PF, SEG = C::SEG, WPG = C::WPG, LPW = C::LPW;
+                       NJC = C::NJC, PF = C::PF, SEG = C::SEG, RS = C::RS, WPG = C::WPG,
+                       LPW = C::LPW;
 
   struct Ctx {
     float2* Hs;
@@ -105,8 +113,8 @@ struct SolveKernel {
     int K, M;
   };
 
-  using WReg = float2[UPT][NA];
-  using EReg = float2[UPT][JC];
+  using WReg = CT[UPT][NA];
+  using EReg = CT[UPT][JC];
 
   __device__ __forceinline__ static int Kd(const Ctx& c) { return EXACT ? KB : c.K; }
   __device__ __forceinline__ static int Md(const Ctx& c) { return EXACT ? MB : c.M; }
@@ -136,44 +144,38 @@ struct SolveKernel {
       for (int i = 0; i < PPT; ++i) {
         if (uok(c, u) && pok(c, i)) {
           const float4 v = *reinterpret_cast<const float4*>(X + user(c, u) * M + 2 * pair(c, i));
-          w[u][2 * i] = make_float2(v.x, v.y);
-          w[u][2 * i + 1] = make_float2(v.z, v.w);
+          w[u][2 * i] = mkc<CT>(v.x, v.y);
+          w[u][2 * i + 1] = mkc<CT>(v.z, v.w);
         } else {
-          w[u][2 * i] = make_float2(0.f, 0.f);
-          w[u][2 * i + 1] = make_float2(0.f, 0.f);
+          w[u][2 * i] = mkc<CT>(0.f, 0.f);
+          w[u][2 * i + 1] = mkc<CT>(0.f, 0.f);
         }
       }
   }
 
-  // e[u][jj] = sum over own antennas m of w[u][m] * X[j][m] (CJ: * conj(X[j][m])),
-  // j = jc*JC + jj.
-  template <bool CJ>
+  // e[u][jj] = sum over own antennas m of w[u][m] * X[j][m], j = jc*JC + jj.
+  // Pairs outer, residual columns inner: consecutive multiply-adds go to
+  // different accumulators.
   __device__ __forceinline__ static void partials(const Ctx& c, const WReg& w, const float2* X,
                                                   int jc, EReg& e) {
     const int K = Kd(c), M = Md(c);
 #pragma unroll
     for (int u = 0; u < UPT; ++u)
 #pragma unroll
-      for (int jj = 0; jj < JC; ++jj) e[u][jj] = make_float2(0.f, 0.f);
+      for (int jj = 0; jj < JC; ++jj) e[u][jj] = mkc<CT>(0.f, 0.f);
 #pragma unroll
-    for (int jj = 0; jj < JC; ++jj) {
-      const int j = jc * JC + jj;
-      if (!EXACT && j >= K) continue;
-      const float2* row = X + j * M;
+    for (int i = 0; i < PPT; ++i) {
+      if (!pok(c, i)) continue;
 #pragma unroll
-      for (int i = 0; i < PPT; ++i) {
-        if (!pok(c, i)) continue;
-        const float4 v = *reinterpret_cast<const float4*>(row + 2 * pair(c, i));
+      for (int jj = 0; jj < JC; ++jj) {
+        const int j = jc * JC + jj;
+        if (!EXACT && j >= K) continue;
+        const float4 v = *reinterpret_cast<const float4*>(X + j * M + 2 * pair(c, i));
         const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
 #pragma unroll
         for (int u = 0; u < UPT; ++u) {
-          if (CJ) {
-            cmac_conj(e[u][jj], w[u][2 * i], x0);
-            cmac_conj(e[u][jj], w[u][2 * i + 1], x1);
-          } else {
-            cmac(e[u][jj], w[u][2 * i], x0);
-            cmac(e[u][jj], w[u][2 * i + 1], x1);
-          }
+          cmac(e[u][jj], w[u][2 * i], x0);
+          cmac(e[u][jj], w[u][2 * i + 1], x1);
         }
       }
     }
@@ -188,10 +190,10 @@ struct SolveKernel {
   // Returns the sum of squares of the entries this thread wrote.
   __device__ __forceinline__ static float reduce(const Ctx& c, const EReg& e, int jc,
                                                  float scale, bool sub_s) {
-    float* row = c.red + (c.a * GM + c.b) * PF;
+    float* row = c.red + (c.a * GM + c.b) * RS;
 #pragma unroll
     for (int s = 0; s < GM; ++s) {
-      float* dst = row + (s ^ c.b) * SEG;
+      float* dst = row + s * SEG;
       if constexpr (SEG % 4 == 0) {
 #pragma unroll
         for (int q = 0; q < SEG; q += 4)
@@ -205,29 +207,37 @@ struct SolveKernel {
       }
     }
     __syncwarp(c.wmask);
-    float acc[SEG];
-#pragma unroll
-    for (int q = 0; q < SEG; ++q) acc[q] = 0.f;
+    // gather the GM partial segments of this thread's slot, then sum them as a tree
+    float part[GM][SEG];
 #pragma unroll
     for (int bb = 0; bb < GM; ++bb) {
-      const float* src = c.red + (c.a * GM + bb) * PF + (c.b ^ bb) * SEG;
+      const float* src = c.red + (c.a * GM + bb) * RS + c.b * SEG;
       if constexpr (SEG % 4 == 0) {
 #pragma unroll
         for (int q = 0; q < SEG; q += 4) {
           const float4 v = *reinterpret_cast<const float4*>(src + q);
-          acc[q] += v.x;
-          acc[q + 1] += v.y;
-          acc[q + 2] += v.z;
-          acc[q + 3] += v.w;
+          part[bb][q] = v.x;
+          part[bb][q + 1] = v.y;
+          part[bb][q + 2] = v.z;
+          part[bb][q + 3] = v.w;
         }
       } else if constexpr (SEG == 2) {
         const float2 v = *reinterpret_cast<const float2*>(src);
-        acc[0] += v.x;
-        acc[1] += v.y;
+        part[bb][0] = v.x;
+        part[bb][1] = v.y;
       } else {
-        acc[0] += *src;
+        part[bb][0] = *src;
       }
     }
+#pragma unroll
+    for (int span = 1; span < GM; span <<= 1)
+#pragma unroll
+      for (int bb = 0; bb + span < GM; bb += 2 * span)
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) part[bb][q] += part[bb + span][q];
+    float acc[SEG];
+#pragma unroll
+    for (int q = 0; q < SEG; ++q) acc[q] = part[0][q];
     float ssq = 0.f;
     float* Ef = reinterpret_cast<float*>(c.Es);
 #pragma unroll
@@ -308,23 +318,25 @@ struct SolveKernel {
 #pragma unroll 4
     for (int j = 0; j < KB; ++j) {
       if (!EXACT && j >= K) break;
-      float2 ej[UPT];
+      {
+        float2 ej[UPT];
 #pragma unroll
-      for (int u = 0; u < UPT; ++u) ej[u] = c.Es[user(c, u) * KB + j];
-      const float2* row = X + j * M;
+        for (int u = 0; u < UPT; ++u) ej[u] = c.Es[user(c, u) * KB + j];
+        const float2* row = X + j * M;
 #pragma unroll
-      for (int i = 0; i < PPT; ++i) {
-        if (!pok(c, i)) continue;
-        const float4 v = *reinterpret_cast<const float4*>(row + 2 * pair(c, i));
-        const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
+        for (int i = 0; i < PPT; ++i) {
+          if (!pok(c, i)) continue;
+          const float4 v = *reinterpret_cast<const float4*>(row + 2 * pair(c, i));
+          const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);
 #pragma unroll
-        for (int u = 0; u < UPT; ++u) {
-          if (CJ) {
-            cmsub_conj(w[u][2 * i], ej[u], x0);
-            cmsub_conj(w[u][2 * i + 1], ej[u], x1);
-          } else {
-            cmsub(w[u][2 * i], ej[u], x0);
-            cmsub(w[u][2 * i + 1], ej[u], x1);
+          for (int u = 0; u < UPT; ++u) {
+            if (CJ) {
+              cmsub_conj(w[u][2 * i], ej[u], x0);
+              cmsub_conj(w[u][2 * i + 1], ej[u], x1);
+            } else {
+              cmsub(w[u][2 * i], ej[u], x0);
+              cmsub(w[u][2 * i + 1], ej[u], x1);
+            }
           }
         }
       }
@@ -333,27 +345,38 @@ struct SolveKernel {
 
   // Projected-layer setup from Es = G^T = conj(H H^H) (Hermitian, same diagonal
   // and conditioning as G).  Its inverse is G^{-T}, so Q = G^{-T} H^* is formed
-  // directly.  Writes Q to Qs and W^(0) = S Q into w.  Returns the instance
-  // flags (FP64 fallback, singular, non-finite).
+  // directly.  The equilibrated matrix D G^T D (D = diag(G)^{-1/2}) is inverted
+  // in place by Gauss-Jordan elimination without pivoting, every thread owning
+  // fixed entries; its pivots are the LDL^H pivots d_p, so max(d)/min(d) is the
+  // condition estimate that decides the FP64 fallback.  Writes Q to Qs and
+  // W^(0) = S Q into w.  Returns the instance flags.
   __device__ static int setup_proj(Ctx& c, WReg& w, float cond_thr) {
     const int K = Kd(c), M = Md(c);
-    // equilibration D = diag(G)^{-1/2}
+    constexpr int NE = (KB * KB + TPI - 1) / TPI;  // matrix entries per thread
+    constexpr int LKB = KB == 4 ? 2 : KB == 8 ? 3 : KB == 16 ? 4 : 5;
+    static_assert((1 << LKB) == KB, "bucket K is a power of two");
     if (c.g < K) c.dsc[c.g] = rsqrtf(c.Es[c.g * KB + c.g].x);
     gsync(c);
-    for (int idx = c.g; idx < K * K; idx += TPI) {
-      const int i = idx / K, j = idx - i * K;
-      if (j <= i) {
+    // A0 = D G^T D in the reduction buffer (two K x K buffers ping-pong there)
+    float2* A0 = reinterpret_cast<float2*>(c.red);
+    float2* A1 = A0 + KB * KB;
+#pragma unroll
+    for (int r = 0; r < NE; ++r) {
+      const int idx = c.g + r * TPI;
+      const int i = idx >> LKB, j = idx & (KB - 1);
+      if (idx < KB * KB && i < K && j < K) {
         const float s = c.dsc[i] * c.dsc[j];
-        float2 v = c.Es[i * KB + j];
-        c.Es[i * KB + j] = make_float2(v.x * s, v.y * s);
+        const float2 v = c.Es[i * KB + j];
+        A0[i * KB + j] = make_float2(v.x * s, v.y * s);
       }
     }
     gsync(c);
-    // LDL^H elimination of the equilibrated Gram, lower triangle in place
     bool fail = false;
     float dmin = FLT_MAX, dmax = 0.f;
-    for (int j = 0; j < K; ++j) {
-      const float d = c.Es[j * KB + j].x;
+    float2* cur = A0;
+    float2* nxt = A1;
+    for (int p = 0; p < K; ++p) {
+      const float d = cur[p * KB + p].x;
       if (!(d > 0.f) || !(d < FLT_MAX)) {
         fail = true;
         break;
@@ -361,73 +384,68 @@ struct SolveKernel {
       dmin = fminf(dmin, d);
       dmax = fmaxf(dmax, d);
       const float inv = 1.f / d;
-      const int R = K - 1 - j;
-      for (int idx = c.g; idx < R * R; idx += TPI) {
-        const int i = j + 1 + idx / R, l = j + 1 + idx % R;
-        if (l > i) continue;
-        const float2 aij = c.Es[i * KB + j], alj = c.Es[l * KB + j];
-        float2 v = c.Es[i * KB + l];
-        cmsub_conj(v, make_float2(aij.x * inv, aij.y * inv), alj);
-        c.Es[i * KB + l] = v;
-      }
-      gsync(c);
-    }
-    if (!fail && !(dmax > cond_thr * dmin)) {
-      // U = L'^{-1} (unit lower), one column per thread; L'_ip = A_ip / d_p
-      float2* U = reinterpret_cast<float2*>(c.red);
-      if (c.g < K) c.piv[c.g] = 1.f / c.Es[c.g * KB + c.g].x;
-      gsync(c);
-      if (c.g < K) {
-        const int col = c.g;
-        U[col * KB + col] = make_float2(1.f, 0.f);
-        for (int i = col + 1; i < K; ++i) {
-          float2 s = make_float2(0.f, 0.f);
-          for (int p = col; p < i; ++p) {
-            const float2 a = c.Es[i * KB + p];
-            const float ip = c.piv[p];
-            cmac(s, make_float2(a.x * ip, a.y * ip), U[p * KB + col]);
+#pragma unroll
+      for (int r = 0; r < NE; ++r) {
+        const int idx = c.g + r * TPI;
+        const int i = idx >> LKB, j = idx & (KB - 1);
+        if (idx < KB * KB && i < K && j < K) {
+          float2 v;
+          if (i == p && j == p) {
+            v = make_float2(inv, 0.f);
+          } else if (i == p) {
+            const float2 a = cur[p * KB + j];
+            v = make_float2(a.x * inv, a.y * inv);
+          } else if (j == p) {
+            const float2 a = cur[i * KB + p];
+            v = make_float2(-a.x * inv, -a.y * inv);
+          } else {
+            const float2 aip = cur[i * KB + p], apj = cur[p * KB + j];
+            v = cur[i * KB + j];
+            cmsub(v, make_float2(aip.x * inv, aip.y * inv), apj);
           }
-          U[i * KB + col] = make_float2(-s.x, -s.y);
+          nxt[i * KB + j] = v;
         }
       }
       gsync(c);
-      // (G^T)^{-1}_ij = dsc_i dsc_j sum_{p >= max(i,j)} conj(U_pi) U_pj / d_p  -> Es
-      for (int idx = c.g; idx < K * K; idx += TPI) {
-        const int i = idx / K, j = idx - i * K;
-        float2 s = make_float2(0.f, 0.f);
-        for (int p = (i > j ? i : j); p < K; ++p) {
-          const float2 upi = U[p * KB + i];
-          const float ip = c.piv[p];
-          cmac_conj(s, U[p * KB + j], make_float2(upi.x * ip, upi.y * ip));
-        }
-        const float sc = c.dsc[i] * c.dsc[j];
-        c.Es[i * KB + j] = make_float2(s.x * sc, s.y * sc);
-      }
-      gsync(c);
-      // Q = G^{-T} H^* on own entries; W^(0) = t_k Q
-#pragma unroll
-      for (int u = 0; u < UPT; ++u)
-#pragma unroll
-        for (int q = 0; q < NA; ++q) w[u][q] = make_float2(0.f, 0.f);
-      for (int l = 0; l < K; ++l) {
-        float2 gl[UPT];
-#pragma unroll
-        for (int u = 0; u < UPT; ++u) gl[u] = c.Es[user(c, u) * KB + l];
-#pragma unroll
-        for (int i = 0; i < PPT; ++i) {
-          if (!pok(c, i)) continue;
-          const float4 v = *reinterpret_cast<const float4*>(c.Hs + l * M + 2 * pair(c, i));
-#pragma unroll
-          for (int u = 0; u < UPT; ++u) {
-            cmac_conj(w[u][2 * i], gl[u], make_float2(v.x, v.y));
-            cmac_conj(w[u][2 * i + 1], gl[u], make_float2(v.z, v.w));
-          }
-        }
-      }
-      store_q_and_start(c, w);
-      return 0;
+      float2* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
     }
-    return setup_proj_fp64(c, w);
+    if (fail || dmax > cond_thr * dmin) return setup_proj_fp64(c, w);
+    // G^{-T} = D (D G^T D)^{-1} D  -> Es
+#pragma unroll
+    for (int r = 0; r < NE; ++r) {
+      const int idx = c.g + r * TPI;
+      const int i = idx >> LKB, j = idx & (KB - 1);
+      if (idx < KB * KB && i < K && j < K) {
+        const float s = c.dsc[i] * c.dsc[j];
+        const float2 v = cur[i * KB + j];
+        c.Es[i * KB + j] = make_float2(v.x * s, v.y * s);
+      }
+    }
+    gsync(c);
+    // Q = G^{-T} H^* on own entries; W^(0) = t_k Q
+#pragma unroll
+    for (int u = 0; u < UPT; ++u)
+#pragma unroll
+      for (int q = 0; q < NA; ++q) w[u][q] = mkc<CT>(0.f, 0.f);
+    for (int l = 0; l < K; ++l) {
+      float2 gl[UPT];
+#pragma unroll
+      for (int u = 0; u < UPT; ++u) gl[u] = c.Es[user(c, u) * KB + l];
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        if (!pok(c, i)) continue;
+        const float4 v = *reinterpret_cast<const float4*>(c.Hs + l * M + 2 * pair(c, i));
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+          cmac_conj(w[u][2 * i], gl[u], make_float2(v.x, v.y));
+          cmac_conj(w[u][2 * i + 1], gl[u], make_float2(v.z, v.w));
+        }
+      }
+    }
+    store_q_and_start(c, w);
+    return 0;
   }
 
   // Q = w into Qs for own entries, then w <- t_k Q.
@@ -438,13 +456,13 @@ struct SolveKernel {
       const float tk = uok(c, u) ? c.tks[user(c, u)] : 0.f;
 #pragma unroll
       for (int i = 0; i < PPT; ++i) {
-        const float2 q0 = w[u][2 * i];
-        const float2 q1 = w[u][2 * i + 1];
+        const CT q0 = w[u][2 * i];
+        const CT q1 = w[u][2 * i + 1];
         if (uok(c, u) && pok(c, i))
           *reinterpret_cast<float4*>(c.Qs + user(c, u) * M + 2 * pair(c, i)) =
               make_float4(q0.x, q0.y, q1.x, q1.y);
-        w[u][2 * i] = make_float2(tk * q0.x, tk * q0.y);
-        w[u][2 * i + 1] = make_float2(tk * q1.x, tk * q1.y);
+        w[u][2 * i] = mkc<CT>(tk * q0.x, tk * q0.y);
+        w[u][2 * i + 1] = mkc<CT>(tk * q1.x, tk * q1.y);
       }
     }
     gsync(c);
@@ -501,7 +519,7 @@ struct SolveKernel {
 #pragma unroll
       for (int u = 0; u < UPT; ++u)
 #pragma unroll
-        for (int q = 0; q < NA; ++q) w[u][q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < NA; ++q) w[u][q] = mkc<CT>(0.f, 0.f);
       return fl | PRECODE_F_SINGULAR;
     }
     if (c.g < K) pv[c.g] = 1.0 / G[c.g * KB + c.g].x;
@@ -550,7 +568,7 @@ struct SolveKernel {
               zi += gkl.x * x.y + gkl.y * x.x;
             }
           }
-          w[u][2 * i + h] = make_float2((float)zr, (float)-zi);  // Q = conj(G^{-1} H)
+          w[u][2 * i + h] = mkc<CT>((float)zr, (float)-zi);  // Q = conj(G^{-1} H)
         }
     gsync(c);  // every thread is done with the FP64 scratch before Q overwrites it
     store_q_and_start(c, w);
@@ -599,48 +617,67 @@ struct SolveKernel {
     c.misc = reinterpret_cast<int*>(c.piv + KB);
     c.wsum = reinterpret_cast<float*>(c.misc + 8);
     c.bar = reinterpret_cast<uint64_t*>(gs + C::BAR_OFF);
+    c.Hs = reinterpret_cast<float2*>(gs + C::H_OFF);
 
-    if (c.g == 0) mbar_init(c.bar, 1);
+    constexpr int NHB = C::NHB;
+    if (c.g == 0)
+      for (int q = 0; q < NHB; ++q) mbar_init(c.bar + q, 1);
     fence_mbar_init();
     __syncthreads();
 
-    uint32_t phase = 0;
+    float2* const hbuf0 = reinterpret_cast<float2*>(gs + C::H_OFF);
+    uint32_t phases = 0;  // bit q: parity of the next completion of buffer q
     const int64_t n_inst = A.tbl ? (int64_t)(*A.count) : A.B;
-    WReg w;
-    EReg e;
-    float r2[NA];
-#pragma unroll 1
-    for (int64_t it = (int64_t)blockIdx.x * C::GROUPS + c.gid; it < n_inst;
-         it += (int64_t)gridDim.x * C::GROUPS) {
-      int64_t inst, h_off, w_off, t_off;
+    const int64_t stride = (int64_t)gridDim.x * C::GROUPS;
+    // where instance `it` lives: H / W / t offsets and shape
+    auto locate = [&](int64_t it, int64_t& inst, int64_t& h_off, int64_t& w_off, int64_t& t_off,
+                      int& Kr, int& Mr) {
       if (A.tbl) {
         inst = A.index[it];
         const InstDesc d = A.tbl[inst];
         h_off = d.h_off;
         w_off = d.w_off;
         t_off = d.t_off;
-        c.K = d.K;
-        c.M = d.M;
+        Kr = d.K;
+        Mr = d.M;
       } else {
         inst = it;
-        c.K = A.K;
-        c.M = A.M;
+        Kr = A.K;
+        Mr = A.M;
         h_off = it * (int64_t)A.K * A.M;
         w_off = h_off;
         t_off = it * A.t_stride;
       }
+    };
+    // one bulk async copy of instance `it`'s channel into channel buffer q
+    auto issue_copy = [&](int64_t it, int q) {
+      if (c.g != 0 || it >= n_inst) return;
+      int64_t inst, h_off, w_off, t_off;
+      int Kr, Mr;
+      locate(it, inst, h_off, w_off, t_off, Kr, Mr);
+      const uint32_t bytes = (uint32_t)((EXACT ? KB : Kr) * (EXACT ? MB : Mr)) * 8u;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(c.bar + q, bytes);
+      bulk_g2s(hbuf0 + q * (KB * MB), A.H + h_off, bytes, c.bar + q);
+    };
+    WReg w;
+    EReg e;
+    float r2[NA];
+    const int64_t first = (int64_t)blockIdx.x * C::GROUPS + c.gid;
+    for (int q = 0; q < NHB; ++q) issue_copy(first + q * stride, q);
+    int cur = 0;  // channel buffer of the current instance
+#pragma unroll 1
+    for (int64_t it = first; it < n_inst; it += stride, cur = (cur + 1) % NHB) {
+      int64_t inst, h_off, w_off, t_off;
+      locate(it, inst, h_off, w_off, t_off, c.K, c.M);
       const int K = Kd(c), M = Md(c);
+      c.Hs = hbuf0 + cur * (KB * MB);
+      const uint32_t par = (phases >> cur) & 1u;
 
-      // ---- channel copy into shared memory (one bulk async copy)
+      // ---- wait for this instance's channel (its copy was issued earlier)
       gsync(c);  // every thread of the group is done with the previous instance
-      if (c.g == 0) {
-        fence_proxy_async_smem();
-        const uint32_t bytes = (uint32_t)(K * M) * 8u;
-        mbar_arrive_expect_tx(c.bar, bytes);
-        bulk_g2s(c.Hs, A.H + h_off, bytes, c.bar);
-      }
       if (c.g < K) c.tks[c.g] = A.t[t_off + c.g];
-      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs) ? 1 : 0;
       gsync(c);
       if (c.misc[0] == 0) {
         // the copy did not land in time: report, then wait (bounded) for it
@@ -648,15 +685,16 @@ struct SolveKernel {
         if (c.g == 0) {
           atomicAdd(A.err, 1ull);
           if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
-          c.misc[1] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+          c.misc[1] = mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs) ? 1 : 0;
         }
         gsync(c);
         if (c.misc[1] == 0) return;
-        phase ^= 1;
+        phases ^= 1u << cur;
+        issue_copy(it + NHB * stride, cur);
         continue;
       }
-      if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);  // already complete
-      phase ^= 1;
+      if (c.g != 0) mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs);  // already complete
+      phases ^= 1u << cur;
 
       // ---- steps -1 .. T of one instance.  Step -1 (Gram, when needed) and
       // step T (final residual, when requested) share the residual code of the
@@ -685,7 +723,7 @@ struct SolveKernel {
         rs = 0.f;
 #pragma unroll 1
         for (int jc = 0; jc < NJC; ++jc) {
-          partials<false>(c, w, c.Hs, jc, e);
+          partials(c, w, c.Hs, jc, e);
           rs += reduce(c, e, jc, scale, s >= 0);
         }
         if (s < 0) {
@@ -715,7 +753,10 @@ struct SolveKernel {
           for (int k = 0; k < K; ++k) rs += c.tks[k] * c.tks[k];
       }
 
-      // ---- epilogue: objective, residual, W
+      // ---- the channel buffer is free: start the next instance's copy, then
+      // finish this one (objective, residual, W) while it is in flight
+      gsync(c);
+      issue_copy(it + NHB * stride, cur);
       colnorm2(c, w, r2);
       float o = 0.f;
 #pragma unroll
@@ -749,9 +790,10 @@ struct SolveKernel {
   }
 };
 
-template <int MODE, int KB, int MB, int GK, int GM, int JC, bool EXACT, int NW, int MINB>
+template <int MODE, int KB, int MB, int GK, int GM, int JC, bool EXACT, int NW, int MINB,
+          bool SPLIT, bool DB>
 __global__ void __launch_bounds__(NW * 32, MINB) solve_kernel(SolveArgs A) {
-  SolveKernel<MODE, KB, MB, GK, GM, JC, EXACT, NW>::run(A);
+  SolveKernel<MODE, KB, MB, GK, GM, JC, EXACT, NW, SPLIT, DB>::run(A);
 }
 
 }  // namespace precode

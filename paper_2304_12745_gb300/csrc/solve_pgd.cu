@@ -5,11 +5,11 @@
 namespace precode {
 
 void register_solve_pgd(std::vector<Variant>& v) {
-#define X(KB, MB, GK, GM, JC, EXACT, NW, MINB)                                                 \
-  v.push_back(Variant{kModePGD, KB, MB, GK, GM, JC, NW, MINB, EXACT,                           \
-                      (const void*)&solve_kernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW, MINB>, \
-                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::SMEM_BYTES, NW * 32,      \
-                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::GROUPS});
+#define X(KB, MB, GK, GM, JC, EXACT, NW, MINB, SPLIT, DB)                                                 \
+  v.push_back(Variant{kModePGD, KB, MB, GK, GM, JC, NW, MINB, EXACT, SPLIT, DB,                           \
+                      (const void*)&solve_kernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW, MINB, SPLIT, DB>, \
+                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW, DB>::SMEM_BYTES, NW * 32,      \
+                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW, DB>::GROUPS});
 #include "solve_variants.inc"
 #undef X
 }
