@@ -73,6 +73,9 @@ typedef enum {
 #define PRECODE_F_NONFINITE 4   /* NaN/Inf met in the input or the output objective */
 #define PRECODE_F_TIMEOUT 8     /* the device-side wait for this instance's channel copy
                                    ran out (about 1 s); W not written */
+#define PRECODE_F_INVALID 16    /* uneven batch: descriptor rejected (shape outside every
+                                   plan bucket, odd M, K > M for PROJ, negative or odd
+                                   offset); W not written */
 
 /* plan flags (precode_desc_t.flags) */
 #define PRECODE_PLAN_AUTOTUNE 1u        /* time the kernel variants of each shape at plan
@@ -80,6 +83,10 @@ typedef enum {
 #define PRECODE_PLAN_STEP_NORMALISED 2u /* PGD only: use eta_l / L_b with the per-instance
                                            Gershgorin bound L_b = max_k sum_j |G_kj| >=
                                            lambda_max(H H^H) instead of eta_l */
+#define PRECODE_PLAN_GRAPHS 4u          /* uneven batches run as one CUDA graph (bucketing
+                                           kernel + one solve node per bucket), built on the
+                                           first precode_solve_varlen call and re-armed with
+                                           new arguments on later calls */
 
 #define PRECODE_MAX_K 32
 #define PRECODE_MAX_M 256
@@ -103,6 +110,17 @@ typedef struct {
 } precode_desc_t;
 
 typedef struct precode_plan_s* precode_plan_t;
+
+/* One instance of an uneven batch.  Offsets are in elements from the H / W base
+ * (complex64 elements, must be even: 16-byte aligned) and from the t base
+ * (floats).  Instance b's H is K*M contiguous complex64 values [K][M]. */
+typedef struct {
+  int64_t h_off;
+  int64_t w_off;
+  int64_t t_off;
+  int32_t M;
+  int32_t K;
+} precode_inst_t;
 
 /* Create a plan: validates the descriptor, picks a kernel variant per shape
  * (autotuned when PRECODE_PLAN_AUTOTUNE is set, which launches kernels on the
@@ -130,6 +148,19 @@ precode_status_t precode_solve_host(precode_plan_t plan, int32_t M, int32_t K, i
                                     const void* H, const float* t, int64_t t_stride,
                                     const float* step, const float* lam, void* W, float* obj,
                                     float* resid, int32_t* flags);
+
+/* Uneven batch of B instances described by the DEVICE table tbl[B] (any mix of
+ * shapes).  A bucketing kernel sorts the instances into the plan's buckets (each
+ * plan shape, plus one generic bucket per bucket size that serves any K <= KB,
+ * M <= MB), then one persistent solve launch per bucket processes its list; with
+ * PRECODE_PLAN_GRAPHS the whole sequence is one CUDA graph launch.  Every
+ * instance's result is the same as from precode_solve with its shape.  Outputs
+ * obj / resid / flags are indexed by b.  Instances no bucket serves get
+ * PRECODE_F_INVALID.  Uses the plan's instance-list workspace (B <= max_instances). */
+precode_status_t precode_solve_varlen(precode_plan_t plan, int64_t B, const precode_inst_t* tbl,
+                                      const void* H, const float* t, const float* step,
+                                      const float* lam, void* W, float* obj, float* resid,
+                                      int32_t* flags, precode_stream_t stream);
 
 /* Number of device-side wait timeouts recorded by the plan's kernels since the
  * plan was created (synchronises the plan's device).  0 in normal operation. */

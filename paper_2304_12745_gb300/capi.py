@@ -16,8 +16,8 @@ LIB_PATH = os.path.join(HERE, "libprecode.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, PENDING, ENOTFOUND = range(8)
 LAYER_PGD, LAYER_PROJ = 0, 1
-F_FP64_CHOL, F_SINGULAR, F_NONFINITE, F_TIMEOUT = 1, 2, 4, 8
-PLAN_AUTOTUNE, PLAN_STEP_NORMALISED = 1, 2
+F_FP64_CHOL, F_SINGULAR, F_NONFINITE, F_TIMEOUT, F_INVALID = 1, 2, 4, 8, 16
+PLAN_AUTOTUNE, PLAN_STEP_NORMALISED, PLAN_GRAPHS = 1, 2, 4
 MAX_K, MAX_M, MAX_T = 32, 256, 65536
 
 
@@ -47,6 +47,7 @@ _SIGS = {
     "precode_solve": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_solve_host": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_plan_errors": [_vp, ctypes.POINTER(ctypes.c_uint64)],
+    "precode_solve_varlen": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
 }
 
 
@@ -107,6 +108,11 @@ def precode_solve(plan, M, K, B, H, t, t_stride, step, lam, W, obj, resid, flags
 def precode_solve_host(plan, M, K, B, H, t, t_stride, step, lam, W, obj, resid, flags):
     check(LIB.precode_solve_host(plan, M, K, B, ptr(H), ptr(t), t_stride, ptr(step), ptr(lam),
                                  ptr(W), ptr(obj), ptr(resid), ptr(flags)), "precode_solve_host")
+
+
+def precode_solve_varlen(plan, B, tbl, H, t, step, lam, W, obj, resid, flags, stream):
+    check(LIB.precode_solve_varlen(plan, B, ptr(tbl), ptr(H), ptr(t), ptr(step), ptr(lam), ptr(W),
+                                   ptr(obj), ptr(resid), ptr(flags), stream), "precode_solve_varlen")
 
 
 def precode_plan_errors(plan) -> int:

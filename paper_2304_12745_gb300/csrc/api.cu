@@ -118,43 +118,39 @@ bool shape_ok(int mode, int M, int K) {
 
 using namespace precode;
 
-struct precode_plan_s {
-  int mode = 0, T = 0, device = 0, num_sms = 0;
-  std::vector<precode_shape_t> shapes;
-  std::vector<const Variant*> chosen;
-  int64_t max_instances = 0;
-  float cond_thr = 1e3f;
-  uint32_t flags = 0;
-  unsigned long long* d_err = nullptr;
-  // host-buffer pipeline
-  static constexpr int kPipe = 2;
-  cudaStream_t hstream[kPipe] = {nullptr, nullptr};
-  int64_t chunk = 0;
-  size_t chunk_elems = 0;  // complex elements per chunk buffer
-  void* dH[kPipe] = {};
-  void* dW[kPipe] = {};
-  float* dt[kPipe] = {};
-  float* dobj[kPipe] = {};
-  float* dres[kPipe] = {};
-  int32_t* dfl[kPipe] = {};
-  float* dparams = nullptr;  // [2][T]
-  std::mutex mu;
-
-  const Variant* variant_for(int M, int K) const {
-    for (size_t i = 0; i < shapes.size(); ++i)
-      if (shapes[i].M == M && shapes[i].K == K) return chosen[i];
-    // not a plan shape: any prepared variant whose bucket holds it
-    const Variant* best = nullptr;
-    for (auto* v : chosen)
-      if (!v->exact && v->KB >= K && v->MB >= M && (!best || v->KB * v->MB < best->KB * best->MB))
-        best = v;
-    return best;
+namespace precode {
+void plan_build_buckets(precode_plan_t p) {
+  p->buckets.clear();
+  for (size_t i = 0; i < p->shapes.size(); ++i) {
+    bool dup = false;
+    for (const auto& b : p->buckets) dup |= (b.M == p->shapes[i].M && b.K == p->shapes[i].K);
+    if (!dup) p->buckets.push_back(Bucket{p->shapes[i].M, p->shapes[i].K, p->chosen[i]});
   }
-};
+  const size_t n = p->buckets.size();
+  for (size_t i = 0; i < n; ++i) {
+    const Variant* v = p->buckets[i].v;
+    if (!v->exact) continue;
+    const Variant* gen = nullptr;
+    for (const auto& cand : variants())
+      if (cand.mode == p->mode && !cand.exact && cand.KB == v->KB && cand.MB == v->MB) {
+        gen = &cand;
+        break;
+      }
+    if (!gen) continue;
+    bool dup = false;
+    for (const auto& b : p->buckets) dup |= (b.v == gen);
+    if (!dup) p->buckets.push_back(Bucket{gen->MB, gen->KB, gen});
+  }
+}
+}  // namespace precode
 
 static void plan_free(precode_plan_t p) {
   if (!p) return;
   DeviceGuard g(p->device);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->d_index);
+  cudaFree(p->d_count);
   if (p->d_err) cudaFree(p->d_err);
   for (int i = 0; i < precode_plan_s::kPipe; ++i) {
     if (p->hstream[i]) cudaStreamDestroy(p->hstream[i]);
@@ -171,17 +167,6 @@ static void plan_free(precode_plan_t p) {
 
 namespace precode {
 precode_status_t autotune_plan(precode_plan_t p, const char* cache_path);
-int plan_mode(precode_plan_t p) { return p->mode; }
-int plan_T(precode_plan_t p) { return p->T; }
-int plan_device(precode_plan_t p) { return p->device; }
-int plan_num_sms(precode_plan_t p) { return p->num_sms; }
-float plan_cond(precode_plan_t p) { return p->cond_thr; }
-uint32_t plan_flags(precode_plan_t p) { return p->flags; }
-unsigned long long* plan_err(precode_plan_t p) { return p->d_err; }
-int64_t plan_max_instances(precode_plan_t p) { return p->max_instances; }
-std::vector<precode_shape_t>& plan_shapes(precode_plan_t p) { return p->shapes; }
-std::vector<const Variant*>& plan_chosen(precode_plan_t p) { return p->chosen; }
-const Variant* plan_variant_for(precode_plan_t p, int M, int K) { return p->variant_for(M, K); }
 }  // namespace precode
 
 extern "C" {
@@ -247,6 +232,10 @@ precode_status_t precode_plan(const precode_desc_t* d, precode_plan_t* out) {
       precode_status_t st = autotune_plan(p.get(), d->tune_cache);
       if (st != PRECODE_OK) return st;
     }
+    plan_build_buckets(p.get());
+    for (const auto& b : p->buckets)
+      if (variant_occupancy(*b.v, p->device) <= 0)
+        return fail(PRECODE_ECUDA, "precode_plan: bucket variant cannot run on this device");
     *out = p.release();
     return PRECODE_OK;
   } catch (const std::exception& ex) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -25,6 +26,9 @@ class DeviceGuard {
 };
 
 bool shape_ok(int mode, int M, int K);
+// (Re)build plan->buckets from plan->shapes / plan->chosen plus one generic bucket
+// per bucket size, so every shape a plan bucket can hold has a home.
+void plan_build_buckets(precode_plan_t p);
 int variant_occupancy(const Variant& v, int device);
 const Variant* pick_variant(int mode, int M, int K);
 std::vector<const Variant*> eligible_variants(int mode, int M, int K);
@@ -32,16 +36,58 @@ std::vector<const Variant*> eligible_variants(int mode, int M, int K);
 precode_status_t launch_variant(const Variant& v, int device, int num_sms, const SolveArgs& A,
                                 int64_t n_hint, cudaStream_t stream);
 
-int plan_mode(precode_plan_t p);
-int plan_T(precode_plan_t p);
-int plan_device(precode_plan_t p);
-int plan_num_sms(precode_plan_t p);
-float plan_cond(precode_plan_t p);
-uint32_t plan_flags(precode_plan_t p);
-unsigned long long* plan_err(precode_plan_t p);
-int64_t plan_max_instances(precode_plan_t p);
-std::vector<precode_shape_t>& plan_shapes(precode_plan_t p);
-std::vector<const Variant*>& plan_chosen(precode_plan_t p);
-const Variant* plan_variant_for(precode_plan_t p, int M, int K);
+// One bucket of an uneven batch: instances of exactly (M, K) when the variant is an
+// exact build, else every shape the generic variant holds.
+struct Bucket {
+  int M, K;
+  const Variant* v;
+};
 
 }  // namespace precode
+
+struct precode_plan_s {
+  int mode = 0, T = 0, device = 0, num_sms = 0;
+  std::vector<precode_shape_t> shapes;
+  std::vector<const precode::Variant*> chosen;
+  // uneven batches: buckets, instance lists, counts and the captured graph
+  std::vector<precode::Bucket> buckets;
+  int32_t* d_index = nullptr;  // [n_buckets][max_instances]
+  int32_t* d_count = nullptr;  // [n_buckets]
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<cudaGraphNode_t> graph_nodes;  // bucketize, then one solve node per bucket
+
+  int64_t max_instances = 0;
+  float cond_thr = 1e3f;
+  uint32_t flags = 0;
+  unsigned long long* d_err = nullptr;
+  // host-buffer pipeline
+  static constexpr int kPipe = 2;
+  cudaStream_t hstream[kPipe] = {nullptr, nullptr};
+  int64_t chunk = 0;
+  size_t chunk_elems = 0;  // complex elements per chunk buffer
+  void* dH[kPipe] = {};
+  void* dW[kPipe] = {};
+  float* dt[kPipe] = {};
+  float* dobj[kPipe] = {};
+  float* dres[kPipe] = {};
+  int32_t* dfl[kPipe] = {};
+  float* dparams = nullptr;  // [2][T]
+  std::mutex mu;
+
+  // Variant serving (M, K): the plan shape's own variant, else the smallest
+  // generic bucket of the plan that holds the shape (nullptr if none).
+  const precode::Variant* variant_for(int M, int K) const {
+    for (size_t i = 0; i < shapes.size(); ++i)
+      if (shapes[i].M == M && shapes[i].K == K) return chosen[i];
+    const precode::Variant* best = nullptr;
+    for (const auto& bk : buckets) {
+      const precode::Variant* v = bk.v;
+      if (!v->exact && v->KB >= K && v->MB >= M && (!best || v->KB * v->MB < best->KB * best->MB))
+        best = v;
+    }
+    return best;
+  }
+};
+
+

@@ -49,7 +49,7 @@ std::string variant_key(const Variant& v) {
 }  // namespace
 
 precode_status_t autotune_plan(precode_plan_t p, const char* cache_path) {
-  const int dev = plan_device(p);
+  const int dev = p->device;
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, dev);
   std::map<std::string, std::string> cache;  // "dev|mode|K|M" -> variant key
@@ -62,21 +62,21 @@ precode_status_t autotune_plan(precode_plan_t p, const char* cache_path) {
     }
   }
   bool dirty = false;
-  auto& shapes = plan_shapes(p);
-  auto& chosen = plan_chosen(p);
+  auto& shapes = p->shapes;
+  auto& chosen = p->chosen;
   for (size_t si = 0; si < shapes.size(); ++si) {
     const int M = shapes[si].M, K = shapes[si].K;
     std::ostringstream ks;
-    ks << prop.name << "|" << plan_mode(p) << "|" << K << "|" << M;
-    const auto cands = eligible_variants(plan_mode(p), M, K);
+    ks << prop.name << "|" << p->mode << "|" << K << "|" << M;
+    const auto cands = eligible_variants(p->mode, M, K);
     auto hit = cache.find(ks.str());
     if (hit != cache.end()) {
       for (auto* v : cands)
         if (variant_key(*v) == hit->second && variant_occupancy(*v, dev) > 0) chosen[si] = v;
       continue;
     }
-    const int64_t B = std::min<int64_t>(plan_max_instances(p), 16384);
-    const int T = plan_T(p);
+    const int64_t B = std::min<int64_t>(p->max_instances, 16384);
+    const int T = p->T;
     float2 *H = nullptr, *W = nullptr;
     float *t = nullptr, *prm = nullptr;
     if (cudaMalloc(&H, (size_t)B * K * M * 8) != cudaSuccess ||
@@ -110,12 +110,12 @@ precode_status_t autotune_plan(precode_plan_t p, const char* cache_path) {
       A.K = K;
       A.M = M;
       A.T = T;
-      A.cond_thr = plan_cond(p);
-      A.err = plan_err(p);
+      A.cond_thr = p->cond_thr;
+      A.err = p->d_err;
       float ms_min = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0);
-        if (launch_variant(*v, dev, plan_num_sms(p), A, B, 0) != PRECODE_OK) break;
+        if (launch_variant(*v, dev, p->num_sms, A, B, 0) != PRECODE_OK) break;
         cudaEventRecord(e1);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -123,7 +123,7 @@ precode_status_t autotune_plan(precode_plan_t p, const char* cache_path) {
         if (rep > 0) ms_min = std::min(ms_min, ms);
       }
       if (std::getenv("PRECODE_TUNE_LOG"))
-        std::fprintf(stderr, "[precode autotune] mode %d K=%d M=%d %s: %.4f ms\n", plan_mode(p), K,
+        std::fprintf(stderr, "[precode autotune] mode %d K=%d M=%d %s: %.4f ms\n", p->mode, K,
                      M, variant_key(*v).c_str(), ms_min);
       if (ms_min < best_ms) {
         best_ms = ms_min;

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "precode.h"
+
 namespace precode {
 
 // One instance of an uneven batch: offsets in elements (complex for H/W, float for t).
@@ -14,6 +16,7 @@ struct InstDesc {
   int32_t M;
   int32_t K;
 };
+static_assert(sizeof(InstDesc) == sizeof(precode_inst_t), "descriptor layout matches the ABI");
 
 enum : uint32_t {
   OPT_STEP_NORMALISED = 1u,  // PGD: eta_l / (max_k sum_j |G_kj|)

@@ -34,3 +34,13 @@ def test_status_strings_without_gpu():
     capi.LIB.precode_status_str.restype = ctypes.c_char_p
     assert capi.LIB.precode_status_str(0) == b"ok"
     assert capi.LIB.precode_status_str(1) == b"invalid argument"
+
+
+def test_instance_descriptor_packing_matches_abi_layout():
+    import numpy as np
+    from paper_2304_12745_gb300.precoder import inst_table
+    t = inst_table([0, 4096], [2, 4098], [0, 8], [64, 256], [8, 32]).numpy()
+    assert t.shape == (2, 4) and t.dtype == np.int64
+    raw = t.view(np.int32).reshape(2, 8)
+    assert list(t[1, :3]) == [4096, 4098, 8]
+    assert list(raw[0, 6:]) == [64, 8] and list(raw[1, 6:]) == [256, 32]
