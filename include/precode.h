@@ -162,6 +162,32 @@ precode_status_t precode_solve_varlen(precode_plan_t plan, int64_t B, const prec
                                       const float* lam, void* W, float* obj, float* resid,
                                       int32_t* flags, precode_stream_t stream);
 
+/* Uneven-batch solve that allocates no device memory (the paper has no
+ * counterpart: this is a deployment variant of precode_solve_varlen).  For
+ * callers that may not call cudaMalloc on their processing path, such as a
+ * real-time baseband loop that reserves all memory at start-up, or a host
+ * application whose memory manager owns the device.  No plan is needed: `desc`
+ * gives mode, T, the shapes (buckets), cond_threshold, device and flags
+ * (PRECODE_PLAN_STEP_NORMALISED only; AUTOTUNE or GRAPHS -> EINVAL); its
+ * max_instances is ignored.  Arguments and results are those of
+ * precode_solve_varlen, with the default kernel variant of each shape.
+ * Scratch (bucket instance lists, counters, timeout counter) is one fixed
+ * array inside the library, about 2 MiB, that every GPU loading the library
+ * holds until exit.  Limits: B <= PRECODE_STATIC_MAX_INSTANCES and at most
+ * PRECODE_STATIC_MAX_BUCKETS buckets (the shapes plus one generic bucket per
+ * bucket size); larger requests return EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and must come
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. */
+#define PRECODE_STATIC_MAX_INSTANCES 65536
+#define PRECODE_STATIC_MAX_BUCKETS 8
+precode_status_t precode_solve_varlen_static(const precode_desc_t* desc, int64_t B,
+                                             const precode_inst_t* tbl, const void* H,
+                                             const float* t, const float* step, const float* lam,
+                                             void* W, float* obj, float* resid, int32_t* flags,
+                                             precode_stream_t stream);
+
 /* Number of device-side wait timeouts recorded by the plan's kernels since the
  * plan was created (synchronises the plan's device).  0 in normal operation. */
 precode_status_t precode_plan_errors(precode_plan_t plan, uint64_t* count);

@@ -48,6 +48,8 @@ _SIGS = {
     "precode_solve_host": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_plan_errors": [_vp, ctypes.POINTER(ctypes.c_uint64)],
     "precode_solve_varlen": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "precode_solve_varlen_static": [ctypes.POINTER(Desc), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    _vp, _vp, _vp],
 }
 
 
@@ -113,6 +115,17 @@ def precode_solve_host(plan, M, K, B, H, t, t_stride, step, lam, W, obj, resid, 
 def precode_solve_varlen(plan, B, tbl, H, t, step, lam, W, obj, resid, flags, stream):
     check(LIB.precode_solve_varlen(plan, B, ptr(tbl), ptr(H), ptr(t), ptr(step), ptr(lam), ptr(W),
                                    ptr(obj), ptr(resid), ptr(flags), stream), "precode_solve_varlen")
+
+
+def precode_solve_varlen_static(mode, T, shapes, B, tbl, H, t, step, lam, W, obj, resid, flags,
+                                stream, cond_threshold: float = 0.0, flags_desc: int = 0,
+                                device: int = 0):
+    """Uneven batch without a plan; the library's fixed scratch array is used."""
+    arr = (Shape * len(shapes))(*[Shape(int(m), int(k)) for (m, k) in shapes])
+    d = Desc(mode, T, len(shapes), arr, 0, cond_threshold, flags_desc, device, None)
+    check(LIB.precode_solve_varlen_static(ctypes.byref(d), B, ptr(tbl), ptr(H), ptr(t), ptr(step),
+                                          ptr(lam), ptr(W), ptr(obj), ptr(resid), ptr(flags),
+                                          stream), "precode_solve_varlen_static")
 
 
 def precode_plan_errors(plan) -> int:
