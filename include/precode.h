@@ -162,6 +162,22 @@ precode_status_t precode_solve_varlen(precode_plan_t plan, int64_t B, const prec
                                       const float* lam, void* W, float* obj, float* resid,
                                       int32_t* flags, precode_stream_t stream);
 
+/* Forward + adjoint through the T layers of a uniform batch (Sec. V: the
+ * per-layer parameters are learned by backpropagating the unsupervised cost).
+ * Loss = mean_b ( a ||W_T||_{2,1} + ||H W_T^T - S||_F^2 ); writes the DEVICE
+ * scalars loss[1], dstep[T] = dLoss/dstep (eta for PGD, mu for PROJ) and, for
+ * PGD, dlam[T] = dLoss/dlam.  Parameters at or below zero (clamped to 0 in the
+ * layers) get gradient 0.  The forward keeps W every ceil(sqrt(T)) layers in
+ * plan workspace (allocated on first use, max_instances sized) and the reverse
+ * pass recomputes the layer inputs from them; per-instance partial gradients are
+ * averaged in FP64 in a fixed order (bitwise reproducible).  flags [B] optional.
+ * EINVAL: B outside [1, max_instances], NULL loss/dstep, PGD without lam/dlam. */
+precode_status_t precode_train_step(precode_plan_t plan, int32_t M, int32_t K, int64_t B,
+                                    const void* H, const float* t, int64_t t_stride,
+                                    const float* step, const float* lam, float a, float* loss,
+                                    float* dstep, float* dlam, int32_t* flags,
+                                    precode_stream_t stream);
+
 /* Uneven-batch solve that allocates no device memory (the paper has no
  * counterpart: this is a deployment variant of precode_solve_varlen).  For
  * callers that may not call cudaMalloc on their processing path, such as a

@@ -48,6 +48,8 @@ _SIGS = {
     "precode_solve_host": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_plan_errors": [_vp, ctypes.POINTER(ctypes.c_uint64)],
     "precode_solve_varlen": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "precode_train_step": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_float, _vp,
+                           _vp, _vp, _vp, _vp],
     "precode_solve_varlen_static": [ctypes.POINTER(Desc), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                     _vp, _vp, _vp],
 }
@@ -126,6 +128,13 @@ def precode_solve_varlen_static(mode, T, shapes, B, tbl, H, t, step, lam, W, obj
     check(LIB.precode_solve_varlen_static(ctypes.byref(d), B, ptr(tbl), ptr(H), ptr(t), ptr(step),
                                           ptr(lam), ptr(W), ptr(obj), ptr(resid), ptr(flags),
                                           stream), "precode_solve_varlen_static")
+
+
+def precode_train_step(plan, M, K, B, H, t, t_stride, step, lam, a, loss, dstep, dlam, flags,
+                       stream):
+    check(LIB.precode_train_step(plan, M, K, B, ptr(H), ptr(t), t_stride, ptr(step), ptr(lam),
+                                 float(a), ptr(loss), ptr(dstep), ptr(dlam), ptr(flags), stream),
+          "precode_train_step")
 
 
 def precode_plan_errors(plan) -> int:

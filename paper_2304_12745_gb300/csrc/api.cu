@@ -151,6 +151,8 @@ static void plan_free(precode_plan_t p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   cudaFree(p->d_index);
   cudaFree(p->d_count);
+  cudaFree(p->d_cp);
+  cudaFree(p->d_part);
   if (p->d_err) cudaFree(p->d_err);
   for (int i = 0; i < precode_plan_s::kPipe; ++i) {
     if (p->hstream[i]) cudaStreamDestroy(p->hstream[i]);

@@ -56,6 +56,11 @@ struct precode_plan_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<cudaGraphNode_t> graph_nodes;  // bucketize, then one solve node per bucket
+  // training: checkpoints and per-instance loss / gradient partials
+  float2* d_cp = nullptr;
+  size_t cp_bytes = 0;
+  float* d_part = nullptr;
+  size_t part_bytes = 0;
 
   int64_t max_instances = 0;
   float cond_thr = 1e3f;

@@ -23,7 +23,20 @@ struct Variant {
   int groups;    // instances resident per block
 };
 
+struct TrainVariant {
+  int mode;
+  int KB, MB;
+  bool exact;
+  const void* fn;
+  int smem;
+  int threads;
+  int groups;
+};
+
 void register_solve_pgd(std::vector<Variant>& v);
+void register_train_pgd(std::vector<TrainVariant>& v);
+void register_train_proj(std::vector<TrainVariant>& v);
+const std::vector<TrainVariant>& train_variants();
 void register_solve_proj(std::vector<Variant>& v);
 const std::vector<Variant>& variants();
 

@@ -1,0 +1,147 @@
+// precode_train_step: forward + adjoint through the T layers of a uniform batch,
+// then a deterministic FP64 batch mean of the per-instance loss and gradients.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "api_internal.h"
+#include "train.cuh"
+
+namespace precode {
+
+const std::vector<TrainVariant>& train_variants() {
+  static std::vector<TrainVariant> v = [] {
+    std::vector<TrainVariant> r;
+    register_train_pgd(r);
+    register_train_proj(r);
+    return r;
+  }();
+  return v;
+}
+
+namespace {
+
+// out[j] = scale * sum_b part[b][j] for j < P, summed in FP64 in a fixed order
+// (thread i takes rows i, i + blockDim, ...; then a fixed tree), one block per j.
+__global__ void batch_mean_kernel(const float* __restrict__ part, int64_t B, int P, double scale,
+                                  float* __restrict__ out) {
+  __shared__ double buf[256];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) s += (double)part[b * P + j];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int span = blockDim.x / 2; span > 0; span >>= 1) {
+    if ((int)threadIdx.x < span) buf[threadIdx.x] += buf[threadIdx.x + span];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = (float)(buf[0] * scale);
+}
+
+
+const TrainVariant* pick_train(int mode, int M, int K) {
+  const TrainVariant* best = nullptr;
+  for (const auto& v : train_variants())
+    if (v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
+  for (const auto& v : train_variants()) {
+    if (v.mode != mode || v.exact || v.KB < K || v.MB < M) continue;
+    if (!best || v.KB * v.MB < best->KB * best->MB) best = &v;
+  }
+  return best;
+}
+
+int train_occupancy(const TrainVariant& v) {
+  if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem) !=
+      cudaSuccess)
+    return 0;
+  cudaFuncSetAttribute(v.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v.fn, v.threads, v.smem) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+}  // namespace
+
+}  // namespace precode
+
+using namespace precode;
+
+extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int32_t K, int64_t B,
+                                               const void* H, const float* t, int64_t t_stride,
+                                               const float* step, const float* lam, float a,
+                                               float* loss, float* dstep, float* dlam,
+                                               int32_t* flags, precode_stream_t stream) {
+  if (!p) return fail(PRECODE_EINVAL, "precode_train_step: NULL plan");
+  if (B < 1 || B > p->max_instances)
+    return fail(PRECODE_EINVAL, "precode_train_step: B outside [1, max_instances]");
+  if (!shape_ok(p->mode, M, K)) return fail(PRECODE_EINVAL, "precode_train_step: bad shape");
+  if (!H || !t || !step || !loss || !dstep)
+    return fail(PRECODE_EINVAL, "precode_train_step: NULL buffer");
+  if (p->mode == PRECODE_LAYER_PGD && (!lam || !dlam))
+    return fail(PRECODE_EINVAL, "precode_train_step: lam and dlam required for the paper layer");
+  if ((uintptr_t)H & 15) return fail(PRECODE_EINVAL, "precode_train_step: H must be 16-byte aligned");
+  if (t_stride != 0 && t_stride < K) return fail(PRECODE_EINVAL, "precode_train_step: t_stride < K");
+  const TrainVariant* v = pick_train(p->mode, M, K);
+  if (!v) return fail(PRECODE_EINVAL, "precode_train_step: no train kernel holds the shape");
+  std::lock_guard<std::mutex> lk(p->mu);
+  DeviceGuard g(p->device);
+  const int T = p->T;
+  const int cpe = (int)std::ceil(std::sqrt((double)T));
+  const int ncp = (T + cpe - 1) / cpe;
+  const size_t cp_need = (size_t)p->max_instances * ncp * v->KB * v->MB * sizeof(float2);
+  const size_t part_need = (size_t)p->max_instances * (1 + 2 * T) * sizeof(float);
+  if (cp_need > p->cp_bytes) {
+    cudaFree(p->d_cp);
+    p->d_cp = nullptr;
+    p->cp_bytes = 0;
+    if (cudaMalloc(&p->d_cp, cp_need) != cudaSuccess)
+      return fail(PRECODE_ENOMEM, "precode_train_step: checkpoint workspace");
+    p->cp_bytes = cp_need;
+  }
+  if (part_need > p->part_bytes) {
+    cudaFree(p->d_part);
+    p->d_part = nullptr;
+    p->part_bytes = 0;
+    if (cudaMalloc(&p->d_part, part_need) != cudaSuccess)
+      return fail(PRECODE_ENOMEM, "precode_train_step: gradient workspace");
+    p->part_bytes = part_need;
+  }
+  const int occ = train_occupancy(*v);
+  if (occ <= 0) return fail(PRECODE_ECUDA, "precode_train_step: kernel cannot run on this device");
+  TrainArgs A{};
+  A.s.H = static_cast<const float2*>(H);
+  A.s.t = t;
+  A.s.t_stride = t_stride;
+  A.s.step = step;
+  A.s.lam = lam ? lam : step;
+  A.s.flags = flags;
+  A.s.B = B;
+  A.s.K = K;
+  A.s.M = M;
+  A.s.T = T;
+  A.s.cond_thr = p->cond_thr;
+  A.s.opts = (p->flags & PRECODE_PLAN_STEP_NORMALISED) ? OPT_STEP_NORMALISED : 0u;
+  A.s.err = p->d_err;
+  A.a = a;
+  A.cp = p->d_cp;
+  A.cp_every = cpe;
+  A.ncp = ncp;
+  A.part = p->d_part;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t grid = std::min<int64_t>((int64_t)occ * p->num_sms, (B + v->groups - 1) / v->groups);
+  void* args[] = {&A};
+  cudaError_t e = cudaLaunchKernel(v->fn, dim3((unsigned)grid), dim3(v->threads), args,
+                                   (size_t)v->smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "precode_train_step: train kernel launch");
+  const int PW = 1 + 2 * T;
+  // loss (column 0) and d step (columns 1..T) into loss / dstep; d lam separately
+  batch_mean_kernel<<<1, 256, 0, s>>>(p->d_part, B, PW, 1.0 / (double)B, loss);
+  batch_mean_kernel<<<T, 256, 0, s>>>(p->d_part + 1, B, PW, 1.0 / (double)B, dstep);
+  if (dlam) batch_mean_kernel<<<T, 256, 0, s>>>(p->d_part + 1 + T, B, PW, 1.0 / (double)B, dlam);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "precode_train_step: batch reduction launch");
+  return PRECODE_OK;
+}

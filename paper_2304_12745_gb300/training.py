@@ -1,0 +1,114 @@
+"""Learning the per-layer parameters (Sec. V): autograd bridge and Adam trainer.
+
+``PrecodeLoss`` is a ``torch.autograd.Function`` whose forward calls the
+library's ``precode_train_step`` (forward + adjoint kernels in one go) and keeps
+the parameter gradients for ``backward``.  ``UnfoldedTrainer`` runs Adam on the
+per-layer parameters over batches of synthetic channels and applies the paper's
+parameter projections after every step:
+
+* paper layer:     lambda <- max(0, lambda), eta <- min(max(eta, 1/(2 L~)), 1/L~),
+                   L~ = (sqrt K + sqrt M)^2 (Marchenko-Pastur edge);
+* projected layer: mu <- max(0, mu).
+
+The unsupervised cost is a ||W_T||_{2,1} + ||H W_T^T - S||_F^2 averaged over the
+batch (a = lambda in the paper's cost; the PA-consumption weight for the
+projected layer).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import capi, channels
+from .precoder import Plan, _stream_handle
+
+
+class PrecodeLoss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, step, lam, plan, H, t, a):
+        B, K, M = H.shape
+        dev = H.device
+        loss = torch.empty(1, device=dev)
+        dstep = torch.empty_like(step)
+        dlam = torch.empty_like(step) if lam is not None else None
+        t_stride = 0 if t.dim() == 1 else K
+        capi.precode_train_step(plan.handle, M, K, B, H, t, t_stride, step.detach().contiguous(),
+                                None if lam is None else lam.detach().contiguous(), a, loss,
+                                dstep, dlam, None, _stream_handle(None))
+        ctx.save_for_backward(dstep, dlam if dlam is not None else dstep)
+        ctx.has_lam = lam is not None
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        dstep, dlam = ctx.saved_tensors
+        return g * dstep, (g * dlam if ctx.has_lam else None), None, None, None, None
+
+
+def mp_bound(K: int, M: int) -> float:
+    """L~ = (sqrt K + sqrt M)^2."""
+    return (math.sqrt(K) + math.sqrt(M)) ** 2
+
+
+class UnfoldedTrainer:
+    """Adam over the per-layer parameters of one layer map on one (M, K)."""
+
+    def __init__(self, mode: int, T: int, K: int, M: int, batch: int, *, a: float,
+                 lr: float = 1e-3, init_step=None, init_lam=None, device: str = "cuda",
+                 step_normalised: bool = False):
+        self.mode, self.T, self.K, self.M, self.batch, self.a = mode, T, K, M, batch, a
+        self.plan = Plan(mode, T, [(M, K)], batch, step_normalised=step_normalised)
+        L = mp_bound(K, M)
+        if init_step is None:
+            init_step = [1.0 / L] * T if mode == capi.LAYER_PGD else [0.05] * T
+        self.step = torch.nn.Parameter(torch.tensor(init_step, dtype=torch.float32, device=device))
+        params = [self.step]
+        self.lam = None
+        if mode == capi.LAYER_PGD:
+            init_lam = [1.0 / 15] * T if init_lam is None else init_lam
+            self.lam = torch.nn.Parameter(torch.tensor(init_lam, dtype=torch.float32,
+                                                       device=device))
+            params.append(self.lam)
+        self.opt = torch.optim.Adam(params, lr=lr)
+        self.steps_done = 0
+
+    def project(self):
+        """Parameter projections after each optimiser step (Sec. V end)."""
+        with torch.no_grad():
+            if self.mode == capi.LAYER_PGD:
+                L = mp_bound(self.K, self.M)
+                self.lam.clamp_(min=0.0)
+                self.step.clamp_(min=1.0 / (2 * L), max=1.0 / L)
+            else:
+                self.step.clamp_(min=0.0)
+
+    def loss(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+        return PrecodeLoss.apply(self.step, self.lam, self.plan, H, t, self.a)
+
+    def train_step(self, H: torch.Tensor, t: torch.Tensor) -> float:
+        self.opt.zero_grad(set_to_none=True)
+        loss = self.loss(H, t)
+        loss.backward()
+        self.opt.step()
+        self.project()
+        self.steps_done += 1
+        return float(loss.detach())
+
+    def make_batch(self, index: int, seed: int, family: str = "rayleigh"):
+        """Channels of batch `index` (deterministic in (seed, index))."""
+        H = channels.channels(family, self.batch, self.K, self.M, seed=seed * 1000003 + index)
+        return torch.from_numpy(H).to(self.step.device)
+
+    def state_dict(self):
+        return {"step": self.step.detach().clone(),
+                "lam": None if self.lam is None else self.lam.detach().clone(),
+                "opt": self.opt.state_dict(), "steps_done": self.steps_done}
+
+    def load_state_dict(self, s):
+        with torch.no_grad():
+            self.step.copy_(s["step"])
+            if self.lam is not None:
+                self.lam.copy_(s["lam"])
+        self.opt.load_state_dict(s["opt"])
+        self.steps_done = s["steps_done"]

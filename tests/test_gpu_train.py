@@ -1,0 +1,169 @@
+"""Adjoint (training) kernels on the GPU against the FP64 oracle's reverse mode.
+
+The oracle's gradients are themselves pinned to central finite differences
+(tests/test_oracle_pins.py).  Instances with a column within reach of a shrink
+kink (|r - tau| small on some layer) are left out, as there the FP32 and FP64
+forward passes may sit on different sides of the kink.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2304_12745_gb300 import channels as ch
+
+pytestmark = pytest.mark.gpu
+
+
+def _far_from_kinks_proj(orc, H, t, mu, margin):
+    keep = []
+    for b in range(len(H)):
+        _, _, tr = orc.ufproj_forward(H[b], t[b], mu, trace=True)
+        d = min(np.abs(np.linalg.norm(tr[l], axis=0) - mu[l]).min() for l in range(len(mu)))
+        keep.append(d > margin)
+    return np.array(keep)
+
+
+def _far_from_kinks_pgd(orc, H, t, eta, lam, margin):
+    keep = []
+    for b in range(len(H)):
+        _, tr = orc.ufpgd_forward(H[b], t[b], eta, lam, trace=True)
+        d = np.inf
+        for l in range(len(eta)):
+            V = tr[l] - eta[l] * ((tr[l] @ H[b].T - np.diag(t[b])) @ H[b].conj())
+            d = min(d, np.abs(np.linalg.norm(V, axis=0) - lam[l] * eta[l]).min())
+        keep.append(d > margin)
+    return np.array(keep)
+
+
+def _train_step(plan, H, t, step, lam, a):
+    from paper_2304_12745_gb300 import capi
+    B, K, M = H.shape
+    Hd = torch.from_numpy(H.astype(np.complex64)).cuda()
+    td = torch.from_numpy(np.ascontiguousarray(t, np.float32)).cuda()
+    sd = torch.tensor(step, dtype=torch.float32, device="cuda")
+    ld = torch.tensor(lam, dtype=torch.float32, device="cuda") if lam is not None else None
+    loss = torch.empty(1, device="cuda")
+    ds = torch.empty(len(step), device="cuda")
+    dl = torch.empty(len(step), device="cuda") if lam is not None else None
+    capi.precode_train_step(plan.handle, M, K, B, Hd, td, K, sd, ld, a, loss, ds, dl, None,
+                            torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return (float(loss.item()), ds.cpu().numpy().astype(np.float64),
+            None if dl is None else dl.cpu().numpy().astype(np.float64))
+
+
+@pytest.mark.parametrize("K,M,T", [(4, 32, 6), (8, 64, 10)])
+def test_projected_gradient_matches_oracle(orc, K, M, T):
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+    B0 = 64
+    H = ch.rayleigh(B0, K, M, seed=40 + K).astype(np.complex128)
+    H = H.astype(np.complex64).astype(np.complex128)  # the GPU sees complex64
+    t = np.ones((B0, K))
+    mu = ch.uniform_steps(T, 0.02, 0.08, seed=41).astype(np.float32).astype(np.float64)
+    keep = _far_from_kinks_proj(orc, H, t, mu, 2e-5)
+    H, t = H[keep], t[keep]
+    B = len(H)
+    assert B >= 16
+    a = 1.0
+    ref = [orc.ufproj_grad(H[b], t[b], mu, a) for b in range(B)]
+    loss_o = np.mean([r[0] for r in ref])
+    g_o = np.mean([r[1] for r in ref], axis=0)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B)
+    loss, g, _ = _train_step(plan, H, t, mu, None, a)
+    plan.close()
+    assert loss == pytest.approx(loss_o, rel=1e-5)
+    assert np.allclose(g, g_o, rtol=1e-3, atol=1e-3 * np.abs(g_o).max()), (g, g_o)
+
+
+def test_paper_layer_gradient_matches_oracle(orc):
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+    K, M, T, B0 = 4, 32, 5, 64
+    H = ch.rayleigh(B0, K, M, seed=50).astype(np.complex128)
+    t = np.ones((B0, K))
+    eta0 = ch.paper_eta(K, M)
+    rs = np.random.default_rng(51)
+    eta = (eta0 * rs.uniform(0.5, 1.0, T)).astype(np.float32).astype(np.float64)
+    lam = rs.uniform(0.5, 3.0, T).astype(np.float32).astype(np.float64)
+    keep = _far_from_kinks_pgd(orc, H, t, eta, lam, 2e-5)
+    H, t = H[keep], t[keep]
+    B = len(H)
+    assert B >= 16
+    a = 1 / 15
+    ref = [orc.ufpgd_grad(H[b], t[b], eta, lam, a) for b in range(B)]
+    loss_o = np.mean([r[0] for r in ref])
+    ge_o = np.mean([r[1] for r in ref], axis=0)
+    gl_o = np.mean([r[2] for r in ref], axis=0)
+    plan = Plan(capi.LAYER_PGD, T, [(M, K)], B)
+    loss, ge, gl = _train_step(plan, H, t, eta, lam, a)
+    plan.close()
+    assert loss == pytest.approx(loss_o, rel=1e-5)
+    assert np.allclose(ge, ge_o, rtol=1e-3, atol=1e-3 * np.abs(ge_o).max()), (ge, ge_o)
+    assert np.allclose(gl, gl_o, rtol=1e-3, atol=1e-3 * np.abs(gl_o).max()), (gl, gl_o)
+
+
+def test_gradient_matches_central_differences_of_the_gpu_loss():
+    """Central differences (h = 1e-3) of the GPU's own FP32 batch loss."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+    K, M, T, B = 8, 64, 10, 2048
+    H = ch.rayleigh(B, K, M, seed=60)
+    t = np.ones((B, K), np.float32)
+    mu = ch.uniform_steps(T, 0.02, 0.08, seed=61).astype(np.float64)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B)
+    _, g, _ = _train_step(plan, H, t, mu, None, 1.0)
+    h = 1e-3
+    for l in (0, 4, 9):
+        mp, mm = mu.copy(), mu.copy()
+        mp[l] += h
+        mm[l] -= h
+        fd = (_train_step(plan, H, t, mp, None, 1.0)[0] - _train_step(plan, H, t, mm, None, 1.0)[0]) / (2 * h)
+        assert fd == pytest.approx(g[l], rel=2e-2, abs=2e-2 * np.abs(g).max()), (l, fd, g[l])
+    plan.close()
+
+
+def test_train_step_deterministic_and_trainer_resume():
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.training import UnfoldedTrainer
+    K, M, T, Bt = 8, 64, 10, 512
+    tr = UnfoldedTrainer(capi.LAYER_PROJ, T, K, M, Bt, a=1.0, lr=2e-3)
+    t = torch.ones(K, device="cuda")
+    H0 = tr.make_batch(0, seed=4)
+    l1 = tr.loss(H0, t)
+    l2 = tr.loss(H0, t)
+    assert float(l1) == float(l2)
+    losses = [tr.train_step(tr.make_batch(i, seed=4), t) for i in range(8)]
+    ref = tr.step.detach().clone()
+    # resume: 4 steps, save, new trainer, load, 4 more
+    a = UnfoldedTrainer(capi.LAYER_PROJ, T, K, M, Bt, a=1.0, lr=2e-3)
+    for i in range(4):
+        a.train_step(a.make_batch(i, seed=4), t)
+    state = a.state_dict()
+    b = UnfoldedTrainer(capi.LAYER_PROJ, T, K, M, Bt, a=1.0, lr=2e-3)
+    b.load_state_dict(state)
+    for i in range(4, 8):
+        b.train_step(b.make_batch(i, seed=4), t)
+    assert torch.equal(b.step.detach(), ref)
+    assert np.all(np.isfinite(losses))
+
+
+def test_paper_layer_training_reduces_the_cost():
+    """Adam on eta, lambda with the paper's projections lowers the unsupervised cost."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.training import UnfoldedTrainer, mp_bound
+    K, M, T, Bt = 8, 64, 10, 1024
+    tr = UnfoldedTrainer(capi.LAYER_PGD, T, K, M, Bt, a=1 / 15, lr=1e-3)
+    t = torch.full((K,), math.sqrt(10.0), device="cuda")
+    Hv = tr.make_batch(999, seed=5)
+    before = float(tr.loss(Hv, t))
+    for i in range(40):
+        tr.train_step(tr.make_batch(i, seed=5), t)
+    after = float(tr.loss(Hv, t))
+    assert after < before
+    L = mp_bound(K, M)
+    assert torch.all(tr.step >= 1 / (2 * L) - 1e-9) and torch.all(tr.step <= 1 / L + 1e-9)
+    assert torch.all(tr.lam >= 0)
