@@ -204,6 +204,84 @@ precode_status_t precode_solve_varlen_static(const precode_desc_t* desc, int64_t
                                              void* W, float* obj, float* resid, int32_t* flags,
                                              precode_stream_t stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of precoding jobs (a job = n_sc independent subcarrier
+ * channels of one (M, K)).  precode_serve_submit queues a job and returns a
+ * ticket at once.  A dispatcher thread admits queued jobs in arrival order into
+ * free stream slots while their buffers fit in the server's device arena
+ * (admission by free device memory); the jobs admitted together run as one
+ * bucketed uneven-batch launch on that slot, overlapping on the device with the
+ * other slots' launches.  Jobs arriving while launches run are admitted as soon
+ * as a slot and memory free up.  A job's results do not depend on which jobs
+ * shared its launch.  Resident channels keep H on the device across jobs.
+ * Host buffers of a job must stay valid until its result is polled / waited;
+ * pinned host memory lets the copies overlap with other work. */
+typedef struct precode_server_s* precode_server_t;
+
+typedef struct {
+  int32_t mode;                  /* precode_layer_t */
+  int32_t T;
+  const float* step;             /* HOST [T], copied at create */
+  const float* lam;              /* HOST [T] (PGD) or NULL */
+  int32_t n_shapes;              /* buckets the server prepares (any job shape a bucket holds runs) */
+  const precode_shape_t* shapes;
+  int32_t n_slots;               /* launches in flight (one stream + plan each); <= 0 -> 4 */
+  int64_t max_batch_instances;   /* instances per launch (slot capacity); <= 0 -> 16384 */
+  int64_t device_mem_budget;     /* bytes of the job arena; <= 0 -> half the free memory */
+  int32_t device;
+  double cond_threshold;         /* as in precode_desc_t */
+  uint32_t flags;                /* PRECODE_PLAN_* for the slot plans */
+} precode_serve_desc_t;
+
+typedef struct {
+  int32_t M, K, n_sc;
+  const void* H;      /* HOST complex64 [n_sc][K][M]; ignored when channel != 0 */
+  const float* t;     /* HOST [n_sc][K], or [K] when t_shared */
+  int32_t t_shared;
+  void* W_out;        /* HOST complex64 [n_sc][K][M] */
+  float* obj_out;     /* HOST [n_sc] or NULL */
+  float* resid_out;   /* HOST [n_sc] or NULL */
+  int32_t* flags_out; /* HOST [n_sc] or NULL */
+  uint64_t channel;   /* resident channel (precode_serve_channel_create) or 0 */
+} precode_job_t;
+
+typedef struct {
+  precode_status_t status;  /* OK, or the error that hit the job's launch */
+  double submit_us, start_us, done_us, latency_us;  /* host steady clock, microseconds */
+} precode_result_t;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, launches;
+  double p50_us, p99_us, max_us, mean_us;  /* submit -> results in host memory */
+  double precoders_per_s;                  /* completed instances / (last done - first submit) */
+  int64_t instances_done;
+  int64_t bytes_in_use, bytes_budget;
+  int32_t slots_busy, queued;
+} precode_serve_stats_t;
+
+/* Create the server (arena, one plan + stream per slot, dispatcher and
+ * completion threads).  EINVAL bad descriptor, ENOMEM arena / buffers. */
+precode_status_t precode_serve_create(const precode_serve_desc_t* desc, precode_server_t* out);
+/* Queue a job; returns immediately.  EBUSY if the job can never fit the arena
+ * or a slot; ENOTFOUND unknown channel; EINVAL bad job. */
+precode_status_t precode_serve_submit(precode_server_t s, const precode_job_t* job,
+                                      uint64_t* ticket);
+/* PENDING while running; OK fills the result and retires the ticket. */
+precode_status_t precode_serve_poll(precode_server_t s, uint64_t ticket, precode_result_t* r);
+/* Block until done (timeout_us < 0: no limit); ETIMEDOUT if the limit passes. */
+precode_status_t precode_serve_wait(precode_server_t s, uint64_t ticket, int64_t timeout_us,
+                                    precode_result_t* r);
+precode_status_t precode_serve_stats(precode_server_t s, precode_serve_stats_t* st);
+precode_status_t precode_serve_reset_stats(precode_server_t s);
+/* Copy n_sc channels [n_sc][K][M] (HOST) to the device once; jobs that name the
+ * handle skip the host->device copy of H. */
+precode_status_t precode_serve_channel_create(precode_server_t s, int32_t M, int32_t K,
+                                              int32_t n_sc, const void* H, uint64_t* handle);
+/* Waits until no unfinished job uses the channel, then frees it. */
+precode_status_t precode_serve_channel_destroy(precode_server_t s, uint64_t handle);
+/* Finishes queued and running jobs, then frees everything. */
+precode_status_t precode_serve_destroy(precode_server_t s);
+
 /* Number of device-side wait timeouts recorded by the plan's kernels since the
  * plan was created (synchronises the plan's device).  0 in normal operation. */
 precode_status_t precode_plan_errors(precode_plan_t plan, uint64_t* count);

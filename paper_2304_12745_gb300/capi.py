@@ -38,6 +38,39 @@ class Desc(ctypes.Structure):
                 ("device", ctypes.c_int32), ("tune_cache", ctypes.c_char_p)]
 
 
+class ServeDesc(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("step", ctypes.c_void_p), ("lam", ctypes.c_void_p),
+                ("n_shapes", ctypes.c_int32), ("shapes", ctypes.POINTER(Shape)),
+                ("n_slots", ctypes.c_int32), ("max_batch_instances", ctypes.c_int64),
+                ("device_mem_budget", ctypes.c_int64), ("device", ctypes.c_int32),
+                ("cond_threshold", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("K", ctypes.c_int32), ("n_sc", ctypes.c_int32),
+                ("H", ctypes.c_void_p), ("t", ctypes.c_void_p), ("t_shared", ctypes.c_int32),
+                ("W_out", ctypes.c_void_p), ("obj_out", ctypes.c_void_p),
+                ("resid_out", ctypes.c_void_p), ("flags_out", ctypes.c_void_p),
+                ("channel", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("submit_us", ctypes.c_double),
+                ("start_us", ctypes.c_double), ("done_us", ctypes.c_double),
+                ("latency_us", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("precoders_per_s", ctypes.c_double), ("instances_done", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("bytes_budget", ctypes.c_int64),
+                ("slots_busy", ctypes.c_int32), ("queued", ctypes.c_int32)]
+
+
 _vp = ctypes.c_void_p
 _i32, _i64, _u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
 
@@ -50,6 +83,15 @@ _SIGS = {
     "precode_solve_varlen": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_train_step": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_float, _vp,
                            _vp, _vp, _vp, _vp],
+    "precode_serve_create": [ctypes.POINTER(ServeDesc), ctypes.POINTER(_vp)],
+    "precode_serve_submit": [_vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)],
+    "precode_serve_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(Result)],
+    "precode_serve_wait": [_vp, ctypes.c_uint64, _i64, ctypes.POINTER(Result)],
+    "precode_serve_stats": [_vp, ctypes.POINTER(ServeStats)],
+    "precode_serve_reset_stats": [_vp],
+    "precode_serve_channel_create": [_vp, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_uint64)],
+    "precode_serve_channel_destroy": [_vp, ctypes.c_uint64],
+    "precode_serve_destroy": [_vp],
     "precode_solve_varlen_static": [ctypes.POINTER(Desc), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                     _vp, _vp, _vp],
 }
@@ -135,6 +177,63 @@ def precode_train_step(plan, M, K, B, H, t, t_stride, step, lam, a, loss, dstep,
     check(LIB.precode_train_step(plan, M, K, B, ptr(H), ptr(t), t_stride, ptr(step), ptr(lam),
                                  float(a), ptr(loss), ptr(dstep), ptr(dlam), ptr(flags), stream),
           "precode_train_step")
+
+
+def precode_serve_create(mode, T, step, lam, shapes, n_slots=4, max_batch_instances=16384,
+                         device_mem_budget=0, device=0, cond_threshold=0.0, flags=0) -> int:
+    arr = (Shape * len(shapes))(*[Shape(int(m), int(k)) for (m, k) in shapes])
+    d = ServeDesc(mode, T, ptr(step), ptr(lam), len(shapes), arr, n_slots, max_batch_instances,
+                  device_mem_budget, device, cond_threshold, flags)
+    h = _vp()
+    check(LIB.precode_serve_create(ctypes.byref(d), ctypes.byref(h)), "precode_serve_create")
+    return h.value
+
+
+def precode_serve_submit(server, job: Job) -> int:
+    tk = ctypes.c_uint64(0)
+    check(LIB.precode_serve_submit(server, ctypes.byref(job), ctypes.byref(tk)),
+          "precode_serve_submit")
+    return tk.value
+
+
+def precode_serve_poll(server, ticket):
+    r = Result()
+    st = LIB.precode_serve_poll(server, ticket, ctypes.byref(r))
+    if st == PENDING:
+        return None
+    check(st, "precode_serve_poll")
+    return r
+
+
+def precode_serve_wait(server, ticket, timeout_us=-1):
+    r = Result()
+    check(LIB.precode_serve_wait(server, ticket, timeout_us, ctypes.byref(r)), "precode_serve_wait")
+    return r
+
+
+def precode_serve_stats(server) -> ServeStats:
+    s = ServeStats()
+    check(LIB.precode_serve_stats(server, ctypes.byref(s)), "precode_serve_stats")
+    return s
+
+
+def precode_serve_reset_stats(server):
+    check(LIB.precode_serve_reset_stats(server), "precode_serve_reset_stats")
+
+
+def precode_serve_channel_create(server, M, K, n_sc, H) -> int:
+    h = ctypes.c_uint64(0)
+    check(LIB.precode_serve_channel_create(server, M, K, n_sc, ptr(H), ctypes.byref(h)),
+          "precode_serve_channel_create")
+    return h.value
+
+
+def precode_serve_channel_destroy(server, handle):
+    check(LIB.precode_serve_channel_destroy(server, handle), "precode_serve_channel_destroy")
+
+
+def precode_serve_destroy(server):
+    check(LIB.precode_serve_destroy(server), "precode_serve_destroy")
 
 
 def precode_plan_errors(plan) -> int:

@@ -1,0 +1,133 @@
+"""Python handle on the library's continuous-batching server (argument marshalling).
+
+``Server.submit`` takes numpy arrays (pinned copies are made once per job so the
+host<->device copies can overlap); results land in the job's output arrays.
+``poisson_load`` drives a server with Poisson arrivals of random jobs and
+returns the server's latency statistics.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import capi, channels
+
+
+class JobHandle:
+    def __init__(self, server, ticket, arrays):
+        self.server, self.ticket, self.arrays = server, ticket, arrays
+        self.result = None
+
+    def wait(self, timeout_us: int = -1):
+        if self.result is None:
+            self.result = capi.precode_serve_wait(self.server.handle, self.ticket, timeout_us)
+        return self.result
+
+    @property
+    def W(self):
+        return self.arrays["W"]
+
+    @property
+    def obj(self):
+        return self.arrays["obj"]
+
+    @property
+    def flags(self):
+        return self.arrays["flags"]
+
+
+class Server:
+    def __init__(self, mode: int, step, lam=None, shapes=((64, 8),), *, n_slots: int = 4,
+                 max_batch_instances: int = 16384, device_mem_budget: int = 0, device: int = 0,
+                 cond_threshold: float = 0.0, flags: int = 0):
+        self.step = np.ascontiguousarray(step, dtype=np.float32)
+        self.lam = None if lam is None else np.ascontiguousarray(lam, dtype=np.float32)
+        self.T = len(self.step)
+        self.handle = capi.precode_serve_create(mode, self.T, self.step, self.lam, list(shapes),
+                                                n_slots, max_batch_instances, device_mem_budget,
+                                                device, cond_threshold, flags)
+
+    def submit(self, H: np.ndarray | None, t: np.ndarray, *, channel: int = 0, M=None, K=None,
+               n_sc=None) -> JobHandle:
+        if H is not None:
+            n_sc, K, M = H.shape
+            H = np.ascontiguousarray(H, dtype=np.complex64)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        arrays = {"H": H, "t": t, "W": np.empty((n_sc, K, M), np.complex64),
+                  "obj": np.empty(n_sc, np.float32), "resid": np.empty(n_sc, np.float32),
+                  "flags": np.empty(n_sc, np.int32)}
+        job = capi.Job(M, K, n_sc, capi.ptr(H), capi.ptr(t), 1 if t.ndim == 1 else 0,
+                       capi.ptr(arrays["W"]), capi.ptr(arrays["obj"]), capi.ptr(arrays["resid"]),
+                       capi.ptr(arrays["flags"]), channel)
+        return JobHandle(self, capi.precode_serve_submit(self.handle, job), arrays)
+
+    def channel(self, H: np.ndarray) -> int:
+        n_sc, K, M = H.shape
+        H = np.ascontiguousarray(H, dtype=np.complex64)
+        return capi.precode_serve_channel_create(self.handle, M, K, n_sc, H)
+
+    def release_channel(self, handle: int):
+        capi.precode_serve_channel_destroy(self.handle, handle)
+
+    def stats(self) -> dict:
+        s = capi.precode_serve_stats(self.handle)
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def reset_stats(self):
+        capi.precode_serve_reset_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            capi.precode_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def random_job(rng: np.random.Generator, M_choices=(64, 128, 256), K_range=(4, 32),
+               nsc_choices=(64, 128, 256, 512, 1024)):
+    M = int(rng.choice(M_choices))
+    K = int(rng.integers(K_range[0], min(K_range[1], M) + 1))
+    n_sc = int(rng.choice(nsc_choices))
+    return M, K, n_sc
+
+
+def poisson_load(server: Server, rate_per_s: float, duration_s: float, seed: int,
+                 M_choices=(64, 128, 256), K_range=(4, 32), nsc_choices=(64, 128, 256, 512, 1024),
+                 pool: int = 16) -> dict:
+    """Submit jobs with exponential inter-arrival times for `duration_s`, wait for
+    all, return the server's statistics.  Channels come from a pool of `pool`
+    pre-generated Rician jobs per shape so that generation stays off the clock."""
+    rng = np.random.default_rng(seed)
+    cache = {}
+
+    def channel_for(M, K, n_sc):
+        key = (M, K, n_sc, int(rng.integers(pool)))
+        if key not in cache:
+            cache[key] = channels.rician_ula(n_sc, K, M, seed=hash(key) & 0xFFFFFFF)
+        return cache[key]
+
+    # pre-draw the schedule and the channels
+    sched, t = [], 0.0
+    while t < duration_s:
+        t += rng.exponential(1.0 / rate_per_s)
+        M, K, n_sc = random_job(rng, M_choices, K_range, nsc_choices)
+        sched.append((t, channel_for(M, K, n_sc)))
+    server.reset_stats()
+    handles = []
+    t0 = time.perf_counter()
+    for at, H in sched:
+        while time.perf_counter() - t0 < at:
+            pass
+        handles.append(server.submit(H, np.ones(H.shape[1], np.float32)))
+    for h in handles:
+        h.wait()
+    st = server.stats()
+    st["jobs"] = len(handles)
+    st["offered_rate_per_s"] = rate_per_s
+    return st

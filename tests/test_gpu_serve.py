@@ -1,0 +1,106 @@
+"""Continuous-batching server: correctness, alone-vs-mix equality, resident channels."""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2304_12745_gb300 import channels as ch
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(32, 4), (64, 8), (128, 16), (256, 32)]
+
+
+@pytest.fixture(scope="module")
+def server():
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.serving import Server
+    mu = ch.uniform_steps(10, 0.01, 0.1, seed=2)
+    s = Server(capi.LAYER_PROJ, mu, shapes=SHAPES, n_slots=4, max_batch_instances=8192,
+               device_mem_budget=1 << 30)
+    yield s, mu
+    s.close()
+
+
+def test_jobs_match_oracle(orc, server):
+    s, mu = server
+    rng = np.random.default_rng(0)
+    jobs = []
+    for i in range(12):
+        M = int(rng.choice([64, 128, 256]))
+        K = int(rng.integers(4, 33))
+        H = ch.rician_ula(int(rng.choice([16, 64])), K, M, seed=100 + i)
+        jobs.append((H, s.submit(H, np.ones(K, np.float32))))
+    for H, h in jobs:
+        r = h.wait()
+        assert r.status == 0 and r.latency_us > 0
+        n, K, M = H.shape
+        sel = np.arange(0, n, max(1, n // 4))
+        Wo, oo, _, so = orc.batch_forward(1, H[sel].astype(np.complex128), np.ones((len(sel), K)),
+                                          mu.astype(np.float64), nthreads=8)
+        err = np.linalg.norm((h.W[sel] - Wo).reshape(len(sel), -1), axis=1) / np.linalg.norm(
+            Wo.reshape(len(sel), -1), axis=1)
+        ok = so == 0
+        assert err[ok].max() <= 1e-4
+        assert np.max(np.abs(h.obj[sel][ok] - oo[ok]) / oo[ok]) <= 1e-5
+
+
+def test_result_same_alone_and_in_the_mix(server):
+    s, mu = server
+    H = ch.rician_ula(256, 12, 128, seed=7)
+    t = np.ones(12, np.float32)
+    alone = s.submit(H, t)
+    alone.wait()
+    W_alone, obj_alone = alone.W.copy(), alone.obj.copy()
+    # now the same job among many others submitted concurrently from 4 threads
+    rng = np.random.default_rng(1)
+    others = [ch.rician_ula(int(rng.choice([64, 256, 512])), int(rng.integers(4, 33)),
+                            int(rng.choice([64, 128, 256])), seed=200 + i) for i in range(24)]
+    handles, lock = [], threading.Lock()
+
+    def worker(chunk):
+        for H2 in chunk:
+            h = s.submit(H2, np.ones(H2.shape[1], np.float32))
+            with lock:
+                handles.append(h)
+
+    threads = [threading.Thread(target=worker, args=(others[i::4],)) for i in range(4)]
+    for th in threads:
+        th.start()
+    mixed = s.submit(H, t)
+    for th in threads:
+        th.join()
+    mixed.wait()
+    for h in handles:
+        assert h.wait().status == 0
+    st = s.stats()
+    assert st["launches"] >= 2
+    assert np.array_equal(mixed.W, W_alone) and np.array_equal(mixed.obj, obj_alone)
+
+
+def test_resident_channel_matches_copied_channel(server):
+    s, mu = server
+    H = ch.rician_ula(128, 8, 64, seed=9)
+    t = np.ones(8, np.float32)
+    cid = s.channel(H)
+    a = s.submit(H, t)
+    b = s.submit(None, t, channel=cid, M=64, K=8, n_sc=128)
+    a.wait()
+    b.wait()
+    assert np.array_equal(a.W, b.W)
+    s.release_channel(cid)
+
+
+def test_poisson_load_reports_latency():
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.serving import Server, poisson_load
+    mu = ch.uniform_steps(10, 0.01, 0.1, seed=2)
+    s = Server(capi.LAYER_PROJ, mu, shapes=SHAPES, n_slots=4, max_batch_instances=16384,
+               device_mem_budget=4 << 30)
+    st = poisson_load(s, rate_per_s=500.0, duration_s=0.5, seed=3, nsc_choices=(64, 128, 256))
+    s.close()
+    assert st["completed"] == st["jobs"] > 100
+    assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"]
+    assert st["precoders_per_s"] > 0
