@@ -162,6 +162,85 @@ def cpu_baseline(H, t, mu, budget_s: float = 10.0):
                       f"layers, {nthreads} threads over contiguous ranges, {dt:.1f} s"}, first_obj
 
 
+def bench_uneven(torch, capi, Plan, inst_table):
+    """Uneven workload: 32,768 instances, (M, K) uniform over the four buckets,
+    Rician channels, T = 10, one CUDA-graph launch (bucketing + one solve per bucket)."""
+    B, T = 32768, 10
+    shapes = ch.uneven_shapes(B, seed=3)
+    sizes = shapes[:, 0].astype(np.int64) * shapes[:, 1]
+    h_off = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    t_off = np.concatenate([[0], np.cumsum(shapes[:, 1])[:-1]]).astype(np.int64)
+    # one Rician pool; instance b views its K*M values (inputs only shape the timing)
+    pool = ch.rician_ula(1, 1, int(sizes.sum()), seed=3)[0, 0]
+    Hd = torch.from_numpy(pool).cuda()
+    td = torch.ones(int(shapes[:, 1].sum()), device="cuda")
+    mu = torch.from_numpy(ch.uniform_steps(T, 0.01, 0.1, seed=2)).cuda()
+    plan = Plan(capi.LAYER_PROJ, T, [tuple(x) for x in ch.UNEVEN_SHAPES], B, graphs=True,
+                autotune=True)
+    tbl = inst_table(h_off, h_off, t_off, shapes[:, 0], shapes[:, 1]).cuda()
+    W = torch.empty_like(Hd)
+    for _ in range(3):
+        plan.solve_varlen(tbl, Hd, td, mu, W=W)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        plan.solve_varlen(tbl, Hd, td, mu, W=W)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    per = {}
+    for (M, K) in ch.UNEVEN_SHAPES:
+        per[f"{M}x{K}"] = int(((shapes[:, 0] == M) & (shapes[:, 1] == K)).sum())
+    plan.close()
+    return {"workload": "uneven: 32,768 instances, (M,K) uniform over (32,4),(64,8),(128,16),"
+                        "(256,32), Rician ULA, T=10, one CUDA graph per call",
+            "precoders_per_s": B / (ms / 1e3), "ms_per_call": ms, "instances_per_bucket": per}
+
+
+def bench_train(torch, capi):
+    """Differentiation workload: Adam over mu_1..mu_10 for 200 batches of 8,192
+    i.i.d. CN(0,1) channels C^{8x64}; loss = mean PA objective + residual penalty."""
+    from paper_2304_12745_gb300.training import UnfoldedTrainer
+    K, M, T, Bt, steps = 8, 64, 10, 8192, 200
+    tr = UnfoldedTrainer(capi.LAYER_PROJ, T, K, M, Bt, a=1.0, lr=1e-3,
+                         init_step=list(ch.fixed_workload_steps(T)))
+    t = torch.ones(K, device="cuda")
+    batches = [tr.make_batch(i % 8, seed=4) for i in range(8)]  # 8 resident batches, cycled
+    first = tr.train_step(batches[0], t)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    last = None
+    for i in range(1, steps):
+        last = tr.train_step(batches[i % 8], t)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (steps - 1)
+    mu = tr.step.detach().cpu().numpy()
+    tr.plan.close()
+    return {"workload": "train: 200 Adam steps x 8,192 instances C^{8x64}, CN(0,1), T=10, lr 1e-3",
+            "instances_per_s": Bt / (ms / 1e3), "ms_per_step": ms, "loss_first": first,
+            "loss_last": last, "mu_learned": [float(x) for x in mu]}, mu
+
+
+def bench_serve(capi, mu, duration_s: float = 2.0):
+    """Serving workload: Poisson arrivals at 2,000 jobs/s, M in {64,128,256},
+    K in {4..32}, N_sc in {64,...,1024}, Rician, T = 10 with the learned steps."""
+    from paper_2304_12745_gb300.serving import Server, poisson_load
+    s = Server(capi.LAYER_PROJ, mu, shapes=[tuple(x) for x in ch.UNEVEN_SHAPES], n_slots=6,
+               max_batch_instances=65536, device_mem_budget=24 << 30)
+    poisson_load(s, 500.0, 0.2, seed=11)  # warm-up
+    st = poisson_load(s, 2000.0, duration_s, seed=12)
+    s.close()
+    return {"workload": "serve: Poisson 2,000 jobs/s for %.1f s; M in {64,128,256}, K in {4..32}, "
+                        "N_sc in {64,128,256,512,1024}; Rician; T=10, learned mu" % duration_s,
+            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+            "precoders_per_s": st["precoders_per_s"], "jobs": st["jobs"],
+            "achieved_jobs_per_s": st["achieved_rate_per_s"], "launches": st["launches"]}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -202,6 +281,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the uneven, training and serving sub-benchmarks")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default kernel variant (no tuning launches; for profiling)")
     args = ap.parse_args()
@@ -334,9 +415,17 @@ def main():
         line["pa_gap"] = {"rel_obj_diff_gpu_vs_oracle_max": float(gap.max()),
                           "rel_obj_diff_gpu_vs_oracle_mean": float(gap.mean()),
                           "instances": n, "mean_pcg_gpu": float(np.mean(pcg))}
+    plan.close()
+    del Hd, W
+    if rank == 0 and not args.no_extras:
+        from paper_2304_12745_gb300.precoder import inst_table
+        torch.cuda.empty_cache()
+        line["uneven"] = bench_uneven(torch, capi, Plan, inst_table)
+        line["train"], mu_learned = bench_train(torch, capi)
+        torch.cuda.empty_cache()
+        line["serving"] = bench_serve(capi, mu_learned)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -89,6 +89,13 @@ class Server:
             pass
 
 
+def pinned(n: int, dtype) -> np.ndarray:
+    """Page-locked host array (lets the server's copies run asynchronously)."""
+    import torch
+    tdt = {np.complex64: torch.complex64, np.float32: torch.float32}[dtype]
+    return torch.empty(n, dtype=tdt, pin_memory=True).numpy()
+
+
 def random_job(rng: np.random.Generator, M_choices=(64, 128, 256), K_range=(4, 32),
                nsc_choices=(64, 128, 256, 512, 1024)):
     M = int(rng.choice(M_choices))
@@ -99,35 +106,52 @@ def random_job(rng: np.random.Generator, M_choices=(64, 128, 256), K_range=(4, 3
 
 def poisson_load(server: Server, rate_per_s: float, duration_s: float, seed: int,
                  M_choices=(64, 128, 256), K_range=(4, 32), nsc_choices=(64, 128, 256, 512, 1024),
-                 pool: int = 16) -> dict:
+                 ring_bytes: int = 4 << 30) -> dict:
     """Submit jobs with exponential inter-arrival times for `duration_s`, wait for
-    all, return the server's statistics.  Channels come from a pool of `pool`
-    pre-generated Rician jobs per shape so that generation stays off the clock."""
+    all, return the server's statistics.
+
+    Inputs come from one pre-generated pool of Rician channels (a job's H is the
+    first n_sc*K*M values of the pool, viewed as [n_sc][K][M]), so generation stays
+    off the clock; outputs go to slices of a host ring buffer that is reused only
+    after the job that held a slice finished."""
     rng = np.random.default_rng(seed)
-    cache = {}
-
-    def channel_for(M, K, n_sc):
-        key = (M, K, n_sc, int(rng.integers(pool)))
-        if key not in cache:
-            cache[key] = channels.rician_ula(n_sc, K, M, seed=hash(key) & 0xFFFFFFF)
-        return cache[key]
-
-    # pre-draw the schedule and the channels
+    n_max = max(nsc_choices) * K_range[1] * max(M_choices)
+    pool = pinned(n_max, np.complex64)
+    pool[:] = channels.rician_ula(1, 1, n_max, seed=seed)[0, 0]
+    ring = pinned(ring_bytes // 8, np.complex64)
+    ones = np.ones(K_range[1], np.float32)
     sched, t = [], 0.0
     while t < duration_s:
         t += rng.exponential(1.0 / rate_per_s)
-        M, K, n_sc = random_job(rng, M_choices, K_range, nsc_choices)
-        sched.append((t, channel_for(M, K, n_sc)))
+        sched.append((t,) + random_job(rng, M_choices, K_range, nsc_choices))
     server.reset_stats()
-    handles = []
+    handles, live, cursor = [], [], 0
     t0 = time.perf_counter()
-    for at, H in sched:
+    for at, M, K, n_sc in sched:
+        n = n_sc * K * M
+        if cursor + n > ring.size:
+            cursor = 0
+        # the ring slice must be free: wait for every live job overlapping it
+        while live and any(lo < cursor + n and cursor < hi for lo, hi, _ in live):
+            lo, hi, h = live.pop(0)
+            h.wait()
         while time.perf_counter() - t0 < at:
             pass
-        handles.append(server.submit(H, np.ones(H.shape[1], np.float32)))
+        H = pool[:n].reshape(n_sc, K, M)
+        W = ring[cursor:cursor + n].reshape(n_sc, K, M)
+        arrays = {"H": H, "t": ones, "W": W, "obj": np.empty(n_sc, np.float32),
+                  "resid": None, "flags": np.empty(n_sc, np.int32)}
+        job = capi.Job(M, K, n_sc, capi.ptr(H), capi.ptr(ones), 1, capi.ptr(W),
+                       capi.ptr(arrays["obj"]), None, capi.ptr(arrays["flags"]), 0)
+        h = JobHandle(server, capi.precode_serve_submit(server.handle, job), arrays)
+        handles.append(h)
+        live.append((cursor, cursor + n, h))
+        cursor += n
     for h in handles:
         h.wait()
+    wall = time.perf_counter() - t0
     st = server.stats()
     st["jobs"] = len(handles)
     st["offered_rate_per_s"] = rate_per_s
+    st["achieved_rate_per_s"] = len(handles) / wall
     return st
