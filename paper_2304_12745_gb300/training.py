@@ -26,7 +26,7 @@ from .precoder import Plan, _stream_handle
 
 class PrecodeLoss(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, step, lam, plan, H, t, a):
+    def forward(ctx, step, lam, plan, H, t, a, group=None):
         B, K, M = H.shape
         dev = H.device
         loss = torch.empty(1, device=dev)
@@ -36,14 +36,17 @@ class PrecodeLoss(torch.autograd.Function):
         capi.precode_train_step(plan.handle, M, K, B, H, t, t_stride, step.detach().contiguous(),
                                 None if lam is None else lam.detach().contiguous(), a, loss,
                                 dstep, dlam, None, _stream_handle(None))
+        if group is not None:  # data-parallel ranks: global batch mean (2T + 2 numbers)
+            from .sharding import allreduce_mean
+            loss, dstep, dlam = allreduce_mean(loss, dstep, dlam, B, group)
         ctx.save_for_backward(dstep, dlam if dlam is not None else dstep)
         ctx.has_lam = lam is not None
-        return loss[0]
+        return loss.reshape(-1)[0]
 
     @staticmethod
     def backward(ctx, g):
         dstep, dlam = ctx.saved_tensors
-        return g * dstep, (g * dlam if ctx.has_lam else None), None, None, None, None
+        return g * dstep, (g * dlam if ctx.has_lam else None), None, None, None, None, None
 
 
 def mp_bound(K: int, M: int) -> float:
@@ -56,8 +59,11 @@ class UnfoldedTrainer:
 
     def __init__(self, mode: int, T: int, K: int, M: int, batch: int, *, a: float,
                  lr: float = 1e-3, init_step=None, init_lam=None, device: str = "cuda",
-                 step_normalised: bool = False):
+                 step_normalised: bool = False, group=None):
+        """`group`: a torch.distributed process group whose ranks each train on
+        their own batches; gradients are averaged over all ranks every step."""
         self.mode, self.T, self.K, self.M, self.batch, self.a = mode, T, K, M, batch, a
+        self.group = group
         self.plan = Plan(mode, T, [(M, K)], batch, step_normalised=step_normalised)
         L = mp_bound(K, M)
         if init_step is None:
@@ -84,7 +90,7 @@ class UnfoldedTrainer:
                 self.step.clamp_(min=0.0)
 
     def loss(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
-        return PrecodeLoss.apply(self.step, self.lam, self.plan, H, t, self.a)
+        return PrecodeLoss.apply(self.step, self.lam, self.plan, H, t, self.a, self.group)
 
     def train_step(self, H: torch.Tensor, t: torch.Tensor) -> float:
         self.opt.zero_grad(set_to_none=True)
