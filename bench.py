@@ -357,16 +357,20 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.070 GHz",
-            "kernel": "solve_kernel<proj,K=8,M=64>", "kernel_ms": kern_ms,
+            "kernel_ms": kern_ms,
             "flop_per_instance": fpi,
             "hbm": {"achieved_gbs": hbm_bytes / (kern_ms / 1e3) / 1e9,
                     "peak_gbs": peaks.get("hbm_gbs"), "algorithmic_bytes": hbm_bytes}}
-    prof = os.path.join(ROOT, "profiles", "solve_proj_k8_m64_fixed.traffic.json")
+    # DRAM traffic per launch from the committed ncu capture, if it was taken on
+    # the kernel variant that ran here
+    plan_kernel_name = capi.precode_plan_describe(plan.handle, M, K)
+    roof["kernel"] = plan_kernel_name
+    prof = os.path.join(ROOT, "profiles", "solve_proj_k8_m64_fixed.traffic.txt")
     if os.path.exists(prof):
-        try:
-            roof["traffic"] = json.load(open(prof)).get("traffic_bytes_per_launch")
-        except Exception:
-            pass
+        kv = dict(line.split(": ", 1) for line in open(prof).read().splitlines() if ": " in line)
+        if kv.get("kernel", "").strip() == plan_kernel_name:
+            roof["traffic"] = int(kv["traffic_bytes_per_launch"])
+            roof["traffic_source"] = kv.get("source")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

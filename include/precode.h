@@ -286,6 +286,12 @@ precode_status_t precode_serve_destroy(precode_server_t s);
  * plan was created (synchronises the plan's device).  0 in normal operation. */
 precode_status_t precode_plan_errors(precode_plan_t plan, uint64_t* count);
 
+/* Writes the kernel the plan runs for (M, K) into buf (NUL-terminated, as the
+ * profiler names it, e.g. "solve_kernel<1, 8, 64, ...>").  EINVAL if the plan
+ * does not cover the shape. */
+precode_status_t precode_plan_describe(precode_plan_t plan, int32_t M, int32_t K, char* buf,
+                                       size_t len);
+
 const char* precode_status_str(precode_status_t status);
 /* Message of the last failing call on this host thread ("" if none). */
 const char* precode_last_error(void);

@@ -80,6 +80,7 @@ _SIGS = {
     "precode_solve": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_solve_host": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_plan_errors": [_vp, ctypes.POINTER(ctypes.c_uint64)],
+    "precode_plan_describe": [_vp, _i32, _i32, ctypes.c_char_p, ctypes.c_size_t],
     "precode_solve_varlen": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_train_step": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_float, _vp,
                            _vp, _vp, _vp, _vp],
@@ -234,6 +235,12 @@ def precode_serve_channel_destroy(server, handle):
 
 def precode_serve_destroy(server):
     check(LIB.precode_serve_destroy(server), "precode_serve_destroy")
+
+
+def precode_plan_describe(plan, M, K) -> str:
+    buf = ctypes.create_string_buffer(256)
+    check(LIB.precode_plan_describe(plan, M, K, buf, 256), "precode_plan_describe")
+    return buf.value.decode()
 
 
 def precode_plan_errors(plan) -> int:

@@ -389,6 +389,17 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
   return st;
 }
 
+precode_status_t precode_plan_describe(precode_plan_t p, int32_t M, int32_t K, char* buf,
+                                       size_t len) {
+  if (!p || !buf || len == 0) return fail(PRECODE_EINVAL, "precode_plan_describe: bad argument");
+  const Variant* v = p->variant_for(M, K);
+  if (!v) return fail(PRECODE_EINVAL, "precode_plan_describe: shape not covered by the plan");
+  std::snprintf(buf, len, "solve_kernel<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v->mode,
+                v->KB, v->MB, v->GK, v->GM, v->JC, v->exact ? 1 : 0, v->NW, v->minb,
+                v->split ? 1 : 0, v->db ? 1 : 0);
+  return PRECODE_OK;
+}
+
 precode_status_t precode_plan_errors(precode_plan_t p, uint64_t* count) {
   if (!p || !count) return fail(PRECODE_EINVAL, "precode_plan_errors: NULL argument");
   DeviceGuard g(p->device);
