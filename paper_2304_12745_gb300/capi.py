@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libprecode.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, PENDING, ENOTFOUND = range(8)
 LAYER_PGD, LAYER_PROJ = 0, 1
 F_FP64_CHOL, F_SINGULAR, F_NONFINITE, F_TIMEOUT, F_INVALID = 1, 2, 4, 8, 16
-PLAN_AUTOTUNE, PLAN_STEP_NORMALISED, PLAN_GRAPHS = 1, 2, 4
+PLAN_AUTOTUNE, PLAN_STEP_NORMALISED, PLAN_GRAPHS, PLAN_TENSOR_CORES = 1, 2, 4, 8
 MAX_K, MAX_M, MAX_T = 32, 256, 65536
 
 

@@ -32,6 +32,7 @@ const std::vector<Variant>& variants() {
     std::vector<Variant> r;
     register_solve_pgd(r);
     register_solve_proj(r);
+    register_solve_tc(r);
     return r;
   }();
   return v;
@@ -63,10 +64,13 @@ int variant_occupancy(const Variant& v, int device) {
 
 // Default choice: the first exact variant of (mode, K, M), else the smallest
 // generic bucket that holds (K, M).
-const Variant* pick_variant(int mode, int M, int K) {
+const Variant* pick_variant(int mode, int M, int K, bool tensor_cores) {
   const Variant* best = nullptr;
+  if (tensor_cores)
+    for (const auto& v : variants())
+      if (v.tc && v.mode == mode && v.KB == K && v.MB == M) return &v;
   for (const auto& v : variants())
-    if (v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
+    if (v.mode == mode && v.exact && !v.tc && v.KB == K && v.MB == M) return &v;
   for (const auto& v : variants()) {
     if (v.mode != mode || v.exact || v.KB < K || v.MB < M) continue;
     if (!best || v.KB * v.MB < best->KB * best->MB) best = &v;
@@ -219,7 +223,7 @@ precode_status_t precode_plan(const precode_desc_t* d, precode_plan_t* out) {
       if (!shape_ok(d->mode, s.M, s.K))
         return fail(PRECODE_EINVAL, "precode_plan: shape (M=" + std::to_string(s.M) + ", K=" +
                                         std::to_string(s.K) + ") unsupported");
-      const Variant* v = pick_variant(d->mode, s.M, s.K);
+      const Variant* v = pick_variant(d->mode, s.M, s.K, (d->flags & PRECODE_PLAN_TENSOR_CORES) != 0);
       if (!v) return fail(PRECODE_EINVAL, "precode_plan: no kernel bucket holds the shape");
       if (variant_occupancy(*v, p->device) <= 0)
         return fail(PRECODE_ECUDA, "precode_plan: kernel variant cannot run on this device");
@@ -394,9 +398,13 @@ precode_status_t precode_plan_describe(precode_plan_t p, int32_t M, int32_t K, c
   if (!p || !buf || len == 0) return fail(PRECODE_EINVAL, "precode_plan_describe: bad argument");
   const Variant* v = p->variant_for(M, K);
   if (!v) return fail(PRECODE_EINVAL, "precode_plan_describe: shape not covered by the plan");
-  std::snprintf(buf, len, "solve_kernel<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v->mode,
-                v->KB, v->MB, v->GK, v->GM, v->JC, v->exact ? 1 : 0, v->NW, v->minb,
-                v->split ? 1 : 0, v->db ? 1 : 0);
+  if (v->tc)
+    std::snprintf(buf, len, "solve_tc_kernel<%d, %d, %d, %d>", v->mode, v->NW, v->minb,
+                  v->db ? 1 : 0);
+  else
+    std::snprintf(buf, len, "solve_kernel<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v->mode,
+                  v->KB, v->MB, v->GK, v->GM, v->JC, v->exact ? 1 : 0, v->NW, v->minb,
+                  v->split ? 1 : 0, v->db ? 1 : 0);
   return PRECODE_OK;
 }
 

@@ -30,7 +30,9 @@ bool shape_ok(int mode, int M, int K);
 // per bucket size, so every shape a plan bucket can hold has a home.
 void plan_build_buckets(precode_plan_t p);
 int variant_occupancy(const Variant& v, int device);
-const Variant* pick_variant(int mode, int M, int K);
+// Default variant for (mode, M, K): the tensor-core build if requested and present,
+// else the first exact build, else the smallest generic bucket holding the shape.
+const Variant* pick_variant(int mode, int M, int K, bool tensor_cores = false);
 std::vector<const Variant*> eligible_variants(int mode, int M, int K);
 // n_hint >= 0: launch no more blocks than needed for n_hint instances.
 precode_status_t launch_variant(const Variant& v, int device, int num_sms, const SolveArgs& A,

@@ -9,7 +9,7 @@ void register_solve_pgd(std::vector<Variant>& v) {
   v.push_back(Variant{kModePGD, KB, MB, GK, GM, JC, NW, MINB, EXACT, SPLIT, DB,                           \
                       (const void*)&solve_kernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW, MINB, SPLIT, DB>, \
                       SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW, DB>::SMEM_BYTES, NW * 32,      \
-                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW, DB>::GROUPS});
+                      SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW, DB>::GROUPS, false});
 #include "solve_variants.inc"
 #undef X
 }

@@ -9,7 +9,7 @@ void register_solve_proj(std::vector<Variant>& v) {
   v.push_back(Variant{kModeProj, KB, MB, GK, GM, JC, NW, MINB, EXACT, SPLIT, DB,                           \
                       (const void*)&solve_kernel<kModeProj, KB, MB, GK, GM, JC, EXACT, NW, MINB, SPLIT, DB>, \
                       SolveCfg<kModeProj, KB, MB, GK, GM, JC, NW, DB>::SMEM_BYTES, NW * 32,      \
-                      SolveCfg<kModeProj, KB, MB, GK, GM, JC, NW, DB>::GROUPS});
+                      SolveCfg<kModeProj, KB, MB, GK, GM, JC, NW, DB>::GROUPS, false});
 #include "solve_variants.inc"
 #undef X
 }

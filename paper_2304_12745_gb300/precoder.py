@@ -34,12 +34,14 @@ class Plan:
     def __init__(self, mode: int, T: int, shapes, max_instances: int, *,
                  cond_threshold: float = 0.0, autotune: bool = False,
                  step_normalised: bool = False, graphs: bool = False,
-                 device: int | None = None, tune_cache: str | None = None):
+                 tensor_cores: bool = False, device: int | None = None,
+                 tune_cache: str | None = None):
         if device is None:
             device = torch.cuda.current_device()
         flags = (capi.PLAN_AUTOTUNE if autotune else 0) | \
                 (capi.PLAN_STEP_NORMALISED if step_normalised else 0) | \
-                (capi.PLAN_GRAPHS if graphs else 0)
+                (capi.PLAN_GRAPHS if graphs else 0) | \
+                (capi.PLAN_TENSOR_CORES if tensor_cores else 0)
         self.mode, self.T, self.device = mode, T, device
         self.shapes = [tuple(s) for s in shapes]
         self.max_instances = max_instances

@@ -287,3 +287,59 @@ def test_fixed_workload_full_size_sampled(pc, orc):
     assert_parity((W[idx], obj[idx], res[idx], fl[idx]), ref)
     assert np.all(np.isfinite(obj)) and np.all(res < 1e-4 * math.sqrt(wl.K))
     assert (fl != 0).mean() < 0.01
+
+
+# ---------------------------------------------------------------- tensor-core build (K=8, M=64)
+
+@pytest.mark.parametrize("mode", ["proj", "pgd"])
+def test_tensor_core_variant_parity(pc, orc, mode):
+    """Warp-MMA build with split-TF32 operands: same tolerances as the FP32 build."""
+    capi, precoder = pc
+    B = 1000
+    if mode == "proj":
+        H = ch.lognormal(B, 8, 64, seed=2)
+        t = ch.targets(B, 8)
+        step, lam, m = ch.fixed_workload_steps(10), None, capi.LAYER_PROJ
+    else:
+        H = ch.rayleigh(B, 8, 64, seed=9)
+        t = ch.targets(B, 8, gamma_db=10.0)
+        L = 1 / ch.paper_eta(8, 64)
+        step = np.linspace(1 / L, 1 / (2 * L), 20).astype(np.float32)
+        lam, m = np.full(20, 1 / 15, np.float32), capi.LAYER_PGD
+    gpu = run_gpu(precoder, m, H, t, step, lam, tensor_cores=True)
+    ref = oracle_ref(orc, 1 if mode == "proj" else 0, H, t, step, lam)
+    e, eo = assert_parity(gpu, ref)
+    if mode == "proj":
+        assert np.all(gpu[2] <= 1e-4 * math.sqrt(8))
+
+
+def test_tensor_core_variant_flags_and_uneven(pc, orc):
+    capi, precoder = pc
+    H = ch.rayleigh(40, 8, 64, seed=23)
+    H[3, 5] = H[3, 2]   # singular
+    H[7, 1, 9] = np.inf  # non-finite
+    t = ch.targets(40, 8)
+    mu = np.full(6, 0.05, np.float32)
+    W, obj, res, fl = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, tensor_cores=True)
+    assert fl[3] & capi.F_SINGULAR and not np.any(W[3]) and obj[3] == 0
+    assert fl[7] & capi.F_NONFINITE
+    ok = [b for b in range(40) if b not in (3, 7)]
+    assert np.all(fl[ok] == 0)
+    assert_parity((W[ok], obj[ok], res[ok], fl[ok]), oracle_ref(orc, 1, H[ok], t[ok], mu))
+
+
+def test_tensor_core_full_size_sampled(pc, orc):
+    capi, precoder = pc
+    wl = ch.WORKLOADS["fixed"]
+    H = ch.lognormal(wl.B, wl.K, wl.M, seed=wl.seed)
+    t = ch.targets(wl.B, wl.K)
+    mu = ch.fixed_workload_steps(wl.T)
+    plan = precoder.Plan(capi.LAYER_PROJ, wl.T, [(wl.M, wl.K)], wl.B, tensor_cores=True)
+    assert "solve_tc_kernel" in capi.precode_plan_describe(plan.handle, wl.M, wl.K)
+    W, obj, res, fl = plan.solve(torch.from_numpy(H).cuda(), torch.from_numpy(t).cuda(),
+                                 torch.from_numpy(mu).cuda())
+    W, obj, res, fl = W.cpu().numpy(), obj.cpu().numpy(), res.cpu().numpy(), fl.cpu().numpy()
+    plan.close()
+    idx = np.sort(np.random.default_rng(1).choice(wl.B, 256, replace=False))
+    assert_parity((W[idx], obj[idx], res[idx], fl[idx]), oracle_ref(orc, 1, H[idx], t[idx], mu))
+    assert np.all(res < 1e-4 * math.sqrt(wl.K)) and (fl != 0).mean() < 0.01
