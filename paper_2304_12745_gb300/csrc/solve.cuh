@@ -469,8 +469,9 @@ struct SolveKernel {
   }
 
   // FP64 Gram, LDL^H and inverse (no equilibration; a pivot below 1e-12 times
-  // its Gram diagonal entry means rank(H) < K).
-  __device__ static int setup_proj_fp64(Ctx& c, WReg& w) {
+  // its Gram diagonal entry means rank(H) < K).  G^{-1} goes to the reduction
+  // buffer (double2, K x K with row stride KB) unless the flags say singular.
+  __device__ static int fp64_inverse(Ctx& c) {
     const int K = Kd(c), M = Md(c);
     double2* G = reinterpret_cast<double2*>(c.Qs);
     double2* U = G + KB * KB;
@@ -516,10 +517,6 @@ struct SolveKernel {
     }
     if (singular) {
       gsync(c);
-#pragma unroll
-      for (int u = 0; u < UPT; ++u)
-#pragma unroll
-        for (int q = 0; q < NA; ++q) w[u][q] = mkc<CT>(0.f, 0.f);
       return fl | PRECODE_F_SINGULAR;
     }
     if (c.g < K) pv[c.g] = 1.0 / G[c.g * KB + c.g].x;
@@ -551,6 +548,23 @@ struct SolveKernel {
       Gi[i * KB + j] = make_double2(sr, si);
     }
     gsync(c);
+    return fl;
+  }
+
+  // FP64 path of the projected-layer setup: fp64_inverse, then Q =
+  // conj(G^{-1} H) on own entries in FP64, rounded once, into Qs and W^(0) = S Q
+  // into w (zero when singular).  Returns the instance flags.
+  __device__ static int setup_proj_fp64(Ctx& c, WReg& w) {
+    const int K = Kd(c), M = Md(c);
+    const int fl = fp64_inverse(c);
+    if (fl & PRECODE_F_SINGULAR) {
+#pragma unroll
+      for (int u = 0; u < UPT; ++u)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) w[u][q] = mkc<CT>(0.f, 0.f);
+      return fl;
+    }
+    const double2* Gi = reinterpret_cast<const double2*>(c.red);
     // own entries of conj(G^{-1} H) in FP64, rounded once
 #pragma unroll
     for (int u = 0; u < UPT; ++u)

@@ -49,14 +49,30 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
   using C = typename Base::C;
   using Ctx = typename Base::Ctx;
   static constexpr int KB = 8, MB = 64;
-  // Per-lane pre-split B fragments of the second contraction, [nt][hi/lo][lane]
-  // float4 (8 KB).  They live in the Q + reduction buffers, which only the setup uses.
-  static constexpr int XF_BYTES = 8 * 2 * 32 * 16;
-  static_assert(C::Q_BYTES + C::RED_BYTES >= XF_BYTES || MODE == kModePGD, "fragment area");
-  static constexpr int XF_OFF = MODE == kModeProj ? C::Q_OFF : C::GROUP_BYTES;
-  static constexpr int GROUP_STRIDE =
-      MODE == kModeProj ? C::GROUP_BYTES : align_up(C::GROUP_BYTES + XF_BYTES, 16);
+  static constexpr int NHB = C::NHB;
+  // Per-warp shared memory, two overlaid phases (bytes):
+  //   setup : H (raw channel) | Q / FP64 scratch | Gauss-Jordan buffers | Gram
+  //   layers: H hi parts (in place) | X fragments hi/lo | H lo parts | norm partials | factors
+  //   both  : t, scalars, copy barriers (and the second channel buffer with prefetch)
+  static constexpr int H_BYTES = KB * MB * 8;
+  static constexpr int OFF_Q = H_BYTES;                       // setup
+  static constexpr int OFF_RED = OFF_Q + KB * MB * 8;         // setup
+  static constexpr int OFF_E = OFF_RED + C::RED_BYTES;        // setup
+  // Without prefetch the layers read H pre-split (hi in place, lo beside it);
+  // with prefetch they split it on the fly, which leaves room for the second
+  // channel buffer at the same occupancy.
+  static constexpr bool PRE = !DB;
+  static constexpr int OFF_XF = H_BYTES;                      // layers, 8 KB
+  static constexpr int OFF_LO = OFF_XF + 8192;                // layers, 4 KB (PRE)
+  static constexpr int OFF_NB = OFF_LO + (PRE ? H_BYTES : 0); // layers, 2 KB
+  static constexpr int OFF_FB = OFF_NB + 2048;                // layers, 256 B
+  static constexpr int OFF_SC = OFF_FB + 256;
+  static constexpr int OFF_BAR = OFF_SC + C::SC_BYTES;
+  static constexpr int OFF_H1 = align_up(OFF_BAR + 8 * NHB, 16);
+  static constexpr int GROUP_STRIDE = OFF_H1 + (DB ? H_BYTES : 0);
   static constexpr int SMEM_BYTES = C::GROUPS * GROUP_STRIDE;
+  static_assert(OFF_E + KB * KB * 8 <= OFF_SC, "setup buffers stay clear of the scalars");
+  static_assert(C::GROUPS == NW, "one instance per warp");
 
   struct Lane {
     int g, q, lane;
@@ -65,36 +81,73 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
   //                                     Im W[g][8s+2q], Im W[g][8s+2q+1])
   using WT = float[8][4];
 
-  __device__ __forceinline__ static void colnorm2(const WT& w, float (&r2)[8][2]) {
+  // Column (antenna) sums over the 8 users of |W|^2: each lane stores its 16
+  // partial squares, then lane (rq, rs) = (lane % 4, lane / 4) adds up antennas
+  // 8 rs + 2 rq + {0, 1} over the users.  Chunks of 4 floats are XOR-swizzled so
+  // that both the 128-bit stores and the 64-bit column reads are conflict free.
+  __device__ __forceinline__ static int nb_swz(int writer) {
+    const int b = writer >> 1;
+    return ((b & 1) << 1) | ((b >> 1) & 1);
+  }
+  __device__ __forceinline__ static float2 colsum(const Lane& L, float* nb, const WT& w) {
+    const int sw = nb_swz(L.lane);
 #pragma unroll
-    for (int s = 0; s < 8; ++s)
+    for (int j = 0; j < 4; ++j) {
+      float4 p;
+      p.x = fmaf(w[2 * j][0], w[2 * j][0], w[2 * j][2] * w[2 * j][2]);
+      p.y = fmaf(w[2 * j][1], w[2 * j][1], w[2 * j][3] * w[2 * j][3]);
+      p.z = fmaf(w[2 * j + 1][0], w[2 * j + 1][0], w[2 * j + 1][2] * w[2 * j + 1][2]);
+      p.w = fmaf(w[2 * j + 1][1], w[2 * j + 1][1], w[2 * j + 1][3] * w[2 * j + 1][3]);
+      *reinterpret_cast<float4*>(nb + L.lane * 16 + 4 * (j ^ sw)) = p;
+    }
+    __syncwarp();
+    const int rq = L.lane & 3, rs = L.lane >> 2;
+    float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) r2[s][h] = fmaf(w[s][h], w[s][h], w[s][2 + h] * w[s][2 + h]);
-#pragma unroll
-    for (int msk = 4; msk < 32; msk <<= 1)
-#pragma unroll
-      for (int s = 0; s < 8; ++s)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) r2[s][h] += __shfl_xor_sync(0xffffffffu, r2[s][h], msk);
+    for (int g = 0; g < 8; ++g) {
+      const int wr = 4 * g + rq;
+      const float2 v =
+          *reinterpret_cast<const float2*>(nb + wr * 16 + 4 * ((rs >> 1) ^ nb_swz(wr)) + (rs & 1) * 2);
+      a.x += v.x;
+      a.y += v.y;
+    }
+    return a;
   }
 
-  __device__ __forceinline__ static void shrink(WT& w, const float (&r2)[8][2], float tau) {
+  // Group soft threshold with the column sums of colsum: the reading lane forms
+  // the factors of its two antennas, every lane then scales its own entries.
+  __device__ __forceinline__ static void shrink(const Lane& L, float* fb, float2 r2, float tau,
+                                                WT& w) {
     const float tau2 = tau * tau;
+    const float f0 = (r2.x > tau2) ? (1.f - tau * rsqrtf(r2.x)) : 0.f;
+    const float f1 = (r2.y > tau2) ? (1.f - tau * rsqrtf(r2.y)) : 0.f;
+    const int rq = L.lane & 3, rs = L.lane >> 2;
+    *reinterpret_cast<float2*>(fb + rq * 16 + 4 * ((rs >> 1) ^ (rq & 2)) + (rs & 1) * 2) =
+        make_float2(f0, f1);
+    __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 8; ++s)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float f = (r2[s][h] > tau2) ? (1.f - tau * rsqrtf(r2[s][h])) : 0.f;
-        w[s][h] *= f;
-        w[s][2 + h] *= f;
-      }
+    for (int j = 0; j < 4; ++j) {
+      const float4 f = *reinterpret_cast<const float4*>(fb + L.q * 16 + 4 * (j ^ (L.q & 2)));
+      w[2 * j][0] *= f.x;
+      w[2 * j][2] *= f.x;
+      w[2 * j][1] *= f.y;
+      w[2 * j][3] *= f.y;
+      w[2 * j + 1][0] *= f.z;
+      w[2 * j + 1][2] *= f.z;
+      w[2 * j + 1][1] *= f.w;
+      w[2 * j + 1][3] *= f.w;
+    }
   }
 
   // E = W H^T (minus S on the diagonal when sub_s): returns the lane's fragment
   // e = (E_re[g][2q], E_re[g][2q+1], E_im[g][2q], E_im[g][2q+1]).  Four blocks of
   // 8 antennas at a time, their MMAs issued term by term over four accumulators.
-  __device__ __forceinline__ static void residual(const Lane& L, const float2* Hs, const WT& w,
-                                                  const float* tks, bool sub_s, float (&e)[4]) {
+  // PRE: H comes pre-split, hi / lo fragments (Hr0, Hr1, Hi0, Hi1) at [s][lane];
+  // otherwise it is read from the raw channel and split here.
+  template <bool PRE>
+  __device__ __forceinline__ static void residual(const Lane& L, const float2* Hs, const float4* hhi,
+                                                  const float4* hlo, const WT& w, const float* tks,
+                                                  bool sub_s, float (&e)[4]) {
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -106,24 +159,36 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int s = s0 + u;
-        const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
-        split_tf32(hv.x, bh[u][0], bl[u][0]);
-        split_tf32(hv.z, bh[u][1], bl[u][1]);
-        split_tf32(hv.y, bh[u][2], bl[u][2]);
-        split_tf32(hv.w, bh[u][3], bl[u][3]);
+        if constexpr (PRE) {
+          const float4 hh = hhi[s * 32 + L.lane], hl = hlo[s * 32 + L.lane];
+          bh[u][0] = __float_as_uint(hh.x);
+          bh[u][1] = __float_as_uint(hh.y);
+          bh[u][2] = __float_as_uint(hh.z);
+          bh[u][3] = __float_as_uint(hh.w);
+          bl[u][0] = __float_as_uint(hl.x);
+          bl[u][1] = __float_as_uint(hl.y);
+          bl[u][2] = __float_as_uint(hl.z);
+          bl[u][3] = __float_as_uint(hl.w);
+        } else {
+          const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+          split_tf32(hv.x, bh[u][0], bl[u][0]);
+          split_tf32(hv.z, bh[u][1], bl[u][1]);
+          split_tf32(hv.y, bh[u][2], bl[u][2]);
+          split_tf32(hv.w, bh[u][3], bl[u][3]);
+        }
         split_tf32(w[s][0], ah[u][0], al[u][0]);  // Re W, h = 0
         split_tf32(w[s][2], ah[u][1], al[u][1]);  // Im W, h = 0
         split_tf32(w[s][1], ah[u][2], al[u][2]);  // Re W, h = 1
         split_tf32(w[s][3], ah[u][3], al[u][3]);  // Im W, h = 1
       }
-      // real block (kb = s): A = (re0, im0, re1, im1), B = (hr0, hr1)
+      // real block: A = (re0, im0, re1, im1), B = (hr0, hr1)
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         mma_tf32(acc[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bl[u][0], bl[u][1]);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         mma_tf32(acc[u], al[u][0], al[u][1], al[u][2], al[u][3], bh[u][0], bh[u][1]);
-      // imaginary block (kb = s + 8): A = (-im0, re0, -im1, re1), B = (hi0, hi1)
+      // imaginary block: A = (-im0, re0, -im1, re1), B = (hi0, hi1)
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         mma_tf32(acc[u], neg_bits(ah[u][1]), ah[u][0], neg_bits(ah[u][3]), ah[u][2], bl[u][2],
@@ -157,7 +222,7 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
     split_tf32(e[1], c1h, c1l);
     split_tf32(e[2], c2h, c2l);
     split_tf32(e[3], c3h, c3l);
-    // -A2: k-step 0 = (-c0, -c2, -c1, -c3), k-step 1 = (c2, -c0, c3, -c1)
+    // -A: k-step 0 = (-c0, -c2, -c1, -c3), k-step 1 = (c2, -c0, c3, -c1)
     const uint32_t n0h = neg_bits(c0h), n1h = neg_bits(c1h), n2h = neg_bits(c2h),
                    n3h = neg_bits(c3h);
     const uint32_t n0l = neg_bits(c0l), n1l = neg_bits(c1l), n2l = neg_bits(c2l),
@@ -191,6 +256,126 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
     }
   }
 
+  // Inverse of the Gram matrix from the lane's fragment e of E = G^T (Hermitian,
+  // same diagonal and conditioning as G): the equilibrated matrix D E D (D =
+  // diag(E)^{-1/2}) is inverted by Gauss-Jordan elimination without pivoting,
+  // every lane keeping its own two entries in registers and fetching the pivot
+  // row and column by shuffles.  The pivots are the LDL^H pivots, so their
+  // spread max/min is the condition estimate.  Returns false (and the caller
+  // takes the FP64 path) when a pivot is not positive and finite or the estimate
+  // exceeds cond_thr; otherwise gi = the lane's entries (g, 2q), (g, 2q + 1) of
+  // G^{-T} = D (D E D)^{-1} D as (re, re, im, im).
+  __device__ __forceinline__ static bool gram_inverse(const Lane& L, const float (&e)[4],
+                                                      float cond_thr, float (&gi)[4]) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const float dg_own = (L.g == 2 * L.q) ? e[0] : e[1];  // E[i][i] sits on lane (i, i / 2)
+    const float sg = rsqrtf(__shfl_sync(FULL, dg_own, 4 * L.g + (L.g >> 1)));
+    const float s0 = rsqrtf(__shfl_sync(FULL, dg_own, 9 * L.q));      // lane (2q, q)
+    const float s1 = rsqrtf(__shfl_sync(FULL, dg_own, 9 * L.q + 4));  // lane (2q + 1, q)
+    float ar0 = e[0] * (sg * s0), ar1 = e[1] * (sg * s1);
+    float ai0 = e[2] * (sg * s0), ai1 = e[3] * (sg * s1);
+    bool fail = false;
+    float dmin = FLT_MAX, dmax = 0.f;
+#pragma unroll
+    for (int p = 0; p < KB; ++p) {
+      const int own = 4 * L.g + (p >> 1);  // lane holding (g, p)
+      const int prow = 4 * p + L.q;        // lane holding (p, 2q), (p, 2q + 1)
+      const float d = __shfl_sync(FULL, (p & 1) ? ar1 : ar0, 4 * p + (p >> 1));
+      const float pr0 = __shfl_sync(FULL, ar0, prow), pr1 = __shfl_sync(FULL, ar1, prow);
+      const float pi0 = __shfl_sync(FULL, ai0, prow), pi1 = __shfl_sync(FULL, ai1, prow);
+      const float cr = __shfl_sync(FULL, (p & 1) ? ar1 : ar0, own);
+      const float ci = __shfl_sync(FULL, (p & 1) ? ai1 : ai0, own);
+      fail |= !(d > 0.f) || !(d < FLT_MAX);
+      dmin = fminf(dmin, d);
+      dmax = fmaxf(dmax, d);
+      const float inv = __frcp_rn(d);
+      const float tr = cr * inv, ti = ci * inv;  // A[g][p] / d
+      // generic entry: a - (A[g][p] / d) A[p][j]
+      float n0r = ar0 - (tr * pr0 - ti * pi0), n0i = ai0 - (tr * pi0 + ti * pr0);
+      float n1r = ar1 - (tr * pr1 - ti * pi1), n1i = ai1 - (tr * pi1 + ti * pr1);
+      const bool rowp = L.g == p, c0p = 2 * L.q == p, c1p = 2 * L.q + 1 == p;
+      if (rowp) {  // pivot row: A[p][j] / d
+        n0r = pr0 * inv;
+        n0i = pi0 * inv;
+        n1r = pr1 * inv;
+        n1i = pi1 * inv;
+      }
+      if (c0p) {  // pivot column: -A[i][p] / d, pivot 1 / d
+        n0r = rowp ? inv : -tr;
+        n0i = rowp ? 0.f : -ti;
+      }
+      if (c1p) {
+        n1r = rowp ? inv : -tr;
+        n1i = rowp ? 0.f : -ti;
+      }
+      ar0 = n0r;
+      ar1 = n1r;
+      ai0 = n0i;
+      ai1 = n1i;
+    }
+    gi[0] = ar0 * (sg * s0);
+    gi[1] = ar1 * (sg * s1);
+    gi[2] = ai0 * (sg * s0);
+    gi[3] = ai1 * (sg * s1);
+    return !fail && !(dmax > cond_thr * dmin);
+  }
+
+  // Q = G^{-T} H^* and its transpose as split-TF32 MMAs on the same fragments:
+  //   Q   tile nt (rows user g, antennas 8nt + 2q + {0,1}) = G^{-T} conj(H), whose
+  //       accumulator is W's own layout, so W^(0) = S Q needs no data movement;
+  //   Q^T tile nt = conj(H)^T G^{-1}, whose accumulator is exactly the update's
+  //       B fragment (Q[2q][8nt+g], Q[2q+1][8nt+g]), stored split into xf.
+  // The A operand of one product is the B operand of the other: the lane's G^{-T}
+  // entries gi and the channel entries H[2q][8nt+g], H[2q+1][8nt+g].
+  __device__ __forceinline__ static void q_mma(const Lane& L, const float2* Hs, const float (&gi)[4],
+                                               float tg, float4* xf, WT& w) {
+    uint32_t gr0h, gr0l, gr1h, gr1l, gi0h, gi0l, gi1h, gi1l;
+    split_tf32(gi[0], gr0h, gr0l);
+    split_tf32(gi[1], gr1h, gr1l);
+    split_tf32(gi[2], gi0h, gi0l);
+    split_tf32(gi[3], gi1h, gi1l);
+    const uint32_t ngi0h = neg_bits(gi0h), ngi0l = neg_bits(gi0l);
+    const uint32_t ngi1h = neg_bits(gi1h), ngi1l = neg_bits(gi1l);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const float2 h0 = Hs[(2 * L.q) * MB + 8 * nt + L.g];
+      const float2 h1 = Hs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+      uint32_t xr0h, xr0l, xr1h, xr1l, xi0h, xi0l, xi1h, xi1l;  // X = conj(H)
+      split_tf32(h0.x, xr0h, xr0l);
+      split_tf32(h1.x, xr1h, xr1l);
+      split_tf32(-h0.y, xi0h, xi0l);
+      split_tf32(-h1.y, xi1h, xi1l);
+      const uint32_t nxi0h = neg_bits(xi0h), nxi0l = neg_bits(xi0l);
+      const uint32_t nxi1h = neg_bits(xi1h), nxi1l = neg_bits(xi1l);
+      float qt[4] = {0.f, 0.f, 0.f, 0.f}, qq[4] = {0.f, 0.f, 0.f, 0.f};
+      // Q^T: k-step 0 A = (xr0, xi0, xr1, xi1), B = (gr0, gr1);
+      //      k-step 1 A = (-xi0, xr0, -xi1, xr1), B = (gi0, gi1)
+      // Q:   k-step 0 A = (gr0, gi0, gr1, gi1), B = (xr0, xr1);
+      //      k-step 1 A = (-gi0, gr0, -gi1, gr1), B = (xi0, xi1)
+      mma_tf32(qt, xr0h, xi0h, xr1h, xi1h, gr0l, gr1l);
+      mma_tf32(qq, gr0h, gi0h, gr1h, gi1h, xr0l, xr1l);
+      mma_tf32(qt, xr0l, xi0l, xr1l, xi1l, gr0h, gr1h);
+      mma_tf32(qq, gr0l, gi0l, gr1l, gi1l, xr0h, xr1h);
+      mma_tf32(qt, nxi0h, xr0h, nxi1h, xr1h, gi0l, gi1l);
+      mma_tf32(qq, ngi0h, gr0h, ngi1h, gr1h, xi0l, xi1l);
+      mma_tf32(qt, nxi0l, xr0l, nxi1l, xr1l, gi0h, gi1h);
+      mma_tf32(qq, ngi0l, gr0l, ngi1l, gr1l, xi0h, xi1h);
+      mma_tf32(qt, xr0h, xi0h, xr1h, xi1h, gr0h, gr1h);
+      mma_tf32(qq, gr0h, gi0h, gr1h, gi1h, xr0h, xr1h);
+      mma_tf32(qt, nxi0h, xr0h, nxi1h, xr1h, gi0h, gi1h);
+      mma_tf32(qq, ngi0h, gr0h, ngi1h, gr1h, xi0h, xi1h);
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) split_tf32(qt[k], h[k], l[k]);
+      xf[(nt * 2 + 0) * 32 + L.lane] = make_float4(__uint_as_float(h[0]), __uint_as_float(h[1]),
+                                                   __uint_as_float(h[2]), __uint_as_float(h[3]));
+      xf[(nt * 2 + 1) * 32 + L.lane] = make_float4(__uint_as_float(l[0]), __uint_as_float(l[1]),
+                                                   __uint_as_float(l[2]), __uint_as_float(l[3]));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[nt][k] = tg * qq[k];
+    }
+  }
+
   __device__ static void run(const SolveArgs& A) {
     extern __shared__ __align__(16) unsigned char smem[];
     Ctx c;
@@ -207,25 +392,26 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
     L.g = c.lane >> 2;
     L.q = c.lane & 3;
     unsigned char* gs = smem + c.gid * GROUP_STRIDE;
-    c.Qs = reinterpret_cast<float2*>(gs + C::Q_OFF);
-    c.red = reinterpret_cast<float*>(gs + C::RED_OFF);
-    c.Es = reinterpret_cast<float2*>(gs + C::E_OFF);
-    c.nrm = reinterpret_cast<float*>(gs + C::NRM_OFF);
-    c.tks = reinterpret_cast<float*>(gs + C::SC_OFF);
+    c.Qs = reinterpret_cast<float2*>(gs + OFF_Q);
+    c.red = reinterpret_cast<float*>(gs + OFF_RED);
+    c.Es = reinterpret_cast<float2*>(gs + OFF_E);
+    c.nrm = nullptr;
+    c.tks = reinterpret_cast<float*>(gs + OFF_SC);
     c.dsc = c.tks + KB;
     c.piv = c.dsc + KB;
     c.misc = reinterpret_cast<int*>(c.piv + KB);
     c.wsum = reinterpret_cast<float*>(c.misc + 8);
-    c.bar = reinterpret_cast<uint64_t*>(gs + C::BAR_OFF);
-    c.Hs = reinterpret_cast<float2*>(gs + C::H_OFF);
-    float4* xf = reinterpret_cast<float4*>(gs + XF_OFF);
-    constexpr int NHB = C::NHB;
+    c.bar = reinterpret_cast<uint64_t*>(gs + OFF_BAR);
+    float4* const xf = reinterpret_cast<float4*>(gs + OFF_XF);
+    float4* const hlo = reinterpret_cast<float4*>(gs + OFF_LO);
+    float* const nb = reinterpret_cast<float*>(gs + OFF_NB);
+    float* const fb = reinterpret_cast<float*>(gs + OFF_FB);
     if (c.g == 0)
       for (int q = 0; q < NHB; ++q) mbar_init(c.bar + q, 1);
     fence_mbar_init();
     __syncthreads();
 
-    float2* const hbuf0 = reinterpret_cast<float2*>(gs + C::H_OFF);
+    auto hbuf = [&](int qb) { return reinterpret_cast<float2*>(gs + (qb == 0 ? 0 : OFF_H1)); };
     uint32_t phases = 0;
     const int64_t n_inst = A.tbl ? (int64_t)(*A.count) : A.B;
     const int64_t stride = (int64_t)gridDim.x * C::GROUPS;
@@ -249,20 +435,21 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       locate(it, inst, h_off, w_off, t_off);
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(c.bar + qb, KB * MB * 8);
-      bulk_g2s(hbuf0 + qb * (KB * MB), A.H + h_off, KB * MB * 8, c.bar + qb);
+      bulk_g2s(hbuf(qb), A.H + h_off, KB * MB * 8, c.bar + qb);
     };
     const int64_t first = (int64_t)blockIdx.x * C::GROUPS + c.gid;
     for (int qb = 0; qb < NHB; ++qb) issue_copy(first + qb * stride, qb);
     int cur = 0;
     WT w;
-    float r2[8][2], e[4];
+    float e[4];
 #pragma unroll 1
     for (int64_t it = first; it < n_inst; it += stride, cur = (cur + 1) % NHB) {
       int64_t inst, h_off, w_off, t_off;
       locate(it, inst, h_off, w_off, t_off);
       c.K = KB;
       c.M = MB;
-      c.Hs = hbuf0 + cur * (KB * MB);
+      c.Hs = hbuf(cur);
+      const float4* const hhi = reinterpret_cast<const float4*>(c.Hs);
       const uint32_t par = (phases >> cur) & 1u;
       __syncwarp();
       if (c.g < KB) c.tks[c.g] = A.t[t_off + c.g];
@@ -294,54 +481,136 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
         w[s][2] = -hv.y;
         w[s][3] = -hv.w;
       }
-      const bool need_gram = (MODE == kModeProj) || (A.opts & OPT_STEP_NORMALISED);
-      if (need_gram) {
-        residual(L, c.Hs, w, c.tks, false, e);  // sum_m conj(H_gm) H_jm = G^T
-        *reinterpret_cast<float4*>(c.Es + L.g * KB + 2 * L.q) = make_float4(e[0], e[2], e[1], e[3]);
-        __syncwarp();
-        if constexpr (MODE == kModeProj) {
-          typename Base::WReg wtmp;
-          fl = Base::setup_proj(c, wtmp, A.cond_thr);  // Q = G^{-T} H^* into Qs (natural)
+      bool fast = true;  // projected layer: FP32 register inverse and MMA-formed Q
+      if constexpr (MODE == kModeProj) {
+        residual<false>(L, c.Hs, nullptr, nullptr, w, c.tks, false, e);  // conj(H) H^T = G^T
+        float gi[4];
+        fast = gram_inverse(L, e, A.cond_thr, gi);
+        if (fast) {
+          // xf lies outside the raw channel, which the other lanes still read
+          q_mma(L, c.Hs, gi, c.tks[L.g], xf, w);
         } else {
-          invL = Base::inv_gershgorin(c);
-        }
-      }
-      const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
-      // fragments X[2q][8nt+g], X[2q+1][8nt+g] of the update, read before the
-      // fragment area (which overlaps Q) is written
-      {
-        const float2* X = (MODE == kModeProj) ? c.Qs : c.Hs;
-        const float csign = (MODE == kModeProj) ? 1.f : -1.f;  // paper layer: X = conj(H)
-        float2 x0[8], x1[8];
+          fl = Base::fp64_inverse(c);  // G^{-1} in FP64 into the reduction buffer
+          if (!(fl & PRECODE_F_SINGULAR)) {
+            // Q = conj(G^{-1} H) in FP64, rounded once, into Qs (natural); one entry
+            // at a time keeps this rare path light on registers
+            const double2* Gi = reinterpret_cast<const double2*>(c.red);
+#pragma unroll 1
+            for (int idx = L.lane; idx < KB * MB; idx += 32) {
+              const int k = idx / MB, m = idx - k * MB;
+              double zr = 0.0, zi = 0.0;
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-          x0[nt] = singular ? make_float2(0.f, 0.f) : X[(2 * L.q) * MB + 8 * nt + L.g];
-          x1[nt] = singular ? make_float2(0.f, 0.f) : X[(2 * L.q + 1) * MB + 8 * nt + L.g];
-        }
-        if constexpr (MODE == kModeProj) {  // W^(0) = S Q
-          const float tg = c.tks[L.g];
-#pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            const float4 qv = singular ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                       : *reinterpret_cast<const float4*>(c.Qs + L.g * MB + 8 * s + 2 * L.q);
-            w[s][0] = tg * qv.x;
-            w[s][1] = tg * qv.z;
-            w[s][2] = tg * qv.y;
-            w[s][3] = tg * qv.w;
+              for (int l = 0; l < KB; ++l) {
+                const double2 gkl = Gi[k * KB + l];
+                const float2 x = c.Hs[l * MB + m];
+                zr += gkl.x * x.x - gkl.y * x.y;
+                zi += gkl.x * x.y + gkl.y * x.x;
+              }
+              c.Qs[idx] = make_float2((float)zr, (float)-zi);
+            }
+            __syncwarp();
           }
         }
+      } else if (A.opts & OPT_STEP_NORMALISED) {
+        residual<false>(L, c.Hs, nullptr, nullptr, w, c.tks, false, e);  // conj(H) H^T = G^T
+        *reinterpret_cast<float4*>(c.Es + L.g * KB + 2 * L.q) = make_float4(e[0], e[2], e[1], e[3]);
         __syncwarp();
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
+        invL = Base::inv_gershgorin(c);
+      }
+      const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
+      // ---- phase change: the layer buffers overwrite the setup buffers, so each
+      // operand is read out (into registers) before its area is reused.
+      {
+        float4* const hh = reinterpret_cast<float4*>(c.Hs);
+        // update fragments X[2q][8nt+g], X[2q+1][8nt+g], split into xf
+        auto put_x = [&](int nt, float2 x0, float2 x1, float csign) {
           uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
-          split_tf32(x0[nt].x, h0, l0);
-          split_tf32(x1[nt].x, h1, l1);
-          split_tf32(csign * x0[nt].y, h2, l2);
-          split_tf32(csign * x1[nt].y, h3, l3);
+          split_tf32(x0.x, h0, l0);
+          split_tf32(x1.x, h1, l1);
+          split_tf32(csign * x0.y, h2, l2);
+          split_tf32(csign * x1.y, h3, l3);
           xf[(nt * 2 + 0) * 32 + L.lane] = make_float4(__uint_as_float(h0), __uint_as_float(h1),
                                                        __uint_as_float(h2), __uint_as_float(h3));
           xf[(nt * 2 + 1) * 32 + L.lane] = make_float4(__uint_as_float(l0), __uint_as_float(l1),
                                                        __uint_as_float(l2), __uint_as_float(l3));
+        };
+        // H hi parts in place of the raw channel, lo parts beside them, from the
+        // lane's own entries v[s] = (Re, Re, Im, Im) at antennas 8s + 2q + {0, 1}
+        auto put_h = [&](const float (&v)[8][4]) {
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+            split_tf32(v[s][0], h0, l0);
+            split_tf32(v[s][1], h1, l1);
+            split_tf32(v[s][2], h2, l2);
+            split_tf32(v[s][3], h3, l3);
+            hh[s * 32 + L.lane] = make_float4(__uint_as_float(h0), __uint_as_float(h1),
+                                              __uint_as_float(h2), __uint_as_float(h3));
+            hlo[s * 32 + L.lane] = make_float4(__uint_as_float(l0), __uint_as_float(l1),
+                                               __uint_as_float(l2), __uint_as_float(l3));
+          }
+        };
+        if constexpr (MODE == kModePGD) {
+          // X = conj(H) from the raw channel; xf lies outside it
+#pragma unroll
+          for (int nt = 0; nt < 8; ++nt)
+            put_x(nt, c.Hs[(2 * L.q) * MB + 8 * nt + L.g], c.Hs[(2 * L.q + 1) * MB + 8 * nt + L.g], -1.f);
+          if constexpr (PRE) {
+            __syncwarp();
+            float v[8][4];  // w = conj(H) = W^(0) stays live
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              v[s][0] = w[s][0];
+              v[s][1] = w[s][1];
+              v[s][2] = -w[s][2];
+              v[s][3] = -w[s][3];
+            }
+            put_h(v);
+          }
+        } else {
+          // H re-read from the raw channel (w is rebuilt from Q below); all lanes
+          // read before any overwrites it
+          if constexpr (PRE) {
+            float v[8][4];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const float4 hv = *reinterpret_cast<const float4*>(c.Hs + L.g * MB + 8 * s + 2 * L.q);
+              v[s][0] = hv.x;
+              v[s][1] = hv.z;
+              v[s][2] = hv.y;
+              v[s][3] = hv.w;
+            }
+            __syncwarp();
+            put_h(v);
+          }
+          if (!fast) {
+            // X = Q from the FP64 path: tiles 4..7 of xf lie in the Gauss-Jordan
+            // area, tiles 0..3 over Q
+            const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int nt = 4; nt < 8; ++nt)
+              put_x(nt, singular ? z : c.Qs[(2 * L.q) * MB + 8 * nt + L.g],
+                    singular ? z : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g], 1.f);
+            const float tg = c.tks[L.g];  // W^(0) = S Q
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const float4 qv = singular ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                         : *reinterpret_cast<const float4*>(c.Qs + L.g * MB + 8 * s + 2 * L.q);
+              w[s][0] = tg * qv.x;
+              w[s][1] = tg * qv.z;
+              w[s][2] = tg * qv.y;
+              w[s][3] = tg * qv.w;
+            }
+            float2 x0[4], x1[4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+              x0[nt] = singular ? z : c.Qs[(2 * L.q) * MB + 8 * nt + L.g];
+              x1[nt] = singular ? z : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) put_x(nt, x0[nt], x1[nt], 1.f);
+          }
         }
       }
       __syncwarp();
@@ -353,22 +622,20 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
 #pragma unroll 1
         for (int l = 0; l < T; ++l) {
           if constexpr (MODE == kModeProj) {
-            colnorm2(w, r2);
-            shrink(w, r2, fmaxf(__ldg(A.step + l), 0.f));
-            residual(L, c.Hs, w, c.tks, true, e);
+            shrink(L, fb, colsum(L, nb, w), fmaxf(__ldg(A.step + l), 0.f), w);
+            residual<PRE>(L, c.Hs, hhi, hlo, w, c.tks, true, e);
             update(L, xf, e, w);
           } else {
             const float eta = __ldg(A.step + l) * invL;
-            residual(L, c.Hs, w, c.tks, true, e);
+            residual<PRE>(L, c.Hs, hhi, hlo, w, c.tks, true, e);
 #pragma unroll
             for (int k = 0; k < 4; ++k) e[k] *= eta;
             update(L, xf, e, w);
-            colnorm2(w, r2);
-            shrink(w, r2, fmaxf(fmaxf(__ldg(A.lam + l), 0.f) * eta, 0.f));
+            shrink(L, fb, colsum(L, nb, w), fmaxf(fmaxf(__ldg(A.lam + l), 0.f) * eta, 0.f), w);
           }
         }
         if (A.resid) {
-          residual(L, c.Hs, w, c.tks, true, e);
+          residual<PRE>(L, c.Hs, hhi, hlo, w, c.tks, true, e);
           rs = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + e[3] * e[3];
 #pragma unroll
           for (int msk = 1; msk < 32; msk <<= 1) rs += __shfl_xor_sync(0xffffffffu, rs, msk);
@@ -384,12 +651,10 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       // ---- channel buffer free: next copy, then objective and W
       __syncwarp();
       issue_copy(it + NHB * stride, cur);
-      colnorm2(w, r2);
-      float o = 0.f;
+      const float2 r2 = colsum(L, nb, w);
+      float o = sqrtf(r2.x) + sqrtf(r2.y);
 #pragma unroll
-      for (int s = 0; s < 8; ++s) o += sqrtf(r2[s][0]) + sqrtf(r2[s][1]);
-      o += __shfl_xor_sync(0xffffffffu, o, 1);
-      o += __shfl_xor_sync(0xffffffffu, o, 2);
+      for (int msk = 1; msk < 32; msk <<= 1) o += __shfl_xor_sync(0xffffffffu, o, msk);
 #pragma unroll
       for (int s = 0; s < 8; ++s)
         *reinterpret_cast<float4*>(A.W + w_off + L.g * MB + 8 * s + 2 * L.q) =
@@ -400,6 +665,7 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
         if (A.resid) A.resid[inst] = sqrtf(rs);
         if (A.flags) A.flags[inst] = fl;
       }
+      __syncwarp();  // norm partials read out before the next instance
     }
   }
 };

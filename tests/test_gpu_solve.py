@@ -328,6 +328,26 @@ def test_tensor_core_variant_flags_and_uneven(pc, orc):
     assert_parity((W[ok], obj[ok], res[ok], fl[ok]), oracle_ref(orc, 1, H[ok], t[ok], mu))
 
 
+def test_tensor_core_ill_conditioned_uses_fp64(pc, orc):
+    """K = 8, M = 64 with one almost collinear user pair in every other instance:
+    the tensor-core kernel's register Gauss-Jordan flags the pivot spread and the
+    FP64 setup forms Q instead; the rest keep the FP32 inverse and MMA-formed Q."""
+    capi, precoder = pc
+    rs = np.random.default_rng(6)
+    H = ch.rayleigh(16, 8, 64, seed=24)
+    for b in range(0, 16, 2):
+        H[b, 5] = H[b, 2] + (1e-3 * (rs.standard_normal(64) + 1j * rs.standard_normal(64))).astype(np.complex64)
+    t = ch.targets(16, 8)
+    mu = np.full(4, 0.02, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, cond_threshold=1e3, tensor_cores=True)
+    assert np.all(gpu[3][0::2] == capi.F_FP64_CHOL)
+    assert np.all(gpu[3][1::2] == 0)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    assert_parity(tuple(x[1::2] for x in gpu), tuple(x[1::2] for x in ref))
+    # the conditioning amplifies FP32 rounding of the layers themselves
+    assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
+
+
 def test_tensor_core_full_size_sampled(pc, orc):
     capi, precoder = pc
     wl = ch.WORKLOADS["fixed"]
