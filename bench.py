@@ -4,9 +4,10 @@ Workload (the headline): 65,536 independent channels H in C^{8x64} (K=8 users,
 M=64 antennas), CN(0,1) entries with 8 dB log-normal per-user gains, unit
 targets, T=10 projected layers with per-layer steps mu_t drawn once from
 U[0.01, 0.1] (seed 2).  One step = one pass of the whole hot path over the
-batch: channel load, Gram + equilibrated Cholesky + G^{-1} + ZF start, 10
-layers (shrink, residual, projection), objective, residual, W write-back.  It is
-one persistent kernel launch.  Inputs stay resident in HBM (268 MB of H, larger
+batch: channel load, Gram matrix, its equilibrated inverse, Q = G^{-T} H^* and
+the ZF start, 10 layers (shrink, residual, projection), objective, residual, W
+write-back.  It is one persistent kernel launch (the tensor-core kernel for
+K = 8, M = 64).  Inputs stay resident in HBM (268 MB of H, larger
 than the 129 MB L2; W is another 268 MB), so no L2 flush is needed between steps.
 
 Lines printed (rank 0, one JSON line):
@@ -14,7 +15,8 @@ Lines printed (rank 0, one JSON line):
   e2e        the same through precode_solve_host with pinned host buffers
              (host->device, solve, device->host inside the timed region)
   roofline   FP32 FMA-pipe roofline of the solve kernel (the path is
-             arithmetic-bound: ~86 flop per HBM byte)
+             arithmetic-bound: ~86 flop per HBM byte); on the tensor-core
+             kernel also the issued split-TF32 MMA rate against the TF32 peak
   cpu_baseline  the FP64 oracle on this host's cores, bounded sample
   pa_gap     relative PA-consumption (||W||_{2,1}) difference GPU vs oracle on
              that sample, and the mean PCG of the GPU output
@@ -53,6 +55,14 @@ def flops_per_instance(K: int, M: int, T: int, mode: int) -> float:
     per_layer = 2 * K * K * M
     setup = 0.0 if mode == 0 else K * K * M / 2 + K ** 3 / 6 + K * K * M
     return 8.0 * (T * per_layer + setup)
+
+
+def mma_per_instance(T: int) -> int:
+    """Warp MMAs (m16n8k8) the tensor-core kernel issues for one projected-layer
+    instance: 48 per 8 x 64 complex contraction (2 real-form blocks x 8 tiles x 3
+    split-TF32 terms), two per layer, plus the Gram matrix, Q and Q^T in the
+    setup and the final residual."""
+    return 96 * T + 48 + 96 + 48
 
 
 def fp32_peak_tflops() -> float:
@@ -305,7 +315,7 @@ def main():
     H = ch.lognormal(B, K, M, seed=wl.seed + 1000 * rank)
     t = ch.targets(B, K)
     mu = ch.fixed_workload_steps(T)
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=not args.no_autotune)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=not args.no_autotune, tensor_cores=True)
     Hd = torch.from_numpy(H).cuda()
     td = torch.from_numpy(t).cuda()
     md = torch.from_numpy(mu).cuda()
@@ -361,12 +371,22 @@ def main():
             "flop_per_instance": fpi,
             "hbm": {"achieved_gbs": hbm_bytes / (kern_ms / 1e3) / 1e9,
                     "peak_gbs": peaks.get("hbm_gbs"), "algorithmic_bytes": hbm_bytes}}
-    # DRAM traffic per launch from the committed ncu capture, if it was taken on
-    # the kernel variant that ran here
     plan_kernel_name = capi.precode_plan_describe(plan.handle, M, K)
     roof["kernel"] = plan_kernel_name
-    prof = os.path.join(ROOT, "profiles", "solve_proj_k8_m64_fixed.traffic.txt")
-    if os.path.exists(prof):
+    if plan_kernel_name.startswith("solve_tc_kernel"):
+        # the contractions run on the tensor cores as split TF32 (three MMAs per
+        # FP32-accurate product): issued MMA work against the TF32 dense peak
+        # (the measured bf16 peak times the nominal TF32 / bf16 ratio 1.1 / 2.25)
+        mma = mma_per_instance(T)
+        issued = mma * 2 * 16 * 8 * 8 * B / (kern_ms / 1e3) / 1e12
+        tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        roof["tensor"] = {"mma_m16n8k8_per_instance": mma, "issued_tflops": issued,
+                          "peak_tf32_tflops": tf32_peak, "frac": issued / tf32_peak,
+                          "peak_source": "of measured: bf16_tflops x 1.1 / 2.25"}
+    # DRAM traffic per launch from a committed ncu capture, if one was taken on
+    # the kernel variant that ran here
+    import glob
+    for prof in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.traffic.txt"))):
         kv = dict(line.split(": ", 1) for line in open(prof).read().splitlines() if ": " in line)
         if kv.get("kernel", "").strip() == plan_kernel_name:
             roof["traffic"] = int(kv["traffic_bytes_per_launch"])

@@ -11,10 +11,8 @@ void register_solve_tc(std::vector<Variant>& v) {
                       SolveTC<MODE, NW, DB>::SMEM_BYTES, NW * 32,                       \
                       SolveTC<MODE, NW, DB>::C::GROUPS, true});
   X(kModeProj, 4, 3, false)
-  X(kModeProj, 2, 6, false)
   X(kModeProj, 4, 3, true)
   X(kModePGD, 4, 3, false)
-  X(kModePGD, 2, 6, false)
   X(kModePGD, 4, 3, true)
 #undef X
 }
