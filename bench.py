@@ -174,14 +174,13 @@ def cpu_baseline(H, t, mu, budget_s: float = 10.0):
 
 def bench_uneven(torch, capi, Plan, inst_table):
     """Uneven workload: 32,768 instances, (M, K) uniform over the four buckets,
-    Rician channels, T = 10, one CUDA-graph launch (bucketing + one solve per bucket)."""
+    Rician channels, T = 10, one CUDA-graph launch (bucketing + one solve per bucket).
+    Also each bucket alone (a uniform solve of its instances) with its FP32 roofline
+    fraction."""
     B, T = 32768, 10
     shapes = ch.uneven_shapes(B, seed=3)
-    sizes = shapes[:, 0].astype(np.int64) * shapes[:, 1]
-    h_off = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    pool, h_off = ch.uneven_channels(shapes, seed=3)
     t_off = np.concatenate([[0], np.cumsum(shapes[:, 1])[:-1]]).astype(np.int64)
-    # one Rician pool; instance b views its K*M values (inputs only shape the timing)
-    pool = ch.rician_ula(1, 1, int(sizes.sum()), seed=3)[0, 0]
     Hd = torch.from_numpy(pool).cuda()
     td = torch.ones(int(shapes[:, 1].sum()), device="cuda")
     mu = torch.from_numpy(ch.uniform_steps(T, 0.01, 0.1, seed=2)).cuda()
@@ -189,24 +188,46 @@ def bench_uneven(torch, capi, Plan, inst_table):
                 autotune=True)
     tbl = inst_table(h_off, h_off, t_off, shapes[:, 0], shapes[:, 1]).cuda()
     W = torch.empty_like(Hd)
-    for _ in range(3):
-        plan.solve_varlen(tbl, Hd, td, mu, W=W)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    e0.record()
-    for _ in range(reps):
-        plan.solve_varlen(tbl, Hd, td, mu, W=W)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    per = {}
-    for (M, K) in ch.UNEVEN_SHAPES:
-        per[f"{M}x{K}"] = int(((shapes[:, 0] == M) & (shapes[:, 1] == K)).sum())
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: plan.solve_varlen(tbl, Hd, td, mu, W=W))
+    fl = plan.solve_varlen(tbl, Hd, td, mu, W=W)[3]
+    fp64 = int(((fl.cpu().numpy() & capi.F_FP64_CHOL) != 0).sum())
     plan.close()
+    peak = fp32_peak_tflops()
+    per, flops_total = {}, 0.0
+    for (M, K) in ch.UNEVEN_SHAPES:
+        idx = np.nonzero((shapes[:, 0] == M) & (shapes[:, 1] == K))[0]
+        n = len(idx)
+        Hb = torch.from_numpy(pool[h_off[idx][:, None] + np.arange(K * M)[None, :]]
+                              .reshape(n, K, M)).cuda()
+        tb = torch.ones(n, K, device="cuda")
+        pb = Plan(capi.LAYER_PROJ, T, [(M, K)], n, autotune=True, tensor_cores=True)
+        out = (torch.empty_like(Hb), torch.empty(n, device="cuda"), None,
+               torch.empty(n, device="cuda", dtype=torch.int32))
+        msb = timed(lambda: pb.solve(Hb, tb, mu, out=out))
+        fpi = flops_per_instance(K, M, T, 1)
+        flops_total += fpi * n
+        per[f"{M}x{K}"] = {"instances": n, "precoders_per_s": n / (msb / 1e3), "ms": msb,
+                           "fp32_roofline_frac": fpi * n / (msb / 1e3) / 1e12 / peak,
+                           "kernel": capi.precode_plan_describe(pb.handle, M, K)}
+        pb.close()
     return {"workload": "uneven: 32,768 instances, (M,K) uniform over (32,4),(64,8),(128,16),"
-                        "(256,32), Rician ULA, T=10, one CUDA graph per call",
-            "precoders_per_s": B / (ms / 1e3), "ms_per_call": ms, "instances_per_bucket": per}
+                        "(256,32), Rician ULA per instance, T=10, one CUDA graph per call",
+            "precoders_per_s": B / (ms / 1e3), "ms_per_call": ms,
+            "fp32_roofline_frac": flops_total / (ms / 1e3) / 1e12 / peak,
+            "fp64_fallbacks": fp64, "buckets": per}
 
 
 def bench_train(torch, capi):

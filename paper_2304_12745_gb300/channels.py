@@ -119,6 +119,25 @@ def uneven_shapes(B: int, seed: int) -> np.ndarray:
     return np.asarray(UNEVEN_SHAPES, dtype=np.int32)[idx]
 
 
+def uneven_channels(shapes: np.ndarray, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Rician ULA channels for an uneven batch, packed instance after instance.
+
+    Returns (pool, h_off): pool is complex64 holding instance b's K x M channel at
+    element offset h_off[b]; each bucket's instances are drawn together with
+    ``rician_ula`` (seed + bucket index)."""
+    shapes = np.asarray(shapes)
+    sizes = shapes[:, 0].astype(np.int64) * shapes[:, 1]
+    h_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    pool = np.empty(int(sizes.sum()), dtype=np.complex64)
+    for i, (M, K) in enumerate(UNEVEN_SHAPES):
+        idx = np.nonzero((shapes[:, 0] == M) & (shapes[:, 1] == K))[0]
+        if len(idx) == 0:
+            continue
+        Hb = rician_ula(len(idx), K, M, seed + i).reshape(len(idx), K * M)
+        pool[h_off[idx][:, None] + np.arange(K * M)[None, :]] = Hb
+    return pool, h_off
+
+
 def fixed_workload_steps(T: int = 10) -> np.ndarray:
     return uniform_steps(T, 0.01, 0.1, seed=2)
 

@@ -312,8 +312,12 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
   DeviceGuard g(p->device);
   cudaError_t e;
   const size_t n = (size_t)K * M;
-  // chunk: at least 8 waves of work per chunk boundary, at most 8 chunks
-  int64_t chunk = std::max<int64_t>(std::min<int64_t>(B, 8192), (B + 7) / 8);
+  // Chunks rotate over kPipe streams, each stream running copy in -> solve ->
+  // copy out for its chunks, so the copy in of chunk c + 1, the solve of chunk c
+  // and the copy out of chunk c - 1 overlap (the host link is the bound: both
+  // copy directions together are slower than the solve).  At most 16 chunks, at
+  // least 4,096 instances each.
+  int64_t chunk = std::max<int64_t>(std::min<int64_t>(B, 4096), (B + 15) / 16);
   if (!p->dparams) {
     e = cudaMalloc(&p->dparams, sizeof(float) * 2 * p->T);
     if (e != cudaSuccess) return fail(PRECODE_ENOMEM, "precode_solve_host: params buffer");

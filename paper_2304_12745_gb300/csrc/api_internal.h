@@ -69,8 +69,8 @@ struct precode_plan_s {
   uint32_t flags = 0;
   unsigned long long* d_err = nullptr;
   // host-buffer pipeline
-  static constexpr int kPipe = 2;
-  cudaStream_t hstream[kPipe] = {nullptr, nullptr};
+  static constexpr int kPipe = 4;
+  cudaStream_t hstream[kPipe] = {};
   int64_t chunk = 0;
   size_t chunk_elems = 0;  // complex elements per chunk buffer
   void* dH[kPipe] = {};
