@@ -88,7 +88,7 @@ typedef enum {
                                            first precode_solve_varlen call and re-armed with
                                            new arguments on later calls */
 
-#define PRECODE_PLAN_TENSOR_CORES 8u    /* for shapes with a tensor-core build (K=8, M=64) use it:
+#define PRECODE_PLAN_TENSOR_CORES 8u    /* for shapes with a tensor-core build (8x64, 16x128, 32x256) use it:
                                            contractions as warp MMAs on TF32 operands split
                                            in three terms (products accurate to ~2^-21 rel.) */
 

@@ -33,6 +33,7 @@ const std::vector<Variant>& variants() {
     register_solve_pgd(r);
     register_solve_proj(r);
     register_solve_tc(r);
+    register_solve_tcw(r);
     return r;
   }();
   return v;
@@ -402,9 +403,11 @@ precode_status_t precode_plan_describe(precode_plan_t p, int32_t M, int32_t K, c
   if (!p || !buf || len == 0) return fail(PRECODE_EINVAL, "precode_plan_describe: bad argument");
   const Variant* v = p->variant_for(M, K);
   if (!v) return fail(PRECODE_EINVAL, "precode_plan_describe: shape not covered by the plan");
-  if (v->tc)
+  if (v->tc && v->KB == 8)
     std::snprintf(buf, len, "solve_tc_kernel<%d, %d, %d, %d>", v->mode, v->NW, v->minb,
                   v->db ? 1 : 0);
+  else if (v->tc)
+    std::snprintf(buf, len, "solve_tcw_kernel<%d, %d, %d>", v->mode, v->NW, v->minb);
   else
     std::snprintf(buf, len, "solve_kernel<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v->mode,
                   v->KB, v->MB, v->GK, v->GM, v->JC, v->exact ? 1 : 0, v->NW, v->minb,

@@ -21,7 +21,7 @@ struct Variant {
   int smem;      // dynamic shared memory per block (bytes)
   int threads;   // threads per block
   int groups;    // instances resident per block
-  bool tc;       // contractions on the tensor cores (warp MMA, split TF32), K=8/M=64 only
+  bool tc;       // contractions on the tensor cores (warp MMA, split TF32); exact M = 8K shapes
 };
 
 struct TrainVariant {
@@ -40,6 +40,7 @@ void register_train_proj(std::vector<TrainVariant>& v);
 const std::vector<TrainVariant>& train_variants();
 void register_solve_proj(std::vector<Variant>& v);
 void register_solve_tc(std::vector<Variant>& v);
+void register_solve_tcw(std::vector<Variant>& v);
 const std::vector<Variant>& variants();
 
 }  // namespace precode

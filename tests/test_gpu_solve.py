@@ -348,6 +348,54 @@ def test_tensor_core_ill_conditioned_uses_fp64(pc, orc):
     assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
 
 
+@pytest.mark.parametrize("K,M,B", [(16, 128, 2600), (32, 256, 700)])
+@pytest.mark.parametrize("mode", ["proj", "pgd"])
+def test_tensor_core_large_buckets(pc, orc, K, M, B, mode):
+    """Multi-warp tensor-core build (one CTA of K/8 warps per instance) against the
+    oracle, over more instances than one persistent round, so CTAs take a ragged
+    number of instances."""
+    capi, precoder = pc
+    if mode == "proj":
+        H = ch.rician_ula(B, K, M, seed=5)
+        t = ch.targets(B, K)
+        step, lam, m = ch.uniform_steps(10, 0.01, 0.1, seed=7), None, capi.LAYER_PROJ
+    else:
+        H = ch.rayleigh(B, K, M, seed=9)
+        t = ch.targets(B, K, gamma_db=10.0)
+        L = 1 / ch.paper_eta(K, M)
+        step = np.linspace(1 / L, 1 / (2 * L), 10).astype(np.float32)
+        lam, m = np.full(10, 1 / 15, np.float32), capi.LAYER_PGD
+    gpu = run_gpu(precoder, m, H, t, step, lam, tensor_cores=True)
+    ref = oracle_ref(orc, 1 if mode == "proj" else 0, H, t, step, lam)
+    assert_parity(gpu, ref)
+
+
+def test_tensor_core_large_flags_and_fp64(pc, orc):
+    """32 x 256 on the multi-warp build: a singular Gram matrix, a non-finite
+    input and near-collinear user pairs (FP64 Gauss-Jordan path)."""
+    capi, precoder = pc
+    rs = np.random.default_rng(8)
+    H = ch.rayleigh(24, 32, 256, seed=25)
+    H[3, 7] = H[3, 2]
+    H[5, 0, 9] = np.nan
+    for b in range(8, 24, 2):
+        H[b, 20] = H[b, 11] + (1e-3 * (rs.standard_normal(256) + 1j * rs.standard_normal(256))).astype(np.complex64)
+    t = ch.targets(24, 32)
+    mu = np.full(4, 0.02, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, cond_threshold=1e3, tensor_cores=True)
+    W, obj, res, fl = gpu
+    assert fl[3] & capi.F_SINGULAR and fl[3] & capi.F_FP64_CHOL and not np.any(W[3])
+    assert fl[5] & capi.F_NONFINITE
+    fb = list(range(8, 24, 2))
+    assert np.all(fl[fb] == capi.F_FP64_CHOL)
+    ok = [b for b in range(24) if b not in (3, 5) and b not in fb]
+    assert np.all(fl[ok] == 0)
+    assert_parity(tuple(x[ok] for x in gpu), oracle_ref(orc, 1, H[ok], t[ok], mu))
+    # the conditioning amplifies FP32 rounding of the layers themselves
+    assert_parity(tuple(x[fb] for x in gpu), oracle_ref(orc, 1, H[fb], t[fb], mu),
+                  w_tol=2e-3, obj_tol=2e-4)
+
+
 def test_tensor_core_full_size_sampled(pc, orc):
     capi, precoder = pc
     wl = ch.WORKLOADS["fixed"]
