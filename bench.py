@@ -260,8 +260,11 @@ def bench_serve(capi, mu, duration_s: float = 2.0):
     """Serving workload: Poisson arrivals at 2,000 jobs/s, M in {64,128,256},
     K in {4..32}, N_sc in {64,...,1024}, Rician, T = 10 with the learned steps."""
     from paper_2304_12745_gb300.serving import Server, poisson_load
-    s = Server(capi.LAYER_PROJ, mu, shapes=[tuple(x) for x in ch.UNEVEN_SHAPES], n_slots=6,
-               max_batch_instances=65536, device_mem_budget=24 << 30)
+    # buckets: every job shape (M in {64,128,256}, any K <= 32) fits a user-padded
+    # tensor-core bucket of 8, 16, 24 or 32 users
+    shapes = [(m, k) for m in (64, 128, 256) for k in (8, 16, 24, 32)]
+    s = Server(capi.LAYER_PROJ, mu, shapes=shapes, n_slots=6, max_batch_instances=65536,
+               device_mem_budget=24 << 30, flags=capi.PLAN_TENSOR_CORES)
     poisson_load(s, 500.0, 0.2, seed=11)  # warm-up
     st = poisson_load(s, 2000.0, duration_s, seed=12)
     s.close()

@@ -33,7 +33,9 @@ const std::vector<Variant>& variants() {
     register_solve_pgd(r);
     register_solve_proj(r);
     register_solve_tc(r);
-    register_solve_tcw(r);
+    register_solve_tcw_64(r);
+    register_solve_tcw_128(r);
+    register_solve_tcw_256(r);
     return r;
   }();
   return v;
@@ -63,17 +65,23 @@ int variant_occupancy(const Variant& v, int device) {
   return c[idx];
 }
 
-// Default choice: the first exact variant of (mode, K, M), else the smallest
-// generic bucket that holds (K, M).
+// Default choice: with tensor cores, the exact tensor-core build of (mode, K, M),
+// else the smallest user-padded one with M antennas; then the first exact FP32
+// variant, else the smallest generic bucket that holds (K, M).
 const Variant* pick_variant(int mode, int M, int K, bool tensor_cores) {
   const Variant* best = nullptr;
-  if (tensor_cores)
+  if (tensor_cores) {
     for (const auto& v : variants())
-      if (v.tc && v.mode == mode && v.KB == K && v.MB == M) return &v;
+      if (v.tc && v.exact && v.mode == mode && variant_fits(v, M, K)) return &v;
+    for (const auto& v : variants())
+      if (v.tc && !v.exact && v.mode == mode && variant_fits(v, M, K) && (!best || v.KB < best->KB))
+        best = &v;
+    if (best) return best;
+  }
   for (const auto& v : variants())
-    if (v.mode == mode && v.exact && !v.tc && v.KB == K && v.MB == M) return &v;
+    if (v.mode == mode && v.exact && !v.tc && variant_fits(v, M, K)) return &v;
   for (const auto& v : variants()) {
-    if (v.mode != mode || v.exact || v.KB < K || v.MB < M) continue;
+    if (v.mode != mode || v.exact || v.tc || !variant_fits(v, M, K)) continue;
     if (!best || v.KB * v.MB < best->KB * best->MB) best = &v;
   }
   return best;
@@ -81,10 +89,8 @@ const Variant* pick_variant(int mode, int M, int K, bool tensor_cores) {
 
 std::vector<const Variant*> eligible_variants(int mode, int M, int K) {
   std::vector<const Variant*> r;
-  for (const auto& v : variants()) {
-    if (v.mode != mode) continue;
-    if (v.exact ? (v.KB == K && v.MB == M) : (v.KB >= K && v.MB >= M)) r.push_back(&v);
-  }
+  for (const auto& v : variants())
+    if (v.mode == mode && variant_fits(v, M, K)) r.push_back(&v);
   return r;
 }
 
@@ -126,25 +132,22 @@ using namespace precode;
 namespace precode {
 void plan_build_buckets(precode_plan_t p) {
   p->buckets.clear();
-  for (size_t i = 0; i < p->shapes.size(); ++i) {
-    bool dup = false;
-    for (const auto& b : p->buckets) dup |= (b.M == p->shapes[i].M && b.K == p->shapes[i].K);
-    if (!dup) p->buckets.push_back(Bucket{p->shapes[i].M, p->shapes[i].K, p->chosen[i]});
-  }
+  auto add = [&](int M, int K, const Variant* v) {
+    for (const auto& b : p->buckets)
+      if (b.v == v && (!v->exact || (b.M == M && b.K == K))) return;
+    p->buckets.push_back(Bucket{M, K, v});
+  };
+  for (size_t i = 0; i < p->shapes.size(); ++i) add(p->shapes[i].M, p->shapes[i].K, p->chosen[i]);
+  // Every bucket also gets the generic FP32 build of its (KB, MB), so any shape
+  // that fits the bucket has a kernel (a tensor-core build needs M == MB), and an
+  // exact tensor-core bucket its user-padded tensor-core build.
   const size_t n = p->buckets.size();
   for (size_t i = 0; i < n; ++i) {
     const Variant* v = p->buckets[i].v;
-    if (!v->exact) continue;
-    const Variant* gen = nullptr;
-    for (const auto& cand : variants())
-      if (cand.mode == p->mode && !cand.exact && cand.KB == v->KB && cand.MB == v->MB) {
-        gen = &cand;
-        break;
-      }
-    if (!gen) continue;
-    bool dup = false;
-    for (const auto& b : p->buckets) dup |= (b.v == gen);
-    if (!dup) p->buckets.push_back(Bucket{gen->MB, gen->KB, gen});
+    for (const auto& cand : variants()) {
+      if (cand.mode != p->mode || cand.exact || cand.KB != v->KB || cand.MB != v->MB) continue;
+      if (!cand.tc || (v->tc && v->exact)) add(cand.MB, cand.KB, &cand);
+    }
   }
 }
 }  // namespace precode
@@ -403,11 +406,11 @@ precode_status_t precode_plan_describe(precode_plan_t p, int32_t M, int32_t K, c
   if (!p || !buf || len == 0) return fail(PRECODE_EINVAL, "precode_plan_describe: bad argument");
   const Variant* v = p->variant_for(M, K);
   if (!v) return fail(PRECODE_EINVAL, "precode_plan_describe: shape not covered by the plan");
-  if (v->tc && v->KB == 8)
+  if (v->tc && v->exact && v->KB == 8 && v->MB == 64)
     std::snprintf(buf, len, "solve_tc_kernel<%d, %d, %d, %d>", v->mode, v->NW, v->minb,
                   v->db ? 1 : 0);
   else if (v->tc)
-    std::snprintf(buf, len, "solve_tcw_kernel<%d, %d, %d>", v->mode, v->NW, v->minb);
+    std::snprintf(buf, len, "solve_tcw_kernel<%d, %d, %d, %d>", v->mode, v->NW, v->MB, v->minb);
   else
     std::snprintf(buf, len, "solve_kernel<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v->mode,
                   v->KB, v->MB, v->GK, v->GM, v->JC, v->exact ? 1 : 0, v->NW, v->minb,

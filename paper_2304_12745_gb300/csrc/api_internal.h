@@ -87,11 +87,12 @@ struct precode_plan_s {
   const precode::Variant* variant_for(int M, int K) const {
     for (size_t i = 0; i < shapes.size(); ++i)
       if (shapes[i].M == M && shapes[i].K == K) return chosen[i];
+    // smallest bucket that fits; on a tie the tensor-core build (as bucketize_kernel)
     const precode::Variant* best = nullptr;
+    auto score = [](const precode::Variant* v) { return 2 * v->KB * v->MB - (v->tc ? 1 : 0); };
     for (const auto& bk : buckets) {
       const precode::Variant* v = bk.v;
-      if (!v->exact && v->KB >= K && v->MB >= M && (!best || v->KB * v->MB < best->KB * best->MB))
-        best = v;
+      if (!v->exact && precode::variant_fits(*v, M, K) && (!best || score(v) < score(best))) best = v;
     }
     return best;
   }

@@ -21,8 +21,16 @@ struct Variant {
   int smem;      // dynamic shared memory per block (bytes)
   int threads;   // threads per block
   int groups;    // instances resident per block
-  bool tc;       // contractions on the tensor cores (warp MMA, split TF32); exact M = 8K shapes
+  bool tc;       // contractions on the tensor cores (warp MMA, split TF32); a non-exact
+                 // tensor-core build pads users (K <= KB) but needs M == MB
 };
+
+// The instance shapes (M, K) a variant solves.
+inline bool variant_fits(const Variant& v, int M, int K) {
+  if (v.exact) return v.KB == K && v.MB == M;
+  if (v.tc) return v.KB >= K && v.MB == M;
+  return v.KB >= K && v.MB >= M;
+}
 
 struct TrainVariant {
   int mode;
@@ -40,7 +48,9 @@ void register_train_proj(std::vector<TrainVariant>& v);
 const std::vector<TrainVariant>& train_variants();
 void register_solve_proj(std::vector<Variant>& v);
 void register_solve_tc(std::vector<Variant>& v);
-void register_solve_tcw(std::vector<Variant>& v);
+void register_solve_tcw_64(std::vector<Variant>& v);
+void register_solve_tcw_128(std::vector<Variant>& v);
+void register_solve_tcw_256(std::vector<Variant>& v);
 const std::vector<Variant>& variants();
 
 }  // namespace precode

@@ -373,7 +373,8 @@ precode_status_t precode_serve_create(const precode_serve_desc_t* d, precode_ser
   pd.shapes = s->shapes.data();
   pd.max_instances = s->desc.max_batch_instances;
   pd.cond_threshold = d->cond_threshold;
-  pd.flags = d->flags & (PRECODE_PLAN_STEP_NORMALISED | PRECODE_PLAN_GRAPHS | PRECODE_PLAN_AUTOTUNE);
+  pd.flags = d->flags & (PRECODE_PLAN_STEP_NORMALISED | PRECODE_PLAN_GRAPHS | PRECODE_PLAN_AUTOTUNE |
+                         PRECODE_PLAN_TENSOR_CORES);
   pd.device = d->device;
   const int64_t cap = s->desc.max_batch_instances;
   for (int i = 0; i < s->desc.n_slots; ++i) {

@@ -1,6 +1,9 @@
-// Tensor-core solve kernel for the larger buckets, K = 8 KW users and M = 64 KW
-// antennas (KW = 2: 16 x 128, KW = 4: 32 x 256).  One CTA of KW warps works on
-// one instance at a time (persistent over instances).  Warp w owns users
+// Multi-warp tensor-core solve kernel for buckets of up to KB = 8 KW users and
+// exactly MB antennas (MB a multiple of 64).  One CTA of KW warps works on one
+// instance at a time (persistent over instances).  Instances with K < KB users
+// run padded: the missing channel rows are zero, their targets zero and their
+// Gram diagonal one, so their W rows stay exactly zero and the real users'
+// iteration is unchanged.  Warp w owns users
 // 8w .. 8w + 7 across all antennas; lane (g, q) = (lane / 4, lane % 4) holds user
 // 8w + g at antennas 8s + 2q + {0, 1} (s < M / 8) in the m16n8k8 accumulator
 // order (Re, Re, Im, Im), as in the K = 8 kernel, so both contractions take their
@@ -25,9 +28,10 @@
 
 namespace precode {
 
-template <int KW>
+template <int KW, int MB_>
 struct TcwCfg {
-  static constexpr int KB = 8 * KW, MB = 64 * KW, NS = MB / 8, NT = 32 * KW;
+  static constexpr int KB = 8 * KW, MB = MB_, NS = MB / 8, NT = 32 * KW;
+  static_assert(MB % 64 == 0, "8 antenna blocks per lane at least (the reduce-scatter halves them 3 times)");
   static constexpr int RSF = MB + 2;                      // channel row stride in float2 (+16 B)
   static constexpr int H_BYTES = KB * RSF * 8;
   static constexpr int E_BYTES = KB * KB * 8;             // Gram, then G^{-T} (float2, natural)
@@ -55,9 +59,9 @@ struct TcwCfg {
   static_assert((RSF * 8) % 16 == 0 && OFF_E % 16 == 0 && OFF_X % 16 == 0, "16-byte alignment");
 };
 
-template <int MODE, int KW>
+template <int MODE, int KW, int MB_>
 struct SolveTCW {
-  using C = TcwCfg<KW>;
+  using C = TcwCfg<KW, MB_>;
   static constexpr int KB = C::KB, MB = C::MB, NS = C::NS, NT = C::NT, RSF = C::RSF;
   static constexpr unsigned FULL = 0xffffffffu;
 
@@ -250,12 +254,46 @@ struct SolveTCW {
     }
   }
 
+  // NQ = NS / 4 consecutive floats per lane after the reduce-scatter: stored and
+  // loaded 16, 8 or 4 bytes at a time as NQ allows.
+  static constexpr int NQ = NS / 4;
+  __device__ __forceinline__ static void st_nq(float* dst, const float* v) {
+    if constexpr (NQ % 4 == 0) {
+#pragma unroll
+      for (int c = 0; c < NQ / 4; ++c)
+        *reinterpret_cast<float4*>(dst + 4 * c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NQ / 2; ++c)
+        *reinterpret_cast<float2*>(dst + 2 * c) = make_float2(v[2 * c], v[2 * c + 1]);
+    }
+  }
+  __device__ __forceinline__ static void add_nq(const float* src, float* r) {
+    if constexpr (NQ % 4 == 0) {
+#pragma unroll
+      for (int c = 0; c < NQ / 4; ++c) {
+        const float4 p = *reinterpret_cast<const float4*>(src + 4 * c);
+        r[4 * c] += p.x;
+        r[4 * c + 1] += p.y;
+        r[4 * c + 2] += p.z;
+        r[4 * c + 3] += p.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NQ / 2; ++c) {
+        const float2 p = *reinterpret_cast<const float2*>(src + 2 * c);
+        r[2 * c] += p.x;
+        r[2 * c + 1] += p.y;
+      }
+    }
+  }
+
   // Per-antenna sums over all K users of |W|^2.  Afterwards the lane holds the
   // totals r[j], j < NS / 4, of columns i0 + j (column i = 2s + h <-> antenna
   // 8s + 2q + h); returns i0.  par selects the partial buffer (alternating
   // between consecutive calls, so one barrier per call suffices).
   __device__ __forceinline__ static int colsum(const Lane& L, float* np, int par, const WT& w,
-                                               float (&r)[NS / 4]) {
+                                               float (&r)[NQ]) {
     float v[2 * NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -267,46 +305,26 @@ struct SolveTCW {
     rs_step<NS / 2>(v, b1, 8);
     rs_step<NS / 4>(v, b0, 4);
     const int i0 = b2 * NS + b1 * (NS / 2) + b0 * (NS / 4);
-    float* mine = np + ((par * KW + L.w) * 4 + L.q) * C::NPR + i0;
-#pragma unroll
-    for (int c = 0; c < NS / 16; ++c)
-      *reinterpret_cast<float4*>(mine + 4 * c) =
-          make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    st_nq(np + ((par * KW + L.w) * 4 + L.q) * C::NPR + i0, v);
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NS / 4; ++j) r[j] = 0.f;
+    for (int j = 0; j < NQ; ++j) r[j] = 0.f;
 #pragma unroll
-    for (int ww = 0; ww < KW; ++ww) {
-      const float* src = np + ((par * KW + ww) * 4 + L.q) * C::NPR + i0;
-#pragma unroll
-      for (int c = 0; c < NS / 16; ++c) {
-        const float4 p = *reinterpret_cast<const float4*>(src + 4 * c);
-        r[4 * c] += p.x;
-        r[4 * c + 1] += p.y;
-        r[4 * c + 2] += p.z;
-        r[4 * c + 3] += p.w;
-      }
-    }
+    for (int ww = 0; ww < KW; ++ww) add_nq(np + ((par * KW + ww) * 4 + L.q) * C::NPR + i0, r);
     return i0;
   }
 
   // Group soft threshold with tau on all antennas.
   __device__ __forceinline__ static void shrink(const Lane& L, float* np, float* fb, int par,
                                                 float tau, WT& w) {
-    float r[NS / 4];
+    float r[NQ];
     const int i0 = colsum(L, np, par, w, r);
     const float tau2 = tau * tau;
     float* fw = fb + (L.w * 4 + L.q) * C::NPR;
+    float f[NQ];
 #pragma unroll
-    for (int c = 0; c < NS / 16; ++c) {
-      float f[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float x = r[4 * c + k];
-        f[k] = (x > tau2) ? (1.f - tau * rsqrtf(x)) : 0.f;
-      }
-      *reinterpret_cast<float4*>(fw + i0 + 4 * c) = make_float4(f[0], f[1], f[2], f[3]);
-    }
+    for (int j = 0; j < NQ; ++j) f[j] = (r[j] > tau2) ? (1.f - tau * rsqrtf(r[j])) : 0.f;
+    st_nq(fw + i0, f);
     __syncwarp();
 #pragma unroll
     for (int c = 0; c < NS / 2; ++c) {
@@ -387,7 +405,7 @@ struct SolveTCW {
   // FP64 path: A = G^T from the raw channel in FP64, Gauss-Jordan in FP64 (no
   // equilibration; a pivot below 1e-12 of its Gram diagonal means rank(H) < K),
   // Es = G^{-T} rounded once.  Returns the instance flags.
-  __device__ static int gj_fp64(const Lane& L, const float2* Hs, float2* Es, double2* A,
+  __device__ static int gj_fp64(const Lane& L, int K, const float2* Hs, float2* Es, double2* A,
                                 double2* rowp, double2* colp, double* orig) {
     for (int idx = L.tid; idx < KB * KB; idx += NT) {
       const int i = idx / KB, j = idx % KB;
@@ -401,6 +419,8 @@ struct SolveTCW {
       A[i * KB + j] = make_double2(sr, si);
       A[j * KB + i] = make_double2(sr, -si);
     }
+    __syncthreads();
+    if (L.tid >= K && L.tid < KB) A[L.tid * KB + L.tid] = make_double2(1.0, 0.0);  // padded users
     __syncthreads();
     if (L.tid < KB) orig[L.tid] = A[L.tid * KB + L.tid].x;
     int fl = PRECODE_F_FP64_CHOL;
@@ -485,16 +505,19 @@ struct SolveTCW {
     uint32_t phase = 0;
     int par = 0;
     const int64_t n_inst = A.tbl ? (int64_t)(*A.count) : A.B;
-    auto locate = [&](int64_t it, int64_t& inst, int64_t& h_off, int64_t& w_off, int64_t& t_off) {
+    auto locate = [&](int64_t it, int64_t& inst, int64_t& h_off, int64_t& w_off, int64_t& t_off,
+                      int& K) {
       if (A.tbl) {
         inst = A.index[it];
         const InstDesc d = A.tbl[inst];
         h_off = d.h_off;
         w_off = d.w_off;
         t_off = d.t_off;
+        K = d.K;
       } else {
         inst = it;
-        h_off = it * (int64_t)(KB * MB);
+        K = A.K;
+        h_off = it * (int64_t)(K * MB);
         w_off = h_off;
         t_off = it * A.t_stride;
       }
@@ -503,18 +526,20 @@ struct SolveTCW {
     auto issue_copy = [&](int64_t it) {
       if (L.tid != 0 || it >= n_inst) return;
       int64_t inst, h_off, w_off, t_off;
-      locate(it, inst, h_off, w_off, t_off);
+      int K;
+      locate(it, inst, h_off, w_off, t_off, K);
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(bar, KB * MB * 8);
-      for (int k = 0; k < KB; ++k) bulk_g2s(Hs + k * RSF, A.H + h_off + k * MB, MB * 8, bar);
+      mbar_arrive_expect_tx(bar, K * MB * 8);
+      for (int k = 0; k < K; ++k) bulk_g2s(Hs + k * RSF, A.H + h_off + k * MB, MB * 8, bar);
     };
     issue_copy(blockIdx.x);
     WT w;
 #pragma unroll 1
     for (int64_t it = blockIdx.x; it < n_inst; it += gridDim.x) {
       int64_t inst, h_off, w_off, t_off;
-      locate(it, inst, h_off, w_off, t_off);
-      if (L.tid < KB) tks[L.tid] = A.t[t_off + L.tid];
+      int K;
+      locate(it, inst, h_off, w_off, t_off, K);
+      if (L.tid < KB) tks[L.tid] = L.tid < K ? A.t[t_off + L.tid] : 0.f;
       if (L.tid == 0) misc[0] = mbar_wait_bounded(bar, phase, kCopyWaitNs) ? 1 : 0;
       __syncthreads();
       if (misc[0] == 0) {
@@ -532,6 +557,11 @@ struct SolveTCW {
       }
       if (L.tid != 0) mbar_wait_bounded(bar, phase, kCopyWaitNs);  // completed: returns at once
       phase ^= 1u;
+      if (K < KB) {  // padded users: zero channel rows
+        for (int idx = L.tid; idx < (KB - K) * MB; idx += NT)
+          Hs[(K + idx / MB) * RSF + idx % MB] = make_float2(0.f, 0.f);
+        __syncthreads();
+      }
 
       // ---- setup
       int fl = 0;
@@ -546,11 +576,15 @@ struct SolveTCW {
           *reinterpret_cast<float4*>(row) = make_float4(e[0], e[2], e[1], e[3]);
         }
         __syncthreads();
+        if (MODE == kModeProj && K < KB) {  // padded users: unit Gram diagonal
+          if (L.tid >= K && L.tid < KB) Es[L.tid * KB + L.tid] = make_float2(1.f, 0.f);
+          __syncthreads();
+        }
       }
       bool singular = false;
       if constexpr (MODE == kModeProj) {
         if (!gj_fp32(L, Es, dsc, rowp, colp, A.cond_thr)) {
-          fl = gj_fp64(L, Hs, Es, A64, r64, c64, o64);
+          fl = gj_fp64(L, K, Hs, Es, A64, r64, c64, o64);
           singular = (fl & PRECODE_F_SINGULAR) != 0;
         }
         if (!singular) {
@@ -579,9 +613,9 @@ struct SolveTCW {
         }
       } else {
         if (A.opts & OPT_STEP_NORMALISED) {  // 1 / Gershgorin bound max_k sum_j |G_kj|
-          if (L.tid < KB) {
+          if (L.tid < K) {
             float sacc = 0.f;
-            for (int j = 0; j < KB; ++j) {
+            for (int j = 0; j < K; ++j) {
               const float2 v = Es[L.tid * KB + j];
               sacc += sqrtf(v.x * v.x + v.y * v.y);
             }
@@ -589,7 +623,7 @@ struct SolveTCW {
           }
           __syncthreads();
           float Lg = 0.f;
-          for (int k = 0; k < KB; ++k) Lg = fmaxf(Lg, dsc[k]);
+          for (int k = 0; k < K; ++k) Lg = fmaxf(Lg, dsc[k]);
           invL = 1.f / Lg;
         }
         const float2* hr = Hs + (8 * L.w + L.g) * RSF + 2 * L.q;  // W^(0) = conj(H)
@@ -639,20 +673,22 @@ struct SolveTCW {
 
       // ---- objective (column norms over all users), then the channel buffer is
       // free: next copy, W write-back, scalars
-      float r[NS / 4];
+      float r[NQ];
       colsum(L, np, par, w, r);
       par ^= 1;
       float o = 0.f;
 #pragma unroll
-      for (int j = 0; j < NS / 4; ++j) o += sqrtf(r[j]);
+      for (int j = 0; j < NQ; ++j) o += sqrtf(r[j]);
 #pragma unroll
       for (int msk = 1; msk < 32; msk <<= 1) o += __shfl_xor_sync(FULL, o, msk);
       __syncthreads();  // every warp is done with the channel and wred is complete
       issue_copy(it + gridDim.x);
-      float2* const Wg = A.W + w_off + (8 * L.w + L.g) * MB + 2 * L.q;
+      if (8 * L.w + L.g < K) {
+        float2* const Wg = A.W + w_off + (8 * L.w + L.g) * MB + 2 * L.q;
 #pragma unroll
-      for (int s = 0; s < NS; ++s)
-        *reinterpret_cast<float4*>(Wg + 8 * s) = make_float4(w[s][0], w[s][2], w[s][1], w[s][3]);
+        for (int s = 0; s < NS; ++s)
+          *reinterpret_cast<float4*>(Wg + 8 * s) = make_float4(w[s][0], w[s][2], w[s][1], w[s][3]);
+      }
       if (L.tid == 0) {
         float rs = 0.f;
         for (int k = 0; k < KW; ++k) rs += wred[k];
@@ -665,9 +701,9 @@ struct SolveTCW {
   }
 };
 
-template <int MODE, int KW, int MINB>
+template <int MODE, int KW, int MB, int MINB>
 __global__ void __launch_bounds__(KW * 32, MINB) solve_tcw_kernel(SolveArgs A) {
-  SolveTCW<MODE, KW>::run(A);
+  SolveTCW<MODE, KW, MB>::run(A);
 }
 
 }  // namespace precode

@@ -16,12 +16,13 @@ namespace precode {
 
 namespace {
 
-constexpr int kMaxBuckets = 16;
+constexpr int kMaxBuckets = 32;
 
 struct BucketTable {
   int n;
   int mode;
   int M[kMaxBuckets], K[kMaxBuckets], KB[kMaxBuckets], MB[kMaxBuckets], exact[kMaxBuckets];
+  int mfix[kMaxBuckets];  // non-exact bucket that needs M == MB (user-padded tensor-core build)
 };
 
 __global__ void bucketize_kernel(const InstDesc* __restrict__ tbl, int64_t B, BucketTable bt,
@@ -40,8 +41,10 @@ __global__ void bucketize_kernel(const InstDesc* __restrict__ tbl, int64_t B, Bu
       if (s < 0) {
         int best = 1 << 30;
         for (int i = 0; i < bt.n; ++i)
-          if (!bt.exact[i] && bt.KB[i] >= d.K && bt.MB[i] >= d.M && bt.KB[i] * bt.MB[i] < best) {
-            best = bt.KB[i] * bt.MB[i];
+          // smallest bucket; on a tie the tensor-core build (as the host's variant_for)
+          if (!bt.exact[i] && bt.KB[i] >= d.K && bt.MB[i] >= d.M && (!bt.mfix[i] || bt.MB[i] == d.M) &&
+              2 * bt.KB[i] * bt.MB[i] - bt.mfix[i] < best) {
+            best = 2 * bt.KB[i] * bt.MB[i] - bt.mfix[i];
             s = i;
           }
       }
@@ -90,6 +93,7 @@ void fill_args(precode_plan_t p, VarlenCall& call, const precode_inst_t* tbl, in
     call.bt.KB[i] = v->KB;
     call.bt.MB[i] = v->MB;
     call.bt.exact[i] = v->exact ? 1 : 0;
+    call.bt.mfix[i] = (!v->exact && v->tc) ? 1 : 0;
   }
   call.tbl = reinterpret_cast<const InstDesc*>(tbl);
   call.B = B;

@@ -162,7 +162,8 @@ extern "C" precode_status_t precode_solve_varlen_static(
   for (int i = 0; i < nshape_buckets; ++i) {
     if (!bv[i]->exact) continue;
     for (const auto& cand : variants())
-      if (cand.mode == d->mode && !cand.exact && cand.KB == bv[i]->KB && cand.MB == bv[i]->MB) {
+      if (cand.mode == d->mode && !cand.exact && !cand.tc && cand.KB == bv[i]->KB &&
+          cand.MB == bv[i]->MB) {
         if (!add(cand.MB, cand.KB, &cand))
           return fail(PRECODE_EINVAL,
                       "precode_solve_varlen_static: more than PRECODE_STATIC_MAX_BUCKETS = 8 buckets");

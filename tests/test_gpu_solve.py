@@ -370,6 +370,28 @@ def test_tensor_core_large_buckets(pc, orc, K, M, B, mode):
     assert_parity(gpu, ref)
 
 
+@pytest.mark.parametrize("K,M", [(5, 64), (13, 64), (27, 64), (3, 128), (20, 128), (9, 256), (27, 256)])
+def test_tensor_core_padded_users(pc, orc, K, M):
+    """User-padded tensor-core builds (K < KB users at exactly MB antennas): the
+    padded rows stay zero and the real users match the oracle."""
+    capi, precoder = pc
+    B = 200
+    H = ch.rician_ula(B, K, M, seed=30 + K)
+    t = ch.targets(B, K)
+    mu = ch.uniform_steps(10, 0.01, 0.1, seed=7)
+    plan = precoder.Plan(capi.LAYER_PROJ, 10, [(M, K)], B, tensor_cores=True)
+    assert capi.precode_plan_describe(plan.handle, M, K).startswith("solve_tcw_kernel")
+    plan.close()
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, tensor_cores=True)
+    ref = oracle_ref(orc, 1, H, t, mu)
+    ok = gpu[3] == 0
+    assert ok.sum() > B // 2
+    assert_parity(tuple(x[ok] for x in gpu), tuple(x[ok] for x in ref))
+    if np.any(~ok):  # FP64-path instances: conditioning amplifies the layers' FP32 rounding
+        assert np.all(gpu[3][~ok] == capi.F_FP64_CHOL)
+        assert_parity(tuple(x[~ok] for x in gpu), tuple(x[~ok] for x in ref), w_tol=2e-3, obj_tol=2e-4)
+
+
 def test_tensor_core_large_flags_and_fp64(pc, orc):
     """32 x 256 on the multi-warp build: a singular Gram matrix, a non-finite
     input and near-collinear user pairs (FP64 Gauss-Jordan path)."""

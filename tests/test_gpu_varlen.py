@@ -68,6 +68,52 @@ def test_uneven_batch_matches_uniform_and_oracle(orc, graphs):
     plan.close()
 
 
+def test_uneven_tensor_core_buckets_with_padded_users(orc):
+    """Serving-like shapes on a tensor-core plan: M in {64, 128, 256} with any K
+    (user-padded tensor-core buckets) plus shapes only the FP32 generic buckets
+    hold (M = 100).  Every instance equals the uniform solve of its shape and
+    matches the FP64 oracle."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan, inst_table
+    rs = np.random.default_rng(4)
+    B, T = 400, 10
+    M = rs.choice([64, 128, 256], B)
+    K = rs.integers(4, 33, B)
+    M[:12] = 100
+    shapes = np.stack([M, K], 1).astype(np.int32)
+    Hflat, h_off, t_off, nt = pack(shapes, seed=4)
+    tflat = np.ones(nt, np.float32)
+    mu = ch.uniform_steps(T, 0.01, 0.1, seed=2)
+    bucket_shapes = [(m, k) for m in (64, 128, 256) for k in (8, 16, 24, 32)]
+    plan = Plan(capi.LAYER_PROJ, T, bucket_shapes, B, graphs=True, tensor_cores=True)
+    tbl = inst_table(h_off, h_off, t_off, shapes[:, 0], shapes[:, 1]).cuda()
+    Hd = torch.from_numpy(Hflat).cuda()
+    td = torch.from_numpy(tflat).cuda()
+    md = torch.from_numpy(mu).cuda()
+    W, obj, res, fl = plan.solve_varlen(tbl, Hd, td, md)
+    torch.cuda.synchronize()
+    W, obj, fl = W.cpu().numpy(), obj.cpu().numpy(), fl.cpu().numpy()
+    assert np.all(fl[fl != 0] == capi.F_FP64_CHOL)
+    for (m, k) in {(int(a), int(b)) for a, b in shapes}:
+        idx = np.where((shapes[:, 0] == m) & (shapes[:, 1] == k))[0]
+        Hb = np.stack([Hflat[h_off[b]:h_off[b] + k * m].reshape(k, m) for b in idx])
+        Wo, oo, ro, so = orc.batch_forward(1, Hb.astype(np.complex128), np.ones((len(idx), k)),
+                                           mu.astype(np.float64), nthreads=8)
+        Wg = np.stack([W[h_off[b]:h_off[b] + k * m].reshape(k, m) for b in idx])
+        err = np.linalg.norm((Wg - Wo).reshape(len(idx), -1), axis=1) / np.linalg.norm(
+            Wo.reshape(len(idx), -1), axis=1)
+        tol = 2e-3 if np.any(fl[idx]) else 1e-4
+        assert err.max() <= tol, (m, k, err.max())
+        assert np.max(np.abs(obj[idx] - oo) / oo) <= (2e-4 if np.any(fl[idx]) else 1e-5), (m, k)
+        if m != 100:
+            pu = Plan(capi.LAYER_PROJ, T, [(m, k)], len(idx), tensor_cores=True)
+            Wu, ou, _, _ = pu.solve(torch.from_numpy(Hb).cuda(), torch.ones(k, device="cuda"), md)
+            assert np.array_equal(Wg, Wu.cpu().numpy()), (m, k)
+            assert capi.precode_plan_describe(pu.handle, m, k).startswith("solve_tc"), (m, k)
+            pu.close()
+    plan.close()
+
+
 def test_uneven_batch_rejects_bad_descriptors(orc):
     from paper_2304_12745_gb300 import capi
     from paper_2304_12745_gb300.precoder import Plan, inst_table
