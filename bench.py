@@ -265,7 +265,18 @@ def bench_serve(capi, mu, duration_s: float = 2.0):
     shapes = [(m, k) for m in (64, 128, 256) for k in (8, 16, 24, 32)]
     s = Server(capi.LAYER_PROJ, mu, shapes=shapes, n_slots=6, max_batch_instances=65536,
                device_mem_budget=24 << 30, flags=capi.PLAN_TENSOR_CORES)
-    poisson_load(s, 500.0, 0.2, seed=11)  # warm-up
+    # warm-up: one job per bucket (every kernel the load can use is loaded and its
+    # first launch done), then a short Poisson run
+    rng = np.random.default_rng(10)
+    warm = []
+    for m in (64, 128, 256):
+        for k in (4, 12, 20, 28, 8, 16, 24, 32):
+            H = ch.rician_ula(64, k, m, seed=int(rng.integers(1 << 30)))
+            warm.append(s.submit(H, np.ones(k, np.float32)))
+    for j in warm:
+        j.wait()
+    poisson_load(s, 500.0, 0.2, seed=11)
+    s.reset_stats()
     st = poisson_load(s, 2000.0, duration_s, seed=12)
     s.close()
     return {"workload": "serve: Poisson 2,000 jobs/s for %.1f s; M in {64,128,256}, K in {4..32}, "
@@ -273,6 +284,35 @@ def bench_serve(capi, mu, duration_s: float = 2.0):
             "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
             "precoders_per_s": st["precoders_per_s"], "jobs": st["jobs"],
             "achieved_jobs_per_s": st["achieved_rate_per_s"], "launches": st["launches"]}
+
+
+def run_bucket(args):
+    """One bucket alone (profiling aid): B Rician channels C^{K x M} (seed 5), T = 10
+    projected layers, autotuned plan; two solves, then one inside an NVTX range."""
+    import torch
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+    M, K = (int(x) for x in args.bucket.lower().split("x"))
+    B, T = args.bucket_instances, 10
+    H = torch.from_numpy(ch.rician_ula(B, K, M, seed=5)).cuda()
+    t = torch.ones(B, K, device="cuda")
+    mu = torch.from_numpy(ch.uniform_steps(T, 0.01, 0.1, seed=2)).cuda()
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=True)
+    out = (torch.empty_like(H), torch.empty(B, device="cuda"), None,
+           torch.empty(B, device="cuda", dtype=torch.int32))
+    for _ in range(2):
+        plan.solve(H, t, mu, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("prof")
+    e0.record()
+    plan.solve(H, t, mu, out=out)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"bucket": f"{M}x{K}", "instances": B, "ms": e0.elapsed_time(e1),
+                      "kernel": capi.precode_plan_describe(plan.handle, M, K)}))
+    plan.close()
 
 
 def run_reference(args, rank, world):
@@ -319,10 +359,16 @@ def main():
                     help="skip the uneven, training and serving sub-benchmarks")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default kernel variant (no tuning launches; for profiling)")
+    ap.add_argument("--bucket", default=None, metavar="MxK",
+                    help="profiling aid: solve one uniform bucket of Rician channels (autotuned "
+                         "plan), the last solve inside an NVTX range 'prof', print one line, exit")
+    ap.add_argument("--bucket-instances", type=int, default=4096)
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.bucket:
+        return run_bucket(args)
 
     import torch
     import torch.distributed as dist
