@@ -166,12 +166,15 @@ static void plan_free(precode_plan_t p) {
     if (p->hstream[i]) cudaStreamDestroy(p->hstream[i]);
     cudaFree(p->dH[i]);
     cudaFree(p->dW[i]);
-    cudaFree(p->dt[i]);
-    cudaFree(p->dobj[i]);
-    cudaFree(p->dres[i]);
-    cudaFree(p->dfl[i]);
+
   }
   cudaFree(p->dparams);
+  cudaFree(p->dt_all);
+  cudaFree(p->dobj_all);
+  cudaFree(p->dres_all);
+  cudaFree(p->dfl_all);
+  for (auto& ev : p->hev)
+    if (ev) cudaEventDestroy(ev);
   delete p;
 }
 
@@ -320,7 +323,9 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
   // copy out for its chunks, so the copy in of chunk c + 1, the solve of chunk c
   // and the copy out of chunk c - 1 overlap (the host link is the bound: both
   // copy directions together are slower than the solve).  At most 16 chunks, at
-  // least 4,096 instances each.
+  // least 4,096 instances each.  The targets go in, and the per-instance outputs
+  // come back, as one copy per call each (many small copies cost the copy
+  // engines more than their bytes).
   int64_t chunk = std::max<int64_t>(std::min<int64_t>(B, 4096), (B + 15) / 16);
   if (!p->dparams) {
     e = cudaMalloc(&p->dparams, sizeof(float) * 2 * p->T);
@@ -330,33 +335,53 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
     for (int i = 0; i < precode_plan_s::kPipe; ++i) {
       cudaFree(p->dH[i]);
       cudaFree(p->dW[i]);
-      cudaFree(p->dt[i]);
-      cudaFree(p->dobj[i]);
-      cudaFree(p->dres[i]);
-      cudaFree(p->dfl[i]);
       p->dH[i] = p->dW[i] = nullptr;
-      p->dt[i] = p->dobj[i] = p->dres[i] = nullptr;
-      p->dfl[i] = nullptr;
     }
     p->chunk = std::max<int64_t>(chunk, p->chunk);
     p->chunk_elems = std::max<size_t>((size_t)chunk * n, p->chunk_elems);
     for (int i = 0; i < precode_plan_s::kPipe; ++i) {
       if (cudaMalloc(&p->dH[i], p->chunk_elems * 8) != cudaSuccess ||
-          cudaMalloc(&p->dW[i], p->chunk_elems * 8) != cudaSuccess ||
-          cudaMalloc(&p->dt[i], (size_t)p->chunk * PRECODE_MAX_K * 4) != cudaSuccess ||
-          cudaMalloc(&p->dobj[i], (size_t)p->chunk * 4) != cudaSuccess ||
-          cudaMalloc(&p->dres[i], (size_t)p->chunk * 4) != cudaSuccess ||
-          cudaMalloc(&p->dfl[i], (size_t)p->chunk * 4) != cudaSuccess)
+          cudaMalloc(&p->dW[i], p->chunk_elems * 8) != cudaSuccess)
         return fail(PRECODE_ENOMEM, "precode_solve_host: staging buffers");
       if (!p->hstream[i] &&
           cudaStreamCreateWithFlags(&p->hstream[i], cudaStreamNonBlocking) != cudaSuccess)
         return fail(PRECODE_ECUDA, "precode_solve_host: stream");
     }
   }
+  for (auto& ev : p->hev)
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(PRECODE_ECUDA, "precode_solve_host: event");
+  const int64_t t_elems = t_stride ? B * t_stride : K;
+  if (t_elems > p->t_cap) {
+    cudaFree(p->dt_all);
+    p->dt_all = nullptr;
+    if (cudaMalloc(&p->dt_all, (size_t)t_elems * 4) != cudaSuccess)
+      return fail(PRECODE_ENOMEM, "precode_solve_host: target buffer");
+    p->t_cap = t_elems;
+  }
+  if (B > p->out_cap) {
+    cudaFree(p->dobj_all);
+    cudaFree(p->dres_all);
+    cudaFree(p->dfl_all);
+    p->dobj_all = p->dres_all = nullptr;
+    p->dfl_all = nullptr;
+    if (cudaMalloc(&p->dobj_all, (size_t)B * 4) != cudaSuccess ||
+        cudaMalloc(&p->dres_all, (size_t)B * 4) != cudaSuccess ||
+        cudaMalloc(&p->dfl_all, (size_t)B * 4) != cudaSuccess)
+      return fail(PRECODE_ENOMEM, "precode_solve_host: output buffers");
+    p->out_cap = B;
+  }
   e = cudaMemcpy(p->dparams, step, sizeof(float) * p->T, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && lam)
     e = cudaMemcpy(p->dparams + p->T, lam, sizeof(float) * p->T, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "precode_solve_host: params copy");
+  // targets once, on stream 0; the other streams wait for them
+  cudaStream_t S0 = p->hstream[0];
+  e = cudaMemcpyAsync(p->dt_all, t, (size_t)t_elems * 4, cudaMemcpyHostToDevice, S0);
+  if (e == cudaSuccess) e = cudaEventRecord(p->hev[precode_plan_s::kPipe], S0);
+  for (int i = 1; i < precode_plan_s::kPipe && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(p->hstream[i], p->hev[precode_plan_s::kPipe], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "precode_solve_host: targets copy");
   const char* Hc = static_cast<const char*>(H);
   char* Wc = static_cast<char*>(W);
   precode_status_t st = PRECODE_OK;
@@ -366,33 +391,35 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
     const int64_t nb = std::min<int64_t>(chunk, B - c0);
     e = cudaMemcpyAsync(p->dH[s], Hc + (size_t)c0 * n * 8, (size_t)nb * n * 8,
                         cudaMemcpyHostToDevice, S);
-    const size_t tbytes = t_stride ? (size_t)nb * t_stride * 4 : (size_t)K * 4;
-    const float* tsrc = t_stride ? t + (size_t)c0 * t_stride : t;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->dt[s], tsrc, tbytes, cudaMemcpyHostToDevice, S);
     if (e != cudaSuccess) {
       st = cuda_fail(e, "precode_solve_host: copy in");
       break;
     }
-    if (t_stride > PRECODE_MAX_K && (size_t)nb * t_stride > (size_t)p->chunk * PRECODE_MAX_K) {
-      st = fail(PRECODE_EINVAL, "precode_solve_host: t_stride too large for staging");
-      break;
-    }
-    st = precode_solve(p, M, K, nb, p->dH[s], p->dt[s], t_stride, p->dparams,
-                       lam ? p->dparams + p->T : nullptr, p->dW[s], obj ? p->dobj[s] : nullptr,
-                       resid ? p->dres[s] : nullptr, flags ? p->dfl[s] : nullptr, S);
+    st = precode_solve(p, M, K, nb, p->dH[s], t_stride ? p->dt_all + c0 * t_stride : p->dt_all,
+                       t_stride, p->dparams, lam ? p->dparams + p->T : nullptr, p->dW[s],
+                       obj ? p->dobj_all + c0 : nullptr, resid ? p->dres_all + c0 : nullptr,
+                       flags ? p->dfl_all + c0 : nullptr, S);
     if (st != PRECODE_OK) break;
     e = cudaMemcpyAsync(Wc + (size_t)c0 * n * 8, p->dW[s], (size_t)nb * n * 8,
                         cudaMemcpyDeviceToHost, S);
-    if (e == cudaSuccess && obj)
-      e = cudaMemcpyAsync(obj + c0, p->dobj[s], nb * 4, cudaMemcpyDeviceToHost, S);
-    if (e == cudaSuccess && resid)
-      e = cudaMemcpyAsync(resid + c0, p->dres[s], nb * 4, cudaMemcpyDeviceToHost, S);
-    if (e == cudaSuccess && flags)
-      e = cudaMemcpyAsync(flags + c0, p->dfl[s], nb * 4, cudaMemcpyDeviceToHost, S);
     if (e != cudaSuccess) {
       st = cuda_fail(e, "precode_solve_host: copy out");
       break;
     }
+  }
+  // per-instance outputs: stream 0 waits for every stream, then one copy each
+  if (st == PRECODE_OK) {
+    for (int i = 1; i < precode_plan_s::kPipe && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(p->hev[i], p->hstream[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(S0, p->hev[i], 0);
+    }
+    if (e == cudaSuccess && obj)
+      e = cudaMemcpyAsync(obj, p->dobj_all, (size_t)B * 4, cudaMemcpyDeviceToHost, S0);
+    if (e == cudaSuccess && resid)
+      e = cudaMemcpyAsync(resid, p->dres_all, (size_t)B * 4, cudaMemcpyDeviceToHost, S0);
+    if (e == cudaSuccess && flags)
+      e = cudaMemcpyAsync(flags, p->dfl_all, (size_t)B * 4, cudaMemcpyDeviceToHost, S0);
+    if (e != cudaSuccess) st = cuda_fail(e, "precode_solve_host: outputs copy");
   }
   for (int i = 0; i < precode_plan_s::kPipe; ++i) {
     e = cudaStreamSynchronize(p->hstream[i]);

@@ -75,10 +75,13 @@ struct precode_plan_s {
   size_t chunk_elems = 0;  // complex elements per chunk buffer
   void* dH[kPipe] = {};
   void* dW[kPipe] = {};
-  float* dt[kPipe] = {};
-  float* dobj[kPipe] = {};
-  float* dres[kPipe] = {};
-  int32_t* dfl[kPipe] = {};
+  // whole-batch targets and per-instance outputs (one copy each way per call)
+  int64_t out_cap = 0, t_cap = 0;
+  float* dt_all = nullptr;
+  float* dobj_all = nullptr;
+  float* dres_all = nullptr;
+  int32_t* dfl_all = nullptr;
+  cudaEvent_t hev[kPipe + 1] = {};
   float* dparams = nullptr;  // [2][T]
   std::mutex mu;
 
