@@ -20,6 +20,10 @@ Lines printed (rank 0, one JSON line):
   cpu_baseline  the FP64 oracle on this host's cores, bounded sample
   pa_gap     relative PA-consumption (||W||_{2,1}) difference GPU vs oracle on
              that sample, and the mean PCG of the GPU output
+  uneven / train / serving / paper_setting   the other workloads (skipped with
+             --no-extras): uneven buckets, learning the steps, Poisson serving, and
+             the paper's own setting (PGD 5000 iterations vs 20 unfolded layers;
+             per-layer PCG of PGD and of the two unfolded layer maps trained here)
   --impl reference runs the FP64 oracle alone (the CPU comparison arm).
 """
 from __future__ import annotations
@@ -254,6 +258,92 @@ def bench_train(torch, capi):
     return {"workload": "train: 200 Adam steps x 8,192 instances C^{8x64}, CN(0,1), T=10, lr 1e-3",
             "instances_per_s": Bt / (ms / 1e3), "ms_per_step": ms, "loss_first": first,
             "loss_last": last, "mu_learned": [float(x) for x in mu]}, mu
+
+
+def bench_paper_setting(torch, capi):
+    """The paper's own setting (Sec. VI): K = 8, M = 64, i.i.d. CN(0,1) channels,
+    gamma = 10 dB per user (t = sqrt(10), sigma_nu = 1).
+    speed:   the classical PGD of Sec. VI (5,000 iterations, constant eta = 1/L~,
+             lambda = 1/15) through the same paper-layer kernel, next to the 20-layer
+             unfolded network, 8,192 channels per call;
+    quality: PCG = ||W_ZF||_{2,1} / ||W||_{2,1} and the constraint residual
+             ||H W^T - S||_F / ||S||_F after each of the 20 layers, on 4,096 test
+             channels, for PGD (untrained), the unfolded paper layer trained here
+             (eta_t, lambda_t) and the unfolded projected layer trained here (mu_t):
+             Adam, lr 1e-3, 200 steps of 8,192 training channels, loss
+             ||W||_{2,1} + ||H W^T - S||_F^2."""
+    from paper_2304_12745_gb300.precoder import Plan
+    from paper_2304_12745_gb300.training import UnfoldedTrainer
+    K, M, T = 8, 64, 20
+    amp = math.sqrt(10.0)
+    eta = ch.paper_eta(K, M)
+    dev = "cuda"
+    tK = torch.full((K,), amp, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # speed: PGD 5,000 iterations vs the 20-layer network (same kernel, same batch)
+    Bs = 8192
+    Hs = torch.from_numpy(ch.rayleigh(Bs, K, M, seed=40)).cuda()
+    speed = {}
+    for name, TT in (("pgd_5000", 5000), ("unfolded_20", T)):
+        pl = Plan(capi.LAYER_PGD, TT, [(M, K)], Bs, tensor_cores=True)
+        st = torch.full((TT,), eta, device=dev)
+        lm = torch.full((TT,), 1.0 / 15, device=dev)
+        ms = timed(lambda: pl.solve(Hs, tK, st, lm), 2 if TT > 100 else 20)
+        speed[name] = {"ms_per_call": ms, "precoders_per_s": Bs / (ms / 1e3),
+                       "kernel": capi.precode_plan_describe(pl.handle, M, K)}
+        pl.close()
+    speed["ratio"] = speed["pgd_5000"]["ms_per_call"] / speed["unfolded_20"]["ms_per_call"]
+
+    # training
+    trained = {}
+    for name, mode in (("unfolded_paper_layer", capi.LAYER_PGD), ("unfolded_projected_layer",
+                                                                   capi.LAYER_PROJ)):
+        tr = UnfoldedTrainer(mode, T, K, M, 8192, a=1.0, lr=1e-3)
+        batches = [tr.make_batch(i, seed=5) for i in range(8)]
+        for i in range(200):
+            tr.train_step(batches[i % 8], tK)
+        trained[name] = (mode, tr.step.detach().clone(),
+                         None if tr.lam is None else tr.lam.detach().clone())
+        tr.plan.close()
+    trained["pgd"] = (capi.LAYER_PGD, torch.full((T,), eta, device=dev),
+                      torch.full((T,), 1.0 / 15, device=dev))
+
+    # quality per layer on test channels
+    Bt = 4096
+    Ht = torch.from_numpy(ch.rayleigh(Bt, K, M, seed=41)).cuda()
+    pz = Plan(capi.LAYER_PROJ, 1, [(M, K)], Bt, tensor_cores=True)
+    _, obj_zf, _, _ = pz.solve(Ht, tK, torch.zeros(1, device=dev))
+    pz.close()
+    s_norm = amp * math.sqrt(K)
+    quality = {}
+    for name, (mode, st, lm) in trained.items():
+        pcg, res = [], []
+        for TT in range(1, T + 1):
+            pl = Plan(mode, TT, [(M, K)], Bt, tensor_cores=True)
+            _, obj, rsd, _ = pl.solve(Ht, tK, st[:TT].contiguous(),
+                                      None if lm is None else lm[:TT].contiguous())
+            pcg.append(float((obj_zf / obj).mean()))
+            res.append(float(rsd.mean()) / s_norm)
+            pl.close()
+        quality[name] = {"pcg_per_layer": pcg, "rel_residual_per_layer": res,
+                         "steps": [float(x) for x in st.cpu()],
+                         "lambdas": None if lm is None else [float(x) for x in lm.cpu()]}
+    return {"workload": "paper setting: K=8, M=64, CN(0,1), gamma=10 dB; PGD 5000 it. vs 20 "
+                        "unfolded layers; per-layer PCG on 4,096 test channels",
+            "speed": speed, "quality": quality,
+            "paper_printed": {"pcg_unfolded_20": 1.0915, "pcg_cvx_optimum": 1.1160,
+                              "pcg_pgd_20": "about 1"}}
 
 
 def bench_serve(capi, mu, duration_s: float = 2.0):
@@ -518,6 +608,8 @@ def main():
         line["train"], mu_learned = bench_train(torch, capi)
         torch.cuda.empty_cache()
         line["serving"] = bench_serve(capi, mu_learned)
+        torch.cuda.empty_cache()
+        line["paper_setting"] = bench_paper_setting(torch, capi)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
