@@ -358,6 +358,162 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
     }
   }
 
+  // Per-instance setup from the raw channel in c.Hs (and the targets in c.tks):
+  // W^(0) into w, the update's B fragments into xf, H's hi / lo parts (PRE, in
+  // place of the raw channel and into hlo); with xraw, also the raw conj(H) B
+  // fragments of the update layout, (Re X[2q][8nt+g], Re X[2q+1][8nt+g],
+  // Im X[2q][8nt+g], Im X[2q+1][8nt+g]) at [nt][lane].  Returns the instance
+  // flags; invL: the paper layer's step normalisation.
+  __device__ static int setup(Ctx& c, const Lane& L, const SolveArgs& A, float4* xf, float4* hlo,
+                              WT& w, float& invL, float4* xraw) {
+    float e[4];
+    // ---- setup: lane's own conj(H) entries (user g, antennas 8s + 2q + h)
+    int fl = 0;
+    invL = 1.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float4 hv = *reinterpret_cast<const float4*>(c.Hs + L.g * MB + 8 * s + 2 * L.q);
+      w[s][0] = hv.x;
+      w[s][1] = hv.z;
+      w[s][2] = -hv.y;
+      w[s][3] = -hv.w;
+    }
+    bool fast = true;  // projected layer: FP32 register inverse and MMA-formed Q
+    if constexpr (MODE == kModeProj) {
+      residual<false>(L, c.Hs, nullptr, nullptr, w, c.tks, false, e);  // conj(H) H^T = G^T
+      float gi[4];
+      fast = gram_inverse(L, e, A.cond_thr, gi);
+      if (fast) {
+        // xf lies outside the raw channel, which the other lanes still read
+        q_mma(L, c.Hs, gi, c.tks[L.g], xf, w);
+      } else {
+        fl = Base::fp64_inverse(c);  // G^{-1} in FP64 into the reduction buffer
+        if (!(fl & PRECODE_F_SINGULAR)) {
+          // Q = conj(G^{-1} H) in FP64, rounded once, into Qs (natural); one entry
+          // at a time keeps this rare path light on registers
+          const double2* Gi = reinterpret_cast<const double2*>(c.red);
+#pragma unroll 1
+          for (int idx = L.lane; idx < KB * MB; idx += 32) {
+            const int k = idx / MB, m = idx - k * MB;
+            double zr = 0.0, zi = 0.0;
+#pragma unroll
+            for (int l = 0; l < KB; ++l) {
+              const double2 gkl = Gi[k * KB + l];
+              const float2 x = c.Hs[l * MB + m];
+              zr += gkl.x * x.x - gkl.y * x.y;
+              zi += gkl.x * x.y + gkl.y * x.x;
+            }
+            c.Qs[idx] = make_float2((float)zr, (float)-zi);
+          }
+          __syncwarp();
+        }
+      }
+    } else if (A.opts & OPT_STEP_NORMALISED) {
+      residual<false>(L, c.Hs, nullptr, nullptr, w, c.tks, false, e);  // conj(H) H^T = G^T
+      *reinterpret_cast<float4*>(c.Es + L.g * KB + 2 * L.q) = make_float4(e[0], e[2], e[1], e[3]);
+      __syncwarp();
+      invL = Base::inv_gershgorin(c);
+    }
+    const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
+    // ---- phase change: the layer buffers overwrite the setup buffers, so each
+    // operand is read out (into registers) before its area is reused.
+    {
+      float4* const hh = reinterpret_cast<float4*>(c.Hs);
+      // update fragments X[2q][8nt+g], X[2q+1][8nt+g], split into xf
+      auto put_x = [&](int nt, float2 x0, float2 x1, float csign) {
+        uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+        split_tf32(x0.x, h0, l0);
+        split_tf32(x1.x, h1, l1);
+        split_tf32(csign * x0.y, h2, l2);
+        split_tf32(csign * x1.y, h3, l3);
+        xf[(nt * 2 + 0) * 32 + L.lane] = make_float4(__uint_as_float(h0), __uint_as_float(h1),
+                                                     __uint_as_float(h2), __uint_as_float(h3));
+        xf[(nt * 2 + 1) * 32 + L.lane] = make_float4(__uint_as_float(l0), __uint_as_float(l1),
+                                                     __uint_as_float(l2), __uint_as_float(l3));
+      };
+      // H hi parts in place of the raw channel, lo parts beside them, from the
+      // lane's own entries v[s] = (Re, Re, Im, Im) at antennas 8s + 2q + {0, 1}
+      auto put_h = [&](const float (&v)[8][4]) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+          split_tf32(v[s][0], h0, l0);
+          split_tf32(v[s][1], h1, l1);
+          split_tf32(v[s][2], h2, l2);
+          split_tf32(v[s][3], h3, l3);
+          hh[s * 32 + L.lane] = make_float4(__uint_as_float(h0), __uint_as_float(h1),
+                                            __uint_as_float(h2), __uint_as_float(h3));
+          hlo[s * 32 + L.lane] = make_float4(__uint_as_float(l0), __uint_as_float(l1),
+                                             __uint_as_float(l2), __uint_as_float(l3));
+        }
+      };
+      if constexpr (MODE == kModePGD) {
+        // X = conj(H) from the raw channel; xf lies outside it
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+          put_x(nt, c.Hs[(2 * L.q) * MB + 8 * nt + L.g], c.Hs[(2 * L.q + 1) * MB + 8 * nt + L.g], -1.f);
+        if constexpr (PRE) {
+          __syncwarp();
+          float v[8][4];  // w = conj(H) = W^(0) stays live
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            v[s][0] = w[s][0];
+            v[s][1] = w[s][1];
+            v[s][2] = -w[s][2];
+            v[s][3] = -w[s][3];
+          }
+          put_h(v);
+        }
+      } else {
+        // H re-read from the raw channel (w is rebuilt from Q below); all lanes
+        // read before any overwrites it
+        if constexpr (PRE) {
+          float v[8][4];
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const float4 hv = *reinterpret_cast<const float4*>(c.Hs + L.g * MB + 8 * s + 2 * L.q);
+            v[s][0] = hv.x;
+            v[s][1] = hv.z;
+            v[s][2] = hv.y;
+            v[s][3] = hv.w;
+          }
+          __syncwarp();
+          put_h(v);
+        }
+        if (!fast) {
+          // X = Q from the FP64 path: tiles 4..7 of xf lie in the Gauss-Jordan
+          // area, tiles 0..3 over Q
+          const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int nt = 4; nt < 8; ++nt)
+            put_x(nt, singular ? z : c.Qs[(2 * L.q) * MB + 8 * nt + L.g],
+                  singular ? z : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g], 1.f);
+          const float tg = c.tks[L.g];  // W^(0) = S Q
+#pragma unroll
+          for (int s = 0; s < 8; ++s) {
+            const float4 qv = singular ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                       : *reinterpret_cast<const float4*>(c.Qs + L.g * MB + 8 * s + 2 * L.q);
+            w[s][0] = tg * qv.x;
+            w[s][1] = tg * qv.z;
+            w[s][2] = tg * qv.y;
+            w[s][3] = tg * qv.w;
+          }
+          float2 x0[4], x1[4];
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            x0[nt] = singular ? z : c.Qs[(2 * L.q) * MB + 8 * nt + L.g];
+            x1[nt] = singular ? z : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+          }
+          __syncwarp();
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) put_x(nt, x0[nt], x1[nt], 1.f);
+        }
+      }
+    }
+    __syncwarp();
+    return fl;
+  }
+
   __device__ static void run(const SolveArgs& A) {
     extern __shared__ __align__(16) unsigned char smem[];
     Ctx c;
@@ -452,150 +608,10 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       if (c.g != 0) mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs);
       phases ^= 1u << cur;
 
-      // ---- setup: lane's own conj(H) entries (user g, antennas 8s + 2q + h)
-      int fl = 0;
-      float invL = 1.f;
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const float4 hv = *reinterpret_cast<const float4*>(c.Hs + L.g * MB + 8 * s + 2 * L.q);
-        w[s][0] = hv.x;
-        w[s][1] = hv.z;
-        w[s][2] = -hv.y;
-        w[s][3] = -hv.w;
-      }
-      bool fast = true;  // projected layer: FP32 register inverse and MMA-formed Q
-      if constexpr (MODE == kModeProj) {
-        residual<false>(L, c.Hs, nullptr, nullptr, w, c.tks, false, e);  // conj(H) H^T = G^T
-        float gi[4];
-        fast = gram_inverse(L, e, A.cond_thr, gi);
-        if (fast) {
-          // xf lies outside the raw channel, which the other lanes still read
-          q_mma(L, c.Hs, gi, c.tks[L.g], xf, w);
-        } else {
-          fl = Base::fp64_inverse(c);  // G^{-1} in FP64 into the reduction buffer
-          if (!(fl & PRECODE_F_SINGULAR)) {
-            // Q = conj(G^{-1} H) in FP64, rounded once, into Qs (natural); one entry
-            // at a time keeps this rare path light on registers
-            const double2* Gi = reinterpret_cast<const double2*>(c.red);
-#pragma unroll 1
-            for (int idx = L.lane; idx < KB * MB; idx += 32) {
-              const int k = idx / MB, m = idx - k * MB;
-              double zr = 0.0, zi = 0.0;
-#pragma unroll
-              for (int l = 0; l < KB; ++l) {
-                const double2 gkl = Gi[k * KB + l];
-                const float2 x = c.Hs[l * MB + m];
-                zr += gkl.x * x.x - gkl.y * x.y;
-                zi += gkl.x * x.y + gkl.y * x.x;
-              }
-              c.Qs[idx] = make_float2((float)zr, (float)-zi);
-            }
-            __syncwarp();
-          }
-        }
-      } else if (A.opts & OPT_STEP_NORMALISED) {
-        residual<false>(L, c.Hs, nullptr, nullptr, w, c.tks, false, e);  // conj(H) H^T = G^T
-        *reinterpret_cast<float4*>(c.Es + L.g * KB + 2 * L.q) = make_float4(e[0], e[2], e[1], e[3]);
-        __syncwarp();
-        invL = Base::inv_gershgorin(c);
-      }
+      float invL;
+      const int fl0 = setup(c, L, A, xf, hlo, w, invL, nullptr);
+      int fl = fl0;
       const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
-      // ---- phase change: the layer buffers overwrite the setup buffers, so each
-      // operand is read out (into registers) before its area is reused.
-      {
-        float4* const hh = reinterpret_cast<float4*>(c.Hs);
-        // update fragments X[2q][8nt+g], X[2q+1][8nt+g], split into xf
-        auto put_x = [&](int nt, float2 x0, float2 x1, float csign) {
-          uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
-          split_tf32(x0.x, h0, l0);
-          split_tf32(x1.x, h1, l1);
-          split_tf32(csign * x0.y, h2, l2);
-          split_tf32(csign * x1.y, h3, l3);
-          xf[(nt * 2 + 0) * 32 + L.lane] = make_float4(__uint_as_float(h0), __uint_as_float(h1),
-                                                       __uint_as_float(h2), __uint_as_float(h3));
-          xf[(nt * 2 + 1) * 32 + L.lane] = make_float4(__uint_as_float(l0), __uint_as_float(l1),
-                                                       __uint_as_float(l2), __uint_as_float(l3));
-        };
-        // H hi parts in place of the raw channel, lo parts beside them, from the
-        // lane's own entries v[s] = (Re, Re, Im, Im) at antennas 8s + 2q + {0, 1}
-        auto put_h = [&](const float (&v)[8][4]) {
-#pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
-            split_tf32(v[s][0], h0, l0);
-            split_tf32(v[s][1], h1, l1);
-            split_tf32(v[s][2], h2, l2);
-            split_tf32(v[s][3], h3, l3);
-            hh[s * 32 + L.lane] = make_float4(__uint_as_float(h0), __uint_as_float(h1),
-                                              __uint_as_float(h2), __uint_as_float(h3));
-            hlo[s * 32 + L.lane] = make_float4(__uint_as_float(l0), __uint_as_float(l1),
-                                               __uint_as_float(l2), __uint_as_float(l3));
-          }
-        };
-        if constexpr (MODE == kModePGD) {
-          // X = conj(H) from the raw channel; xf lies outside it
-#pragma unroll
-          for (int nt = 0; nt < 8; ++nt)
-            put_x(nt, c.Hs[(2 * L.q) * MB + 8 * nt + L.g], c.Hs[(2 * L.q + 1) * MB + 8 * nt + L.g], -1.f);
-          if constexpr (PRE) {
-            __syncwarp();
-            float v[8][4];  // w = conj(H) = W^(0) stays live
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-              v[s][0] = w[s][0];
-              v[s][1] = w[s][1];
-              v[s][2] = -w[s][2];
-              v[s][3] = -w[s][3];
-            }
-            put_h(v);
-          }
-        } else {
-          // H re-read from the raw channel (w is rebuilt from Q below); all lanes
-          // read before any overwrites it
-          if constexpr (PRE) {
-            float v[8][4];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-              const float4 hv = *reinterpret_cast<const float4*>(c.Hs + L.g * MB + 8 * s + 2 * L.q);
-              v[s][0] = hv.x;
-              v[s][1] = hv.z;
-              v[s][2] = hv.y;
-              v[s][3] = hv.w;
-            }
-            __syncwarp();
-            put_h(v);
-          }
-          if (!fast) {
-            // X = Q from the FP64 path: tiles 4..7 of xf lie in the Gauss-Jordan
-            // area, tiles 0..3 over Q
-            const float2 z = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int nt = 4; nt < 8; ++nt)
-              put_x(nt, singular ? z : c.Qs[(2 * L.q) * MB + 8 * nt + L.g],
-                    singular ? z : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g], 1.f);
-            const float tg = c.tks[L.g];  // W^(0) = S Q
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-              const float4 qv = singular ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                         : *reinterpret_cast<const float4*>(c.Qs + L.g * MB + 8 * s + 2 * L.q);
-              w[s][0] = tg * qv.x;
-              w[s][1] = tg * qv.z;
-              w[s][2] = tg * qv.y;
-              w[s][3] = tg * qv.w;
-            }
-            float2 x0[4], x1[4];
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-              x0[nt] = singular ? z : c.Qs[(2 * L.q) * MB + 8 * nt + L.g];
-              x1[nt] = singular ? z : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g];
-            }
-            __syncwarp();
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) put_x(nt, x0[nt], x1[nt], 1.f);
-          }
-        }
-      }
-      __syncwarp();
 
       // ---- layers
       const int T = A.T;

@@ -15,6 +15,7 @@ const std::vector<TrainVariant>& train_variants() {
     std::vector<TrainVariant> r;
     register_train_pgd(r);
     register_train_proj(r);
+    register_train_tc(r);
     return r;
   }();
   return v;
@@ -40,12 +41,15 @@ __global__ void batch_mean_kernel(const float* __restrict__ part, int64_t B, int
 }
 
 
-const TrainVariant* pick_train(int mode, int M, int K) {
+const TrainVariant* pick_train(int mode, int M, int K, bool tensor_cores) {
   const TrainVariant* best = nullptr;
+  if (tensor_cores)
+    for (const auto& v : train_variants())
+      if (v.tc && v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
   for (const auto& v : train_variants())
-    if (v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
+    if (!v.tc && v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
   for (const auto& v : train_variants()) {
-    if (v.mode != mode || v.exact || v.KB < K || v.MB < M) continue;
+    if (v.tc || v.mode != mode || v.exact || v.KB < K || v.MB < M) continue;
     if (!best || v.KB * v.MB < best->KB * best->MB) best = &v;
   }
   return best;
@@ -84,7 +88,7 @@ extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int3
     return fail(PRECODE_EINVAL, "precode_train_step: lam and dlam required for the paper layer");
   if ((uintptr_t)H & 15) return fail(PRECODE_EINVAL, "precode_train_step: H must be 16-byte aligned");
   if (t_stride != 0 && t_stride < K) return fail(PRECODE_EINVAL, "precode_train_step: t_stride < K");
-  const TrainVariant* v = pick_train(p->mode, M, K);
+  const TrainVariant* v = pick_train(p->mode, M, K, (p->flags & PRECODE_PLAN_TENSOR_CORES) != 0);
   if (!v) return fail(PRECODE_EINVAL, "precode_train_step: no train kernel holds the shape");
   std::lock_guard<std::mutex> lk(p->mu);
   DeviceGuard g(p->device);

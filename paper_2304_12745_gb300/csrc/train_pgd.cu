@@ -9,7 +9,7 @@ void register_train_pgd(std::vector<TrainVariant>& v) {
   v.push_back(TrainVariant{kModePGD, KB, MB, EXACT,                                          \
                            (const void*)&train_kernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW, MINB>, \
                            TrainKernel<kModePGD, KB, MB, GK, GM, JC, EXACT, NW>::SMEM_BYTES, NW * 32, \
-                           SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::GROUPS});
+                           SolveCfg<kModePGD, KB, MB, GK, GM, JC, NW>::GROUPS, false});
 #include "train_variants.inc"
 #undef X
 }

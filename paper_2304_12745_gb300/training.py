@@ -59,12 +59,15 @@ class UnfoldedTrainer:
 
     def __init__(self, mode: int, T: int, K: int, M: int, batch: int, *, a: float,
                  lr: float = 1e-3, init_step=None, init_lam=None, device: str = "cuda",
-                 step_normalised: bool = False, group=None):
+                 step_normalised: bool = False, group=None, tensor_cores: bool = True):
         """`group`: a torch.distributed process group whose ranks each train on
-        their own batches; gradients are averaged over all ranks every step."""
+        their own batches; gradients are averaged over all ranks every step.
+        `tensor_cores`: use the tensor-core (split TF32) forward + adjoint build
+        where the shape has one (K = 8, M = 64)."""
         self.mode, self.T, self.K, self.M, self.batch, self.a = mode, T, K, M, batch, a
         self.group = group
-        self.plan = Plan(mode, T, [(M, K)], batch, step_normalised=step_normalised)
+        self.plan = Plan(mode, T, [(M, K)], batch, step_normalised=step_normalised,
+                         tensor_cores=tensor_cores)
         L = mp_bound(K, M)
         if init_step is None:
             init_step = [1.0 / L] * T if mode == capi.LAYER_PGD else [0.05] * T

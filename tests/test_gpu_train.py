@@ -55,8 +55,9 @@ def _train_step(plan, H, t, step, lam, a):
             None if dl is None else dl.cpu().numpy().astype(np.float64))
 
 
-@pytest.mark.parametrize("K,M,T", [(4, 32, 6), (8, 64, 10)])
-def test_projected_gradient_matches_oracle(orc, K, M, T):
+@pytest.mark.parametrize("K,M,T,tc", [(4, 32, 6, False), (8, 64, 10, False), (8, 64, 10, True)])
+def test_projected_gradient_matches_oracle(orc, K, M, T, tc):
+    """FP32 build, and (tc) the tensor-core build of the forward + adjoint pass."""
     from paper_2304_12745_gb300 import capi
     from paper_2304_12745_gb300.precoder import Plan
     B0 = 64
@@ -72,17 +73,18 @@ def test_projected_gradient_matches_oracle(orc, K, M, T):
     ref = [orc.ufproj_grad(H[b], t[b], mu, a) for b in range(B)]
     loss_o = np.mean([r[0] for r in ref])
     g_o = np.mean([r[1] for r in ref], axis=0)
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, tensor_cores=tc)
     loss, g, _ = _train_step(plan, H, t, mu, None, a)
     plan.close()
     assert loss == pytest.approx(loss_o, rel=1e-5)
     assert np.allclose(g, g_o, rtol=1e-3, atol=1e-3 * np.abs(g_o).max()), (g, g_o)
 
 
-def test_paper_layer_gradient_matches_oracle(orc):
+@pytest.mark.parametrize("K,M,tc", [(4, 32, False), (8, 64, True)])
+def test_paper_layer_gradient_matches_oracle(orc, K, M, tc):
     from paper_2304_12745_gb300 import capi
     from paper_2304_12745_gb300.precoder import Plan
-    K, M, T, B0 = 4, 32, 5, 64
+    T, B0 = 5, 64
     H = ch.rayleigh(B0, K, M, seed=50).astype(np.complex128)
     t = np.ones((B0, K))
     eta0 = ch.paper_eta(K, M)
@@ -98,7 +100,7 @@ def test_paper_layer_gradient_matches_oracle(orc):
     loss_o = np.mean([r[0] for r in ref])
     ge_o = np.mean([r[1] for r in ref], axis=0)
     gl_o = np.mean([r[2] for r in ref], axis=0)
-    plan = Plan(capi.LAYER_PGD, T, [(M, K)], B)
+    plan = Plan(capi.LAYER_PGD, T, [(M, K)], B, tensor_cores=tc)
     loss, ge, gl = _train_step(plan, H, t, eta, lam, a)
     plan.close()
     assert loss == pytest.approx(loss_o, rel=1e-5)
@@ -106,7 +108,8 @@ def test_paper_layer_gradient_matches_oracle(orc):
     assert np.allclose(gl, gl_o, rtol=1e-3, atol=1e-3 * np.abs(gl_o).max()), (gl, gl_o)
 
 
-def test_gradient_matches_central_differences_of_the_gpu_loss():
+@pytest.mark.parametrize("tc", [False, True])
+def test_gradient_matches_central_differences_of_the_gpu_loss(tc):
     """Central differences (h = 1e-3) of the GPU's own FP32 batch loss."""
     from paper_2304_12745_gb300 import capi
     from paper_2304_12745_gb300.precoder import Plan
@@ -114,7 +117,7 @@ def test_gradient_matches_central_differences_of_the_gpu_loss():
     H = ch.rayleigh(B, K, M, seed=60)
     t = np.ones((B, K), np.float32)
     mu = ch.uniform_steps(T, 0.02, 0.08, seed=61).astype(np.float64)
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, tensor_cores=tc)
     _, g, _ = _train_step(plan, H, t, mu, None, 1.0)
     h = 1e-3
     for l in (0, 4, 9):
