@@ -415,6 +415,14 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       invL = Base::inv_gershgorin(c);
     }
     const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
+    if (xraw) {  // raw conj(H) B fragments, read before the channel area is reused
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float2 h0 = c.Hs[(2 * L.q) * MB + 8 * nt + L.g];
+        const float2 h1 = c.Hs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+        xraw[nt * 32 + L.lane] = make_float4(h0.x, h1.x, -h0.y, -h1.y);
+      }
+    }
     // ---- phase change: the layer buffers overwrite the setup buffers, so each
     // operand is read out (into registers) before its area is reused.
     {

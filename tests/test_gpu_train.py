@@ -129,6 +129,28 @@ def test_gradient_matches_central_differences_of_the_gpu_loss(tc):
     plan.close()
 
 
+def test_tensor_core_training_independent_of_earlier_kernels():
+    """The projected-layer training kernel after paper-layer kernels (which leave
+    their own data in shared memory) gives the same finite gradient as alone:
+    every shared-memory operand is written before it is read."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+    K, M, T, B = 8, 64, 20, 4096
+    H = ch.rayleigh(B, K, M, seed=62)
+    t = np.full((B, K), math.sqrt(10.0), np.float32)
+    mu = np.full(T, 0.05)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, tensor_cores=True)
+    alone = _train_step(plan, H, t, mu, None, 1.0)
+    for tc in (True, False):
+        pg = Plan(capi.LAYER_PGD, T, [(M, K)], B, tensor_cores=tc)
+        _train_step(pg, H, t, np.full(T, ch.paper_eta(K, M)), np.full(T, 0.07), 1.0)
+        pg.close()
+        after = _train_step(plan, H, t, mu, None, 1.0)
+        assert np.all(np.isfinite(after[1]))
+        assert after[0] == alone[0] and np.array_equal(after[1], alone[1])
+    plan.close()
+
+
 def test_train_step_deterministic_and_trainer_resume():
     from paper_2304_12745_gb300 import capi
     from paper_2304_12745_gb300.training import UnfoldedTrainer
