@@ -218,8 +218,11 @@ precode_status_t precode_solve_varlen_static(const precode_desc_t* desc, int64_t
  * other slots' launches.  Jobs arriving while launches run are admitted as soon
  * as a slot and memory free up.  A job's results do not depend on which jobs
  * shared its launch.  Resident channels keep H on the device across jobs.
- * Host buffers of a job must stay valid until its result is polled / waited;
- * pinned host memory lets the copies overlap with other work. */
+ * Host buffers of a job must stay valid until its result is polled / waited.
+ * H, t and W_out are copied directly: pinned host memory lets those copies
+ * overlap with other work (a copy into pageable W_out holds the dispatcher until
+ * its launch ends).  obj_out, resid_out and flags_out are staged through the
+ * server's pinned buffers and may be pageable. */
 typedef struct precode_server_s* precode_server_t;
 
 typedef struct {

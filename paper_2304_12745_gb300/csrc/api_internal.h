@@ -33,6 +33,8 @@ int variant_occupancy(const Variant& v, int device);
 // Default variant for (mode, M, K): the tensor-core build if requested and present,
 // else the first exact build, else the smallest generic bucket holding the shape.
 const Variant* pick_variant(int mode, int M, int K, bool tensor_cores = false);
+// Allocates the plan's uneven-batch workspace (bucket lists) if not yet there.
+precode_status_t ensure_workspace(precode_plan_t p);
 std::vector<const Variant*> eligible_variants(int mode, int M, int K);
 // n_hint >= 0: launch no more blocks than needed for n_hint instances.
 precode_status_t launch_variant(const Variant& v, int device, int num_sms, const SolveArgs& A,

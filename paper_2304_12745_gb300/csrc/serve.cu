@@ -111,7 +111,11 @@ struct Slot {
   cudaStream_t stream = nullptr;
   precode_plan_t plan = nullptr;
   precode_inst_t* h_tbl = nullptr;  // pinned
-  float* h_t = nullptr;             // unused (targets copied per job)
+  // per-instance outputs of the launch, staged in pinned memory: a copy into a
+  // caller's pageable buffer would hold the dispatcher until the launch ends
+  float* h_obj = nullptr;
+  float* h_resid = nullptr;
+  int32_t* h_flags = nullptr;
   void* d_tbl = nullptr;
   float* d_obj = nullptr;
   float* d_resid = nullptr;
@@ -242,16 +246,13 @@ void dispatch_loop(precode_server_t s) {
     for (auto& j : batch) {
       if (e != cudaSuccess || ps != PRECODE_OK) break;
       e = cudaMemcpyAsync(j->d.W_out, base + j->w_off, j->w_bytes, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess && j->d.obj_out)
-        e = cudaMemcpyAsync(j->d.obj_out, slot->d_obj + j->first, 4 * j->n, cudaMemcpyDeviceToHost,
-                            st);
-      if (e == cudaSuccess && j->d.resid_out)
-        e = cudaMemcpyAsync(j->d.resid_out, slot->d_resid + j->first, 4 * j->n,
-                            cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess && j->d.flags_out)
-        e = cudaMemcpyAsync(j->d.flags_out, slot->d_flags + j->first, 4 * j->n,
-                            cudaMemcpyDeviceToHost, st);
     }
+    if (e == cudaSuccess && ps == PRECODE_OK)
+      e = cudaMemcpyAsync(slot->h_obj, slot->d_obj, 4 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ps == PRECODE_OK)
+      e = cudaMemcpyAsync(slot->h_resid, slot->d_resid, 4 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ps == PRECODE_OK)
+      e = cudaMemcpyAsync(slot->h_flags, slot->d_flags, 4 * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecord(slot->done, st);
     lk.lock();
     if (e != cudaSuccess || ps != PRECODE_OK) {
@@ -275,6 +276,13 @@ void slot_loop(precode_server_t s, Slot* slot) {
     slot->go = false;
     lk.unlock();
     const cudaError_t e = cudaEventSynchronize(slot->done);
+    if (e == cudaSuccess)  // per-instance outputs from the pinned staging to the callers
+      for (auto& j : slot->jobs) {
+        if (j->status != PRECODE_PENDING) continue;
+        if (j->d.obj_out) std::memcpy(j->d.obj_out, slot->h_obj + j->first, 4 * j->n);
+        if (j->d.resid_out) std::memcpy(j->d.resid_out, slot->h_resid + j->first, 4 * j->n);
+        if (j->d.flags_out) std::memcpy(j->d.flags_out, slot->h_flags + j->first, 4 * j->n);
+      }
     const double t = now_us();
     lk.lock();
     for (auto& j : slot->jobs) {
@@ -322,6 +330,9 @@ void server_free(precode_server_t s) {
     if (sl->stream) cudaStreamDestroy(sl->stream);
     if (sl->done) cudaEventDestroy(sl->done);
     cudaFreeHost(sl->h_tbl);
+    cudaFreeHost(sl->h_obj);
+    cudaFreeHost(sl->h_resid);
+    cudaFreeHost(sl->h_flags);
     cudaFree(sl->d_tbl);
     cudaFree(sl->d_obj);
     cudaFree(sl->d_resid);
@@ -384,7 +395,13 @@ precode_status_t precode_serve_create(const precode_serve_desc_t* d, precode_ser
     if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming) != cudaSuccess)
       return fail(PRECODE_ECUDA, "precode_serve_create: stream / event");
+    // the plan's bucket workspace now, not at the first launch (allocation stalls)
+    st = ensure_workspace(sl->plan);
+    if (st != PRECODE_OK) return st;
     if (cudaMallocHost(&sl->h_tbl, sizeof(precode_inst_t) * cap) != cudaSuccess ||
+        cudaMallocHost(&sl->h_obj, 4 * cap) != cudaSuccess ||
+        cudaMallocHost(&sl->h_resid, 4 * cap) != cudaSuccess ||
+        cudaMallocHost(&sl->h_flags, 4 * cap) != cudaSuccess ||
         cudaMalloc(&sl->d_tbl, sizeof(precode_inst_t) * cap) != cudaSuccess ||
         cudaMalloc(&sl->d_obj, 4 * cap) != cudaSuccess ||
         cudaMalloc(&sl->d_resid, 4 * cap) != cudaSuccess ||

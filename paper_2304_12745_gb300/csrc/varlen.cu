@@ -66,6 +66,8 @@ struct VarlenCall {
   int32_t* flags;
 };
 
+}  // namespace
+
 precode_status_t ensure_workspace(precode_plan_t p) {
   if (p->d_index) return PRECODE_OK;
   const size_t nb = p->buckets.size();
@@ -77,6 +79,8 @@ precode_status_t ensure_workspace(precode_plan_t p) {
   }
   return PRECODE_OK;
 }
+
+namespace {
 
 int bucketize_grid(precode_plan_t p) { return 2 * p->num_sms; }
 

@@ -119,7 +119,8 @@ def poisson_load(server: Server, rate_per_s: float, duration_s: float, seed: int
     pool = pinned(n_max, np.complex64)
     pool[:] = channels.rician_ula(1, 1, n_max, seed=seed)[0, 0]
     ring = pinned(ring_bytes // 8, np.complex64)
-    ones = np.ones(K_range[1], np.float32)
+    ones = pinned(K_range[1], np.float32)
+    ones[:] = 1.0
     sched, t = [], 0.0
     while t < duration_s:
         t += rng.exponential(1.0 / rate_per_s)

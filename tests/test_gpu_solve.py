@@ -418,6 +418,29 @@ def test_tensor_core_large_flags_and_fp64(pc, orc):
                   w_tol=2e-3, obj_tol=2e-4)
 
 
+def test_tensor_core_kernels_independent_of_earlier_kernels(pc):
+    """Each tensor-core solve kernel gives bitwise the same output fresh and after
+    other kernels (with other shared-memory layouts) ran on the device: every
+    shared-memory operand is written before it is read."""
+    capi, precoder = pc
+    cases = [(capi.LAYER_PROJ, 8, 64), (capi.LAYER_PGD, 8, 64), (capi.LAYER_PROJ, 16, 128),
+             (capi.LAYER_PROJ, 32, 256), (capi.LAYER_PROJ, 13, 64)]
+    runs = {}
+    for rep in range(2):
+        for mode, K, M in (cases if rep == 0 else cases[::-1]):
+            H = ch.rician_ula(600, K, M, seed=70 + K)
+            t = ch.targets(600, K)
+            step = ch.uniform_steps(6, 0.01, 0.1, seed=7) if mode == capi.LAYER_PROJ else \
+                np.full(6, ch.paper_eta(K, M), np.float32)
+            lam = None if mode == capi.LAYER_PROJ else np.full(6, 1 / 15, np.float32)
+            out = run_gpu(precoder, mode, H, t, step, lam, tensor_cores=True)
+            if rep == 0:
+                runs[(mode, K, M)] = out
+            else:
+                for a, b in zip(out, runs[(mode, K, M)]):
+                    assert np.array_equal(a, b), (mode, K, M)
+
+
 def test_tensor_core_full_size_sampled(pc, orc):
     capi, precoder = pc
     wl = ch.WORKLOADS["fixed"]
