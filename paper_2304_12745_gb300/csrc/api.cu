@@ -87,10 +87,13 @@ const Variant* pick_variant(int mode, int M, int K, bool tensor_cores) {
   return best;
 }
 
+// Autotuning candidates: every variant that fits, except user-padded tensor-core
+// builds with 8 or more padded users (never faster than the tighter build).
 std::vector<const Variant*> eligible_variants(int mode, int M, int K) {
   std::vector<const Variant*> r;
   for (const auto& v : variants())
-    if (v.mode == mode && variant_fits(v, M, K)) r.push_back(&v);
+    if (v.mode == mode && variant_fits(v, M, K) && (!v.tc || v.exact || v.KB < K + 8))
+      r.push_back(&v);
   return r;
 }
 
