@@ -122,24 +122,28 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
   }
 
   // E = W H^T (minus S on the diagonal when sub_s): returns the lane's fragment
-  // e = (E_re[g][2q], E_re[g][2q+1], E_im[g][2q], E_im[g][2q+1]).  Four blocks of
-  // 8 antennas at a time, their MMAs issued term by term over four accumulators.
+  // e = (E_re[g][2q], E_re[g][2q+1], E_im[g][2q], E_im[g][2q+1]).  Every MMA
+  // takes the same A quad (Re W, Im W rows); products with Re H go to ar, with
+  // Im H to ai, so that
+  //   E_re = [ar]_row g - [ai]_row g+8,   E_im = [ai]_row g + [ar]_row g+8
+  // (no negated or permuted copies of W).  Two blocks of 8 antennas at a time,
+  // term by term (lo terms first).
   // PRE: H comes pre-split, hi / lo fragments (Hr0, Hr1, Hi0, Hi1) at [s][lane];
   // otherwise it is read from the raw channel and split here.
   template <bool PRE>
   __device__ __forceinline__ static void residual(const Lane& L, const float2* Hs, const float4* hhi,
                                                   const float4* hlo, const WT& w, const float* tks,
                                                   bool sub_s, float (&e)[4]) {
-    float acc[4][4];
+    float ar[2][4], ai[2][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+      for (int k = 0; k < 4; ++k) ar[i][k] = ai[i][k] = 0.f;
 #pragma unroll
-    for (int s0 = 0; s0 < 8; s0 += 4) {
-      uint32_t bh[4][4], bl[4][4], ah[4][4], al[4][4];  // [block][hr0 hr1 hi0 hi1 / r0 i0 r1 i1]
+    for (int s0 = 0; s0 < 8; s0 += 2) {
+      uint32_t bh[2][4], bl[2][4], ah[2][4], al[2][4];  // [block][hr0 hr1 hi0 hi1 / r0 i0 r1 i1]
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 2; ++u) {
         const int s = s0 + u;
         if constexpr (PRE) {
           const float4 hh = hhi[s * 32 + L.lane], hl = hlo[s * 32 + L.lane];
@@ -163,32 +167,32 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
         split_tf32(w[s][1], ah[u][2], al[u][2]);  // Re W, h = 1
         split_tf32(w[s][3], ah[u][3], al[u][3]);  // Im W, h = 1
       }
-      // real block: A = (re0, im0, re1, im1), B = (hr0, hr1)
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(acc[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bl[u][0], bl[u][1]);
+      for (int u = 0; u < 2; ++u) {
+        mma_tf32(ar[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bl[u][0], bl[u][1]);
+        mma_tf32(ai[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bl[u][2], bl[u][3]);
+      }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(acc[u], al[u][0], al[u][1], al[u][2], al[u][3], bh[u][0], bh[u][1]);
-      // imaginary block: A = (-im0, re0, -im1, re1), B = (hi0, hi1)
+      for (int u = 0; u < 2; ++u) {
+        mma_tf32(ar[u], al[u][0], al[u][1], al[u][2], al[u][3], bh[u][0], bh[u][1]);
+        mma_tf32(ai[u], al[u][0], al[u][1], al[u][2], al[u][3], bh[u][2], bh[u][3]);
+      }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(acc[u], neg_bits(ah[u][1]), ah[u][0], neg_bits(ah[u][3]), ah[u][2], bl[u][2],
-                 bl[u][3]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(acc[u], neg_bits(al[u][1]), al[u][0], neg_bits(al[u][3]), al[u][2], bh[u][2],
-                 bh[u][3]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(acc[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bh[u][0], bh[u][1]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(acc[u], neg_bits(ah[u][1]), ah[u][0], neg_bits(ah[u][3]), ah[u][2], bh[u][2],
-                 bh[u][3]);
+      for (int u = 0; u < 2; ++u) {
+        mma_tf32(ar[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bh[u][0], bh[u][1]);
+        mma_tf32(ai[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bh[u][2], bh[u][3]);
+      }
     }
+    float r[4], im[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) e[k] = (acc[0][k] + acc[1][k]) + (acc[2][k] + acc[3][k]);
+    for (int k = 0; k < 4; ++k) {
+      r[k] = ar[0][k] + ar[1][k];
+      im[k] = ai[0][k] + ai[1][k];
+    }
+    e[0] = r[0] - im[2];
+    e[1] = r[1] - im[3];
+    e[2] = im[0] + r[2];
+    e[3] = im[1] + r[3];
     if (sub_s) {
       if (2 * L.q == L.g) e[0] -= tks[L.g];
       if (2 * L.q + 1 == L.g) e[1] -= tks[L.g];

@@ -73,15 +73,18 @@ struct SolveTCW {
   // --------------------------------------------------------------- residual
   // E tile ct of the warp's rows: e = (E_re[g][8ct+2q], E_re[g][8ct+2q+1],
   // E_im[g][8ct+2q], E_im[g][8ct+2q+1]) with E = A H^T, A = W (or conj(H)'s own
-  // rows for the Gram matrix), over all antenna blocks; four accumulator chains.
+  // rows for the Gram matrix), over all antenna blocks.  Every MMA takes the
+  // same A quad (Re, Im rows); products with Re H go to ar, with Im H to ai, and
+  //   E_re = [ar]_row g - [ai]_row g+8,   E_im = [ai]_row g + [ar]_row g+8.
+  // Two accumulator pairs (even and odd blocks).
   template <bool A_FROM_H>
   __device__ __forceinline__ static void e_tile(const Lane& L, const float2* Hs, const WT& w, int ct,
                                                 float (&e)[4]) {
-    float acc[4][4];
+    float ar[2][4], ai[2][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+      for (int k = 0; k < 4; ++k) ar[i][k] = ai[i][k] = 0.f;
     const float2* hb = Hs + (8 * ct + L.g) * RSF + 2 * L.q;
     const float2* ha = Hs + (8 * L.w + L.g) * RSF + 2 * L.q;
 #pragma unroll
@@ -109,18 +112,26 @@ struct SolveTCW {
       split_tf32_ordered(hv.z, bh[1], bl[1]);  // Re H[8ct+g][8s+2q+1]
       split_tf32_ordered(hv.y, bh[2], bl[2]);  // Im
       split_tf32_ordered(hv.w, bh[3], bl[3]);
-      float (&a)[4] = acc[s & 3];
-      // real block: A = (re0, im0, re1, im1), B = (Re, Re); imaginary block:
-      // A = (-im0, re0, -im1, re1), B = (Im, Im)
-      mma_tf32(a, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
-      mma_tf32(a, neg_bits(ah[1]), ah[0], neg_bits(ah[3]), ah[2], bl[2], bl[3]);
-      mma_tf32(a, al[0], al[1], al[2], al[3], bh[0], bh[1]);
-      mma_tf32(a, neg_bits(al[1]), al[0], neg_bits(al[3]), al[2], bh[2], bh[3]);
-      mma_tf32(a, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
-      mma_tf32(a, neg_bits(ah[1]), ah[0], neg_bits(ah[3]), ah[2], bh[2], bh[3]);
+      float (&r)[4] = ar[s & 1];
+      float (&i)[4] = ai[s & 1];
+      // A = (re0, im0, re1, im1) throughout; B = (Re, Re) into r, (Im, Im) into i
+      mma_tf32(r, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+      mma_tf32(i, ah[0], ah[1], ah[2], ah[3], bl[2], bl[3]);
+      mma_tf32(r, al[0], al[1], al[2], al[3], bh[0], bh[1]);
+      mma_tf32(i, al[0], al[1], al[2], al[3], bh[2], bh[3]);
+      mma_tf32(r, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
+      mma_tf32(i, ah[0], ah[1], ah[2], ah[3], bh[2], bh[3]);
     }
+    float r[4], im[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) e[k] = (acc[0][k] + acc[1][k]) + (acc[2][k] + acc[3][k]);
+    for (int k = 0; k < 4; ++k) {
+      r[k] = ar[0][k] + ar[1][k];
+      im[k] = ai[0][k] + ai[1][k];
+    }
+    e[0] = r[0] - im[2];
+    e[1] = r[1] - im[3];
+    e[2] = im[0] + r[2];
+    e[3] = im[1] + r[3];
   }
 
   // Subtract S on the diagonal (column tile ct == w, local column 2q or 2q + 1 == g).
