@@ -69,6 +69,14 @@ def mma_per_instance(T: int) -> int:
     return 96 * T + 48 + 96 + 48
 
 
+def mma_per_instance_f16(T: int) -> tuple:
+    """Warp MMAs the split-FP16 kernel issues for one projected-layer instance:
+    (m16n8k16 FP16, m16n8k8 TF32).  Each 8 x 64 complex contraction of a layer is
+    24 FP16 MMAs (4 antenna-block pairs x Re/Im H x 3 split terms for the residual;
+    8 tiles x 3 for the update); the setup's Gram matrix, Q and Q^T stay split TF32."""
+    return 48 * T + 24, 48 + 96
+
+
 def fp32_peak_tflops() -> float:
     """152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (maximum SM clock)."""
     return 152 * 128 * 2 * 2.070e9 / 1e12
@@ -533,7 +541,21 @@ def main():
                     "peak_gbs": peaks.get("hbm_gbs"), "algorithmic_bytes": hbm_bytes}}
     plan_kernel_name = capi.precode_plan_describe(plan.handle, M, K)
     roof["kernel"] = plan_kernel_name
-    if plan_kernel_name.startswith("solve_tc_kernel"):
+    if plan_kernel_name.startswith("solve_tch_kernel"):
+        # layers as split FP16 (m16n8k16), setup as split TF32: issued MMA work as a
+        # share of the dense tensor peaks (FP16 = the measured bf16 peak; TF32 = that
+        # times the nominal ratio 1.1 / 2.25), summed as pipe time
+        n16, n8 = mma_per_instance_f16(T)
+        sec = kern_ms / 1e3
+        i16 = n16 * 2 * 16 * 8 * 16 * B / sec / 1e12
+        i8 = n8 * 2 * 16 * 8 * 8 * B / sec / 1e12
+        f16_peak = peaks.get("bf16_tflops", 1900.0)
+        tf32_peak = f16_peak * 1.1 / 2.25
+        roof["tensor"] = {"mma_m16n8k16_f16_per_instance": n16, "mma_m16n8k8_tf32_per_instance": n8,
+                          "issued_tflops": i16 + i8, "peak_f16_tflops": f16_peak,
+                          "peak_tf32_tflops": tf32_peak, "frac": i16 / f16_peak + i8 / tf32_peak,
+                          "peak_source": "of measured: bf16_tflops (FP16), x 1.1 / 2.25 (TF32)"}
+    elif plan_kernel_name.startswith("solve_tc_kernel"):
         # the contractions run on the tensor cores as split TF32 (three MMAs per
         # FP32-accurate product): issued MMA work against the TF32 dense peak
         # (the measured bf16 peak times the nominal TF32 / bf16 ratio 1.1 / 2.25)

@@ -23,6 +23,7 @@ struct Variant {
   int groups;    // instances resident per block
   bool tc;       // contractions on the tensor cores (warp MMA, split TF32); a non-exact
                  // tensor-core build pads users (K <= KB) but needs M == MB
+  bool f16 = false;  // the layers' contractions as split-FP16 MMAs (scaled instances)
 };
 
 // The instance shapes (M, K) a variant solves.
@@ -50,6 +51,7 @@ void register_train_tc(std::vector<TrainVariant>& v);
 const std::vector<TrainVariant>& train_variants();
 void register_solve_proj(std::vector<Variant>& v);
 void register_solve_tc(std::vector<Variant>& v);
+void register_solve_tch(std::vector<Variant>& v);
 void register_solve_tcw_64(std::vector<Variant>& v);
 void register_solve_tcw_128(std::vector<Variant>& v);
 void register_solve_tcw_256(std::vector<Variant>& v);

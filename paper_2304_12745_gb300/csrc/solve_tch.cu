@@ -1,0 +1,18 @@
+// Instantiations of the split-FP16 tensor-core solve kernel (projected layer,
+// K = 8, M = 64).
+#include "registry.h"
+#include "solve_tch.cuh"
+
+namespace precode {
+
+void register_solve_tch(std::vector<Variant>& v) {
+#define X(NW, MINB)                                                                     \
+  v.push_back(Variant{kModeProj, 8, 64, 4, 8, 8, NW, MINB, true, true, false,           \
+                      (const void*)&solve_tch_kernel<NW, MINB>, SolveTCH<NW>::SMEM_BYTES, \
+                      NW * 32, NW, true, true});
+  X(4, 3)
+  X(4, 4)
+#undef X
+}
+
+}  // namespace precode

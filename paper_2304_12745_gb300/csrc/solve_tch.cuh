@@ -1,0 +1,469 @@
+// Projected-layer solve kernel for K = 8 users, M = 64 antennas with the layers'
+// contractions as split-FP16 warp MMAs (m16n8k16): one warp per instance, the same
+// lane ownership as the TF32 kernel (lane (g, q) holds user g's W at antennas
+// 8s + 2q + {0, 1}), half the MMAs of the TF32 split for the same accuracy, and
+// half its fragment traffic through shared memory.
+//
+// FP16 covers a narrow exponent range, so every instance is solved in scaled
+// units made of exact powers of two, under which the projected iteration is
+// equivariant: with D = diag(d_k) and a scalar b,
+//   H' = D H,  t'_k = b d_k t_k,  W' = b W,  mu' = b mu,  X = Q' = G'^{-T} H'^* = D^{-1} Q,
+// every iterate is W' = b W and the residual is E' = b E D.  d_k puts the largest
+// component of user k's channel row in [1/2, 1), so every row of H' and of Q' is
+// of order one whatever the spread of the users' gains (a weak user's row would
+// otherwise fall into FP16's subnormals, and its errors are amplified by 1 / |h_k|
+// in W); b puts max(|W^(0)'|, t') in [2^6, 2^7).  An instance whose Q' exceeds
+// 2^13 (an equilibrated Gram condition far beyond FP32 accuracy, FP64 path only)
+// is reported as singular.  W, the objective and the residual are scaled back on
+// the way out.
+//
+// Per layer, reduction over antennas (residual E = W H^T, 16 antennas per MMA):
+//   A = (Re W, Im W) rows, B = Re H or Im H, accumulators ar / ai,
+//   E_re = [ar]_g - [ai]_g+8,  E_im = [ai]_g + [ar]_g+8;
+// reduction over users (update W -= E X, k = (Re, Im) x 8 users per MMA):
+//   A rows g: (-E_re, +E_im), rows g+8: (-E_im, -E_re), B = (Re X; Im X).
+// The Gram matrix, its inverse and Q are formed once per instance exactly as in
+// the TF32 kernel (TF32 split MMAs, FP64 path for ill-conditioned instances).
+#pragma once
+
+#include "f16mma.cuh"
+#include "solve_tc.cuh"
+
+namespace precode {
+
+template <int NW>
+struct SolveTCH : SolveTC<kModeProj, NW, false> {
+  using S = SolveTC<kModeProj, NW, false>;
+  using Base = typename S::Base;
+  using C = typename S::C;
+  using Ctx = typename S::Ctx;
+  using Lane = typename S::Lane;
+  using WT = typename S::WT;
+  static constexpr int KB = 8, MB = 64;
+  // Per-warp shared memory, two overlaid phases (bytes):
+  //   setup : H (raw channel, scaled in place) | Q / FP64 scratch | G^{-1} (FP64) | Gram
+  //   layers: H hi / lo FP16 fragments (in place) | X fragments | norm partials | factors
+  //   both  : t, scalars, copy barrier
+  static constexpr int H_BYTES = KB * MB * 8;
+  static constexpr int OFF_Q = H_BYTES;                   // setup, 4 KB
+  static constexpr int OFF_RED = OFF_Q + KB * MB * 8;     // setup, 1 KB
+  static constexpr int OFF_E = OFF_RED + KB * KB * 16;    // setup, 512 B
+  static constexpr int OFF_HL = H_BYTES / 2;              // layers: lo fragments
+  static constexpr int OFF_XF = H_BYTES;                  // layers, 4 KB
+  static constexpr int OFF_NB = OFF_XF + 4096;            // layers, 2 KB
+  static constexpr int OFF_FB = OFF_NB + 2048;            // layers, 256 B
+  static constexpr int OFF_SC = (OFF_FB + 256 > OFF_E + KB * KB * 8) ? OFF_FB + 256 : OFF_E + KB * KB * 8;
+  static constexpr int OFF_BAR = OFF_SC + C::SC_BYTES;
+  static constexpr int GROUP_STRIDE = align_up(OFF_BAR + 8, 16);
+  static constexpr int SMEM_BYTES = NW * GROUP_STRIDE;
+  static constexpr float QMAX = 8192.f;  // bound on |Q'| entries
+
+  // E = W H^T from the FP16 H fragments (hh / hl: [pair][lane] of (Hr block 2p,
+  // Hr block 2p+1, Hi block 2p, Hi block 2p+1) pairs); two pairs of blocks at a
+  // time, term by term (lo terms first).
+  __device__ __forceinline__ static void residual_h(const Lane& L, const uint4* hh, const uint4* hl,
+                                                    const WT& w, float (&e)[4]) {
+    float ar[2][4], ai[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ar[i][k] = ai[i][k] = 0.f;
+#pragma unroll
+    for (int p0 = 0; p0 < 4; p0 += 2) {
+      uint4 bh[2], bl[2];
+      uint32_t ah[2][4], al[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int p = p0 + u;
+        bh[u] = hh[p * 32 + L.lane];
+        bl[u] = hl[p * 32 + L.lane];
+        split_h2(w[2 * p][0], w[2 * p][1], ah[u][0], al[u][0]);          // Re W, block 2p
+        split_h2(w[2 * p][2], w[2 * p][3], ah[u][1], al[u][1]);          // Im W, block 2p
+        split_h2(w[2 * p + 1][0], w[2 * p + 1][1], ah[u][2], al[u][2]);  // Re W, block 2p+1
+        split_h2(w[2 * p + 1][2], w[2 * p + 1][3], ah[u][3], al[u][3]);  // Im W, block 2p+1
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma_f16(ar[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bl[u].x, bl[u].y);
+        mma_f16(ai[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bl[u].z, bl[u].w);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma_f16(ar[u], al[u][0], al[u][1], al[u][2], al[u][3], bh[u].x, bh[u].y);
+        mma_f16(ai[u], al[u][0], al[u][1], al[u][2], al[u][3], bh[u].z, bh[u].w);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma_f16(ar[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bh[u].x, bh[u].y);
+        mma_f16(ai[u], ah[u][0], ah[u][1], ah[u][2], ah[u][3], bh[u].z, bh[u].w);
+      }
+    }
+    float r[4], im[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      r[k] = ar[0][k] + ar[1][k];
+      im[k] = ai[0][k] + ai[1][k];
+    }
+    e[0] = r[0] - im[2];
+    e[1] = r[1] - im[3];
+    e[2] = im[0] + r[2];
+    e[3] = im[1] + r[3];
+  }
+
+  // W -= E X with the FP16 X fragments (xf: [tile][lane] of (Re X hi, Im X hi,
+  // Re X lo, Im X lo) pairs over users 2q, 2q+1 at antenna 8nt + g).
+  __device__ __forceinline__ static void update_h(const Lane& L, const uint4* xf, const float (&e)[4],
+                                                  WT& w) {
+    uint32_t h01, l01, h23, l23;
+    split_h2(e[0], e[1], h01, l01);
+    split_h2(e[2], e[3], h23, l23);
+    const uint32_t nh01 = neg_h2(h01), nl01 = neg_h2(l01), nh23 = neg_h2(h23), nl23 = neg_h2(l23);
+#pragma unroll
+    for (int nt0 = 0; nt0 < 8; nt0 += 4) {
+      uint4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = xf[(nt0 + u) * 32 + L.lane];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mma_f16(w[nt0 + u], nh01, nh23, h23, nh01, x[u].z, x[u].w);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mma_f16(w[nt0 + u], nl01, nl23, l23, nl01, x[u].x, x[u].y);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) mma_f16(w[nt0 + u], nh01, nh23, h23, nh01, x[u].x, x[u].y);
+    }
+  }
+
+  // Q^T tile nt (the update's X values (Re Q[2q][8nt+g], Re Q[2q+1][8nt+g],
+  // Im Q[2q][8nt+g], Im Q[2q+1][8nt+g])) into qt and W^(0) = tg Q (W's layout)
+  // into wj, as split-TF32 MMAs from the lane's G^{-T} entries gi.
+  __device__ __forceinline__ static void q_tile(const Lane& L, const float2* Hs, const float (&gi)[4],
+                                                float tg, int nt, float (&qt)[4], float (&wj)[4]) {
+    uint32_t gr0h, gr0l, gr1h, gr1l, gi0h, gi0l, gi1h, gi1l;
+    split_tf32(gi[0], gr0h, gr0l);
+    split_tf32(gi[1], gr1h, gr1l);
+    split_tf32(gi[2], gi0h, gi0l);
+    split_tf32(gi[3], gi1h, gi1l);
+    const float2 h0 = Hs[(2 * L.q) * MB + 8 * nt + L.g];
+    const float2 h1 = Hs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+    uint32_t xr0h, xr0l, xr1h, xr1l, xi0h, xi0l, xi1h, xi1l;  // X = conj(H)
+    split_tf32(h0.x, xr0h, xr0l);
+    split_tf32(h1.x, xr1h, xr1l);
+    split_tf32(-h0.y, xi0h, xi0l);
+    split_tf32(-h1.y, xi1h, xi1l);
+    float qq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qt[k] = 0.f;
+    mma_tf32(qt, xr0h, xi0h, xr1h, xi1h, gr0l, gr1l);
+    mma_tf32(qq, gr0h, gi0h, gr1h, gi1h, xr0l, xr1l);
+    mma_tf32(qt, xr0l, xi0l, xr1l, xi1l, gr0h, gr1h);
+    mma_tf32(qq, gr0l, gi0l, gr1l, gi1l, xr0h, xr1h);
+    mma_tf32(qt, neg_bits(xi0h), xr0h, neg_bits(xi1h), xr1h, gi0l, gi1l);
+    mma_tf32(qq, neg_bits(gi0h), gr0h, neg_bits(gi1h), gr1h, xi0l, xi1l);
+    mma_tf32(qt, neg_bits(xi0l), xr0l, neg_bits(xi1l), xr1l, gi0h, gi1h);
+    mma_tf32(qq, neg_bits(gi0l), gr0l, neg_bits(gi1l), gr1l, xi0h, xi1h);
+    mma_tf32(qt, xr0h, xi0h, xr1h, xi1h, gr0h, gr1h);
+    mma_tf32(qq, gr0h, gi0h, gr1h, gi1h, xr0h, xr1h);
+    mma_tf32(qt, neg_bits(xi0h), xr0h, neg_bits(xi1h), xr1h, gi0h, gi1h);
+    mma_tf32(qq, neg_bits(gi0h), gr0h, neg_bits(gi1h), gr1h, xi0h, xi1h);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) wj[k] = tg * qq[k];
+  }
+
+  __device__ __forceinline__ static float warp_max(float v) {
+#pragma unroll
+    for (int msk = 1; msk < 32; msk <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, msk));
+    return v;
+  }
+  // 2^-e with v = f 2^e, f in [1/2, 1); 1 for zero or non-finite v
+  __device__ __forceinline__ static float inv_pow2_of(float v) {
+    if (!(v > 0.f) || !(v <= FLT_MAX)) return 1.f;
+    int ex;
+    frexpf(v, &ex);
+    return ldexpf(1.f, -ex);
+  }
+
+  // Per-instance setup: the scaled problem (d_k^{-1} into c.dsc, t' into c.tks),
+  // the X fragments, the H fragments and W^(0)' into w; b into beta.  Returns the
+  // instance flags.
+  __device__ static int setup(Ctx& c, const Lane& L, const SolveArgs& A, uint4* xf, WT& w,
+                              float& beta) {
+    float2* const Hs = c.Hs;
+    // ---- per-user scales: row g of H' = d_g H[g] (in place), t'_g = d_g t_g
+    float hm = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      hm = fmaxf(hm, fmaxf(fmaxf(fabsf(hv.x), fabsf(hv.y)), fmaxf(fabsf(hv.z), fabsf(hv.w))));
+    }
+    hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, 1));  // the 4 lanes of row g
+    hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, 2));
+    const float dg = inv_pow2_of(hm);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      float4* p = reinterpret_cast<float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      const float4 hv = *p;
+      *p = make_float4(dg * hv.x, dg * hv.y, dg * hv.z, dg * hv.w);
+    }
+    if (L.q == 0) {
+      c.tks[L.g] *= dg;
+      c.dsc[L.g] = 1.f / dg;
+    }
+    __syncwarp();
+
+    // ---- Gram, inverse, Q (as the TF32 kernel, on the scaled channel)
+    int fl = 0;
+    float e[4];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      w[s][0] = hv.x;
+      w[s][1] = hv.z;
+      w[s][2] = -hv.y;
+      w[s][3] = -hv.w;
+    }
+    S::template residual<false>(L, Hs, nullptr, nullptr, w, c.tks, false, e);  // G'^T
+    float gi[4];
+    const bool fast = S::gram_inverse(L, e, A.cond_thr, gi);
+    float qt[8][4];
+    bool singular = false;
+    if (fast) {
+      const float tg = c.tks[L.g];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) q_tile(L, Hs, gi, tg, nt, qt[nt], w[nt]);
+    } else {
+      fl = Base::fp64_inverse(c);
+      singular = (fl & PRECODE_F_SINGULAR) != 0;
+      if (!singular) {
+        const double2* Gi = reinterpret_cast<const double2*>(c.red);
+#pragma unroll 1
+        for (int idx = L.lane; idx < KB * MB; idx += 32) {
+          const int k = idx / MB, m = idx - k * MB;
+          double zr = 0.0, zi = 0.0;
+#pragma unroll
+          for (int l = 0; l < KB; ++l) {
+            const double2 gkl = Gi[k * KB + l];
+            const float2 x = Hs[l * MB + m];
+            zr += gkl.x * x.x - gkl.y * x.y;
+            zi += gkl.x * x.y + gkl.y * x.x;
+          }
+          c.Qs[idx] = make_float2((float)zr, (float)-zi);
+        }
+        __syncwarp();
+      }
+      const float tg = c.tks[L.g];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float2 x0 = singular ? make_float2(0.f, 0.f) : c.Qs[(2 * L.q) * MB + 8 * nt + L.g];
+        const float2 x1 = singular ? make_float2(0.f, 0.f) : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+        qt[nt][0] = x0.x;
+        qt[nt][1] = x1.x;
+        qt[nt][2] = x0.y;
+        qt[nt][3] = x1.y;
+        const float4 qv = singular ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : *reinterpret_cast<const float4*>(c.Qs + L.g * MB + 8 * nt + 2 * L.q);
+        w[nt][0] = tg * qv.x;
+        w[nt][1] = tg * qv.z;
+        w[nt][2] = tg * qv.y;
+        w[nt][3] = tg * qv.w;
+      }
+    }
+    // ---- range of Q', then the global scale b from W^(0)' and t'
+    float qm = 0.f, wm = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        qm = fmaxf(qm, fabsf(qt[nt][k]));
+        wm = fmaxf(wm, fabsf(w[nt][k]));
+      }
+    qm = warp_max(qm);
+    wm = warp_max(fmaxf(wm, fabsf(c.tks[L.lane & 7])));
+    if (qm > QMAX && qm <= FLT_MAX) {  // beyond what FP16 fragments hold: reported as singular
+      fl |= PRECODE_F_SINGULAR;
+      singular = true;
+    }
+    beta = 128.f * inv_pow2_of(wm);
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[s][k] = singular ? 0.f : beta * w[s][k];
+    // ---- own channel entries, then the layer buffers over the setup buffers
+    float4 hv[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+    __syncwarp();  // every read of the raw channel, of Q and of t' done
+    if (L.lane < KB) c.tks[L.lane] *= beta;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      uint32_t rh, rl, ih, il;
+      split_h2(qt[nt][0], qt[nt][1], rh, rl);
+      split_h2(qt[nt][2], qt[nt][3], ih, il);
+      xf[nt * 32 + L.lane] = make_uint4(rh, ih, rl, il);
+    }
+    uint4* const hh = reinterpret_cast<uint4*>(Hs);
+    uint4* const hl = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float4 a = hv[2 * p], b = hv[2 * p + 1];
+      uint32_t rah, ral, rbh, rbl, iah, ial, ibh, ibl;
+      split_h2(a.x, a.z, rah, ral);  // Re H', block 2p
+      split_h2(b.x, b.z, rbh, rbl);  // Re H', block 2p+1
+      split_h2(a.y, a.w, iah, ial);  // Im H', block 2p
+      split_h2(b.y, b.w, ibh, ibl);  // Im H', block 2p+1
+      hh[p * 32 + L.lane] = make_uint4(rah, rbh, iah, ibh);
+      hl[p * 32 + L.lane] = make_uint4(ral, rbl, ial, ibl);
+    }
+    __syncwarp();
+    return fl;
+  }
+
+  __device__ static void run(const SolveArgs& A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Ctx c;
+    Lane L;
+    const int tid = threadIdx.x;
+    c.gid = tid >> 5;
+    c.g = tid & 31;
+    c.b = c.g % 8;
+    c.a = c.g / 8;
+    c.lane = tid & 31;
+    c.wig = 0;
+    c.wmask = 0xffffffffu;
+    c.K = KB;
+    c.M = MB;
+    L.lane = c.lane;
+    L.g = c.lane >> 2;
+    L.q = c.lane & 3;
+    unsigned char* gs = smem + c.gid * GROUP_STRIDE;
+    c.Hs = reinterpret_cast<float2*>(gs);
+    c.Qs = reinterpret_cast<float2*>(gs + OFF_Q);
+    c.red = reinterpret_cast<float*>(gs + OFF_RED);
+    c.Es = reinterpret_cast<float2*>(gs + OFF_E);
+    c.nrm = nullptr;
+    c.tks = reinterpret_cast<float*>(gs + OFF_SC);
+    c.dsc = c.tks + KB;
+    c.piv = c.dsc + KB;
+    c.misc = reinterpret_cast<int*>(c.piv + KB);
+    c.wsum = reinterpret_cast<float*>(c.misc + 8);
+    c.bar = reinterpret_cast<uint64_t*>(gs + OFF_BAR);
+    uint4* const xf = reinterpret_cast<uint4*>(gs + OFF_XF);
+    const uint4* const hh = reinterpret_cast<const uint4*>(gs);
+    const uint4* const hl = reinterpret_cast<const uint4*>(gs + OFF_HL);
+    float* const nb = reinterpret_cast<float*>(gs + OFF_NB);
+    float* const fb = reinterpret_cast<float*>(gs + OFF_FB);
+    if (c.g == 0) mbar_init(c.bar, 1);
+    fence_mbar_init();
+    __syncthreads();
+
+    uint32_t phase = 0;
+    const int64_t n_inst = A.tbl ? (int64_t)(*A.count) : A.B;
+    const int64_t stride = (int64_t)gridDim.x * NW;
+    auto locate = [&](int64_t it, int64_t& inst, int64_t& h_off, int64_t& w_off, int64_t& t_off) {
+      if (A.tbl) {
+        inst = A.index[it];
+        const InstDesc d = A.tbl[inst];
+        h_off = d.h_off;
+        w_off = d.w_off;
+        t_off = d.t_off;
+      } else {
+        inst = it;
+        h_off = it * (int64_t)(KB * MB);
+        w_off = h_off;
+        t_off = it * A.t_stride;
+      }
+    };
+    auto issue_copy = [&](int64_t it) {
+      if (c.g != 0 || it >= n_inst) return;
+      int64_t inst, h_off, w_off, t_off;
+      locate(it, inst, h_off, w_off, t_off);
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(c.bar, KB * MB * 8);
+      bulk_g2s(c.Hs, A.H + h_off, KB * MB * 8, c.bar);
+    };
+    const int64_t first = (int64_t)blockIdx.x * NW + c.gid;
+    issue_copy(first);
+    WT w;
+    float e[4];
+#pragma unroll 1
+    for (int64_t it = first; it < n_inst; it += stride) {
+      int64_t inst, h_off, w_off, t_off;
+      locate(it, inst, h_off, w_off, t_off);
+      __syncwarp();
+      if (c.g < KB) c.tks[c.g] = A.t[t_off + c.g];
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+      __syncwarp();
+      if (c.misc[0] == 0) {
+        if (c.g == 0) {
+          atomicAdd(A.err, 1ull);
+          if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
+          c.misc[1] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+        }
+        __syncwarp();
+        if (c.misc[1] == 0) return;
+        phase ^= 1u;
+        issue_copy(it + stride);
+        continue;
+      }
+      if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);
+      phase ^= 1u;
+
+      float beta;
+      int fl = setup(c, L, A, xf, w, beta);
+      const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
+      const float f_out = 1.f / beta;
+
+      // ---- layers (scaled units)
+      const int T = A.T;
+      float rs = 0.f;
+      if (!singular) {
+#pragma unroll 1
+        for (int l = 0; l < T; ++l) {
+          S::shrink(L, fb, S::colsum(L, nb, w), fmaxf(__ldg(A.step + l), 0.f) * beta, w);
+          residual_h(L, hh, hl, w, e);
+          if (2 * L.q == L.g) e[0] -= c.tks[L.g];
+          if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
+          update_h(L, xf, e, w);
+        }
+        if (A.resid) {
+          residual_h(L, hh, hl, w, e);
+          if (2 * L.q == L.g) e[0] -= c.tks[L.g];
+          if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
+          // E' = b E D: columns 2q, 2q + 1 back to E (up to the 1 / b applied below)
+          const float d0 = c.dsc[2 * L.q], d1 = c.dsc[2 * L.q + 1];
+          rs = d0 * d0 * (e[0] * e[0] + e[2] * e[2]) + d1 * d1 * (e[1] * e[1] + e[3] * e[3]);
+#pragma unroll
+          for (int msk = 1; msk < 32; msk <<= 1) rs += __shfl_xor_sync(0xffffffffu, rs, msk);
+        }
+      } else {
+        for (int k = 0; k < KB; ++k) rs += (c.tks[k] * c.dsc[k]) * (c.tks[k] * c.dsc[k]);
+      }
+
+      // ---- channel buffer free: next copy, then objective and W (original units)
+      __syncwarp();
+      issue_copy(it + stride);
+      const float2 r2 = S::colsum(L, nb, w);
+      float o = sqrtf(r2.x) + sqrtf(r2.y);
+#pragma unroll
+      for (int msk = 1; msk < 32; msk <<= 1) o += __shfl_xor_sync(0xffffffffu, o, msk);
+#pragma unroll
+      for (int s = 0; s < 8; ++s)
+        *reinterpret_cast<float4*>(A.W + w_off + L.g * MB + 8 * s + 2 * L.q) =
+            make_float4(f_out * w[s][0], f_out * w[s][2], f_out * w[s][1], f_out * w[s][3]);
+      if (c.g == 0) {
+        o *= f_out;
+        const float res = sqrtf(rs) * f_out;
+        if (!(o < FLT_MAX) || !(res < FLT_MAX)) fl |= PRECODE_F_NONFINITE;
+        if (A.obj) A.obj[inst] = o;
+        if (A.resid) A.resid[inst] = res;
+        if (A.flags) A.flags[inst] = fl;
+      }
+      __syncwarp();  // norm partials read out before the next instance
+    }
+  }
+};
+
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) solve_tch_kernel(SolveArgs A) {
+  SolveTCH<NW>::run(A);
+}
+
+}  // namespace precode

@@ -291,12 +291,27 @@ def test_fixed_workload_full_size_sampled(pc, orc):
 
 # ---------------------------------------------------------------- tensor-core build (K=8, M=64)
 
-@pytest.mark.parametrize("mode", ["proj", "pgd"])
-def test_tensor_core_variant_parity(pc, orc, mode):
-    """Warp-MMA build with split-TF32 operands: same tolerances as the FP32 build."""
+def tf32_build(tmp_path, capi):
+    """Plan options that pin the projected layer at K = 8, M = 64 to the split-TF32
+    build (the split-FP16 build is that shape's default)."""
+    path = tmp_path / "tune_tf32.txt"
+    path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|8|64\t"
+                    "8x64/4x8/jc8/w4/b3/split/tc/exact\n")
+    return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
+
+
+def build_kw(tmp_path, capi, build):
+    return tf32_build(tmp_path, capi) if build == "tf32" else dict(tensor_cores=True)
+
+
+@pytest.mark.parametrize("mode", ["proj", "proj_tf32", "pgd"])
+def test_tensor_core_variant_parity(pc, orc, tmp_path, mode):
+    """Warp-MMA builds (split FP16 / split TF32 operands): same tolerances as the
+    FP32 build."""
     capi, precoder = pc
     B = 1000
-    if mode == "proj":
+    kw = tf32_build(tmp_path, capi) if mode == "proj_tf32" else dict(tensor_cores=True)
+    if mode.startswith("proj"):
         H = ch.lognormal(B, 8, 64, seed=2)
         t = ch.targets(B, 8)
         step, lam, m = ch.fixed_workload_steps(10), None, capi.LAYER_PROJ
@@ -306,21 +321,26 @@ def test_tensor_core_variant_parity(pc, orc, mode):
         L = 1 / ch.paper_eta(8, 64)
         step = np.linspace(1 / L, 1 / (2 * L), 20).astype(np.float32)
         lam, m = np.full(20, 1 / 15, np.float32), capi.LAYER_PGD
-    gpu = run_gpu(precoder, m, H, t, step, lam, tensor_cores=True)
-    ref = oracle_ref(orc, 1 if mode == "proj" else 0, H, t, step, lam)
+    if mode == "proj_tf32":
+        plan = precoder.Plan(m, len(step), [(64, 8)], B, **kw)
+        assert capi.precode_plan_describe(plan.handle, 64, 8).startswith("solve_tc_kernel<1")
+        plan.close()
+    gpu = run_gpu(precoder, m, H, t, step, lam, **kw)
+    ref = oracle_ref(orc, 0 if mode == "pgd" else 1, H, t, step, lam)
     e, eo = assert_parity(gpu, ref)
-    if mode == "proj":
+    if mode != "pgd":
         assert np.all(gpu[2] <= 1e-4 * math.sqrt(8))
 
 
-def test_tensor_core_variant_flags_and_uneven(pc, orc):
+@pytest.mark.parametrize("build", ["default", "tf32"])
+def test_tensor_core_variant_flags_and_uneven(pc, orc, tmp_path, build):
     capi, precoder = pc
     H = ch.rayleigh(40, 8, 64, seed=23)
     H[3, 5] = H[3, 2]   # singular
     H[7, 1, 9] = np.inf  # non-finite
     t = ch.targets(40, 8)
     mu = np.full(6, 0.05, np.float32)
-    W, obj, res, fl = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, tensor_cores=True)
+    W, obj, res, fl = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **build_kw(tmp_path, capi, build))
     assert fl[3] & capi.F_SINGULAR and not np.any(W[3]) and obj[3] == 0
     assert fl[7] & capi.F_NONFINITE
     ok = [b for b in range(40) if b not in (3, 7)]
@@ -328,7 +348,118 @@ def test_tensor_core_variant_flags_and_uneven(pc, orc):
     assert_parity((W[ok], obj[ok], res[ok], fl[ok]), oracle_ref(orc, 1, H[ok], t[ok], mu))
 
 
-def test_tensor_core_ill_conditioned_uses_fp64(pc, orc):
+# Split-FP16 build of the projected layer (K = 8, M = 64), forced through an
+# autotune cache entry naming it; each instance runs in power-of-two scaled units.
+TCH_BUILDS = [3, 4]  # CTAs per SM the register budget is built for
+
+
+def forced_tch(tmp_path, capi, minb):
+    path = tmp_path / "tune.txt"
+    path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|8|64\t"
+                    f"8x64/4x8/jc8/w4/b{minb}/split/tc/f16/exact\n")
+    return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
+
+
+def run_tch(capi, precoder, kw, H, t, mu, **extra):
+    B = len(H)
+    plan = precoder.Plan(capi.LAYER_PROJ, len(mu), [(64, 8)], max(B, 1), **kw, **extra)
+    assert capi.precode_plan_describe(plan.handle, 64, 8).startswith("solve_tch_kernel")
+    plan.close()
+    return run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **kw, **extra)
+
+
+@pytest.mark.parametrize("minb", TCH_BUILDS)
+def test_fp16_split_parity(pc, orc, tmp_path, minb):
+    """Log-normal user gains (8 dB), T = 10 with the fixed workload's steps, B = 999
+    (ragged last block): the FP32 tolerances against the FP64 oracle."""
+    capi, precoder = pc
+    kw = forced_tch(tmp_path, capi, minb)
+    H = ch.lognormal(999, 8, 64, seed=41)
+    t = ch.targets(999, 8)
+    mu = ch.fixed_workload_steps(10)
+    gpu = run_tch(capi, precoder, kw, H, t, mu)
+    assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
+    assert np.all(gpu[2] <= 1e-4 * math.sqrt(8)) and np.all(gpu[3] == 0)
+
+
+def test_fp16_split_scale_invariant(pc, orc, tmp_path):
+    """Channels and targets scaled together by 1e-6 .. 1e6 per instance (W keeps its
+    size, so the same mu does work everywhere): the per-instance power-of-two
+    scaling keeps every instance at the same accuracy."""
+    capi, precoder = pc
+    kw = forced_tch(tmp_path, capi, 4)
+    sc = 10.0 ** np.random.default_rng(42).uniform(-6, 6, size=128)
+    H = (ch.rayleigh(128, 8, 64, seed=43) * sc[:, None, None]).astype(np.complex64)
+    t = (ch.targets(128, 8) * sc[:, None]).astype(np.float32)
+    mu = np.full(6, 0.05, np.float32)
+    gpu = run_tch(capi, precoder, kw, H, t, mu)
+    assert np.all(gpu[3] == 0)
+    assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
+
+
+def test_fp16_split_wide_gain_spread(pc, orc, tmp_path):
+    """One user 1e-5 weaker than the rest (and another 1e-3 in every other
+    instance): without per-user scaling that user's channel row would sit in
+    FP16's subnormals; the Gram matrix is well conditioned after equilibration, so
+    the FP32 inverse is used."""
+    capi, precoder = pc
+    kw = forced_tch(tmp_path, capi, 4)
+    H = ch.rayleigh(32, 8, 64, seed=44)
+    H[:, 3] *= np.float32(1e-5)
+    H[::2, 6] *= np.float32(1e-3)
+    t = ch.targets(32, 8)
+    mu = np.full(8, 0.02, np.float32)
+    gpu = run_tch(capi, precoder, kw, H, t, mu)
+    assert np.all(gpu[3] == 0)
+    assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
+
+
+def test_fp16_split_flags_and_fp64(pc, orc, tmp_path):
+    """Singular and non-finite instances and ill-conditioned ones on the FP64 path."""
+    capi, precoder = pc
+    kw = forced_tch(tmp_path, capi, 4)
+    rs = np.random.default_rng(45)
+    H = ch.rayleigh(41, 8, 64, seed=46)
+    for b in range(10, 30, 2):
+        H[b, 5] = H[b, 2] + (1e-3 * (rs.standard_normal(64) + 1j * rs.standard_normal(64))).astype(np.complex64)
+    H[3, 5] = H[3, 2]    # singular
+    H[7, 1, 9] = np.inf  # non-finite
+    t = ch.targets(41, 8)
+    mu = np.full(6, 0.05, np.float32)
+    W, obj, res, fl = run_tch(capi, precoder, kw, H, t, mu, cond_threshold=1e3)
+    assert fl[3] & capi.F_SINGULAR and not np.any(W[3]) and obj[3] == 0
+    assert fl[7] & capi.F_NONFINITE
+    assert np.all(fl[10:30:2] == capi.F_FP64_CHOL)
+    ok = [b for b in range(41) if b not in (3, 7)]
+    well = [b for b in ok if not (10 <= b < 30 and b % 2 == 0)]
+    assert np.all(fl[well] == 0)
+    gpu, ref = (W[ok], obj[ok], res[ok], fl[ok]), oracle_ref(orc, 1, H[ok], t[ok], mu)
+    sel = np.isin(ok, well)
+    assert_parity(tuple(x[sel] for x in gpu), tuple(x[sel] for x in ref))
+    # the conditioning amplifies the rounding of the layers themselves
+    assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
+
+
+def test_fp16_split_full_size_sampled(pc, orc, tmp_path):
+    capi, precoder = pc
+    wl = ch.WORKLOADS["fixed"]
+    kw = forced_tch(tmp_path, capi, 4)
+    H = ch.lognormal(wl.B, wl.K, wl.M, seed=wl.seed)
+    t = ch.targets(wl.B, wl.K)
+    mu = ch.fixed_workload_steps(wl.T)
+    plan = precoder.Plan(capi.LAYER_PROJ, wl.T, [(wl.M, wl.K)], wl.B, **kw)
+    assert capi.precode_plan_describe(plan.handle, wl.M, wl.K).startswith("solve_tch_kernel")
+    W, obj, res, fl = plan.solve(torch.from_numpy(H).cuda(), torch.from_numpy(t).cuda(),
+                                 torch.from_numpy(mu).cuda())
+    W, obj, res, fl = W.cpu().numpy(), obj.cpu().numpy(), res.cpu().numpy(), fl.cpu().numpy()
+    plan.close()
+    idx = np.sort(np.random.default_rng(3).choice(wl.B, 256, replace=False))
+    assert_parity((W[idx], obj[idx], res[idx], fl[idx]), oracle_ref(orc, 1, H[idx], t[idx], mu))
+    assert np.all(res < 1e-4 * math.sqrt(wl.K)) and (fl != 0).mean() < 0.01
+
+
+@pytest.mark.parametrize("build", ["default", "tf32"])
+def test_tensor_core_ill_conditioned_uses_fp64(pc, orc, tmp_path, build):
     """K = 8, M = 64 with one almost collinear user pair in every other instance:
     the tensor-core kernel's register Gauss-Jordan flags the pivot spread and the
     FP64 setup forms Q instead; the rest keep the FP32 inverse and MMA-formed Q."""
@@ -339,7 +470,8 @@ def test_tensor_core_ill_conditioned_uses_fp64(pc, orc):
         H[b, 5] = H[b, 2] + (1e-3 * (rs.standard_normal(64) + 1j * rs.standard_normal(64))).astype(np.complex64)
     t = ch.targets(16, 8)
     mu = np.full(4, 0.02, np.float32)
-    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, cond_threshold=1e3, tensor_cores=True)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, cond_threshold=1e3,
+                  **build_kw(tmp_path, capi, build))
     assert np.all(gpu[3][0::2] == capi.F_FP64_CHOL)
     assert np.all(gpu[3][1::2] == 0)
     ref = oracle_ref(orc, 1, H, t, mu)
@@ -418,36 +550,39 @@ def test_tensor_core_large_flags_and_fp64(pc, orc):
                   w_tol=2e-3, obj_tol=2e-4)
 
 
-def test_tensor_core_kernels_independent_of_earlier_kernels(pc):
+def test_tensor_core_kernels_independent_of_earlier_kernels(pc, tmp_path):
     """Each tensor-core solve kernel gives bitwise the same output fresh and after
     other kernels (with other shared-memory layouts) ran on the device: every
     shared-memory operand is written before it is read."""
     capi, precoder = pc
-    cases = [(capi.LAYER_PROJ, 8, 64), (capi.LAYER_PGD, 8, 64), (capi.LAYER_PROJ, 16, 128),
-             (capi.LAYER_PROJ, 32, 256), (capi.LAYER_PROJ, 13, 64)]
+    cases = [(capi.LAYER_PROJ, 8, 64, "default"), (capi.LAYER_PROJ, 8, 64, "tf32"),
+             (capi.LAYER_PGD, 8, 64, "default"), (capi.LAYER_PROJ, 16, 128, "default"),
+             (capi.LAYER_PROJ, 32, 256, "default"), (capi.LAYER_PROJ, 13, 64, "default")]
     runs = {}
     for rep in range(2):
-        for mode, K, M in (cases if rep == 0 else cases[::-1]):
+        for mode, K, M, build in (cases if rep == 0 else cases[::-1]):
             H = ch.rician_ula(600, K, M, seed=70 + K)
             t = ch.targets(600, K)
             step = ch.uniform_steps(6, 0.01, 0.1, seed=7) if mode == capi.LAYER_PROJ else \
                 np.full(6, ch.paper_eta(K, M), np.float32)
             lam = None if mode == capi.LAYER_PROJ else np.full(6, 1 / 15, np.float32)
-            out = run_gpu(precoder, mode, H, t, step, lam, tensor_cores=True)
+            out = run_gpu(precoder, mode, H, t, step, lam, **build_kw(tmp_path, capi, build))
             if rep == 0:
-                runs[(mode, K, M)] = out
+                runs[(mode, K, M, build)] = out
             else:
-                for a, b in zip(out, runs[(mode, K, M)]):
-                    assert np.array_equal(a, b), (mode, K, M)
+                for a, b in zip(out, runs[(mode, K, M, build)]):
+                    assert np.array_equal(a, b), (mode, K, M, build)
 
 
-def test_tensor_core_full_size_sampled(pc, orc):
+def test_tensor_core_full_size_sampled(pc, orc, tmp_path):
+    """The split-TF32 build on the full fixed workload (the split-FP16 build has its
+    own full-size test)."""
     capi, precoder = pc
     wl = ch.WORKLOADS["fixed"]
     H = ch.lognormal(wl.B, wl.K, wl.M, seed=wl.seed)
     t = ch.targets(wl.B, wl.K)
     mu = ch.fixed_workload_steps(wl.T)
-    plan = precoder.Plan(capi.LAYER_PROJ, wl.T, [(wl.M, wl.K)], wl.B, tensor_cores=True)
+    plan = precoder.Plan(capi.LAYER_PROJ, wl.T, [(wl.M, wl.K)], wl.B, **tf32_build(tmp_path, capi))
     assert "solve_tc_kernel" in capi.precode_plan_describe(plan.handle, wl.M, wl.K)
     W, obj, res, fl = plan.solve(torch.from_numpy(H).cuda(), torch.from_numpy(t).cuda(),
                                  torch.from_numpy(mu).cuda())
