@@ -6,8 +6,8 @@ targets, T=10 projected layers with per-layer steps mu_t drawn once from
 U[0.01, 0.1] (seed 2).  One step = one pass of the whole hot path over the
 batch: channel load, Gram matrix, its equilibrated inverse, Q = G^{-T} H^* and
 the ZF start, 10 layers (shrink, residual, projection), objective, residual, W
-write-back.  It is one persistent kernel launch (the tensor-core kernel for
-K = 8, M = 64).  Inputs stay resident in HBM (268 MB of H, larger
+write-back.  It is one persistent kernel launch (the split-FP16 tensor-core
+kernel for K = 8, M = 64; --tf32 pins the split-TF32 build instead).  Inputs stay resident in HBM (268 MB of H, larger
 than the 129 MB L2; W is another 268 MB), so no L2 flush is needed between steps.
 
 Lines printed (rank 0, one JSON line):
@@ -16,7 +16,8 @@ Lines printed (rank 0, one JSON line):
              (host->device, solve, device->host inside the timed region)
   roofline   FP32 FMA-pipe roofline of the solve kernel (the path is
              arithmetic-bound: ~86 flop per HBM byte); on the tensor-core
-             kernel also the issued split-TF32 MMA rate against the TF32 peak
+             kernels also the issued MMA work against the dense tensor peaks
+             (split FP16 layers and split TF32 setup; or all split TF32)
   cpu_baseline  the FP64 oracle on this host's cores, bounded sample
   pa_gap     relative PA-consumption (||W||_{2,1}) difference GPU vs oracle on
              that sample, and the mean PCG of the GPU output
@@ -457,6 +458,9 @@ def main():
                     help="skip the uneven, training and serving sub-benchmarks")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default kernel variant (no tuning launches; for profiling)")
+    ap.add_argument("--tf32", action="store_true",
+                    help="pin the headline shape to the split-TF32 tensor-core build (the "
+                         "split-FP16 build is its default); for profiling and comparison")
     ap.add_argument("--bucket", default=None, metavar="MxK",
                     help="profiling aid: solve one uniform bucket of Rician channels (autotuned "
                          "plan), the last solve inside an NVTX range 'prof', print one line, exit")
@@ -483,7 +487,15 @@ def main():
     H = ch.lognormal(B, K, M, seed=wl.seed + 1000 * rank)
     t = ch.targets(B, K)
     mu = ch.fixed_workload_steps(T)
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=not args.no_autotune, tensor_cores=True)
+    if args.tf32:  # an autotune cache entry naming the split-TF32 build
+        cache = os.path.join(tempfile.mkdtemp(), "tune.txt")
+        with open(cache, "w") as f:
+            f.write(f"{torch.cuda.get_device_name(local)}|{capi.LAYER_PROJ}|{K}|{M}\t"
+                    f"{K}x{M}/4x8/jc8/w4/b3/split/tc/exact\n")
+        plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=True, tensor_cores=True,
+                    tune_cache=cache)
+    else:
+        plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=not args.no_autotune, tensor_cores=True)
     Hd = torch.from_numpy(H).cuda()
     td = torch.from_numpy(t).cuda()
     md = torch.from_numpy(mu).cuda()

@@ -69,7 +69,11 @@ typedef enum {
                                    threshold (or FP32 pivot failed): Gram, Cholesky and
                                    G^{-1} were redone in FP64 */
 #define PRECODE_F_SINGULAR 2    /* PROJ: Gram not positive definite even in FP64
-                                   (rank(H) < K): W set to 0, obj 0, resid ||S||_F */
+                                   (rank(H) < K): W set to 0, obj 0, resid ||S||_F.
+                                   The split-FP16 build (K = 8, M = 64) also sets it when
+                                   an entry of Q = G^{-T} H^* in its scaled units exceeds
+                                   2^13 (an equilibrated Gram condition far beyond FP32
+                                   accuracy, met only on the FP64 path) */
 #define PRECODE_F_NONFINITE 4   /* NaN/Inf met in the input or the output objective */
 #define PRECODE_F_TIMEOUT 8     /* the device-side wait for this instance's channel copy
                                    ran out (about 1 s); W not written */
@@ -90,7 +94,11 @@ typedef enum {
 
 #define PRECODE_PLAN_TENSOR_CORES 8u    /* for shapes with a tensor-core build (8x64, 16x128, 32x256) use it:
                                            contractions as warp MMAs on TF32 operands split
-                                           in three terms (products accurate to ~2^-21 rel.) */
+                                           in three terms (products accurate to ~2^-21 rel.);
+                                           the projected layer at K = 8, M = 64 defaults to
+                                           the split-FP16 build (two FP16 terms per value,
+                                           ~2^-22 rel., each instance in exact power-of-two
+                                           units that keep it inside the FP16 range) */
 
 #define PRECODE_MAX_K 32
 #define PRECODE_MAX_M 256
