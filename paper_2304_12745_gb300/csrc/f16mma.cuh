@@ -24,6 +24,18 @@ __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint3
   lo = h2_bits(__floats2half2_rn(x0 - hf.x, x1 - hf.y));
 }
 
+// The same split with its first conversion kept in program order among the
+// other splits (volatile): in long unrolled loops that hold a large W in
+// registers this stops the scheduler from computing many splits ahead of their
+// MMAs (and spilling for it).
+__device__ __forceinline__ void split_h2_ordered(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  uint32_t h;
+  asm volatile("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));  // x0 in the low half
+  const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&h));
+  hi = h;
+  lo = h2_bits(__floats2half2_rn(x0 - hf.x, x1 - hf.y));
+}
+
 __device__ __forceinline__ uint32_t neg_h2(uint32_t x) { return x ^ 0x80008000u; }
 
 // d += a . b  (m16n8k16, row.col, FP16 in, FP32 accumulate)

@@ -52,6 +52,7 @@ const std::vector<TrainVariant>& train_variants();
 void register_solve_proj(std::vector<Variant>& v);
 void register_solve_tc(std::vector<Variant>& v);
 void register_solve_tch(std::vector<Variant>& v);
+void register_solve_tcwh(std::vector<Variant>& v);
 void register_solve_tcw_64(std::vector<Variant>& v);
 void register_solve_tcw_128(std::vector<Variant>& v);
 void register_solve_tcw_256(std::vector<Variant>& v);

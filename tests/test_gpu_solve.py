@@ -300,8 +300,10 @@ def tf32_build(tmp_path, capi):
     return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
 
 
-def build_kw(tmp_path, capi, build):
-    return tf32_build(tmp_path, capi) if build == "tf32" else dict(tensor_cores=True)
+def build_kw(tmp_path, capi, build, M=64, K=8):
+    if build != "tf32":
+        return dict(tensor_cores=True)
+    return tf32_build(tmp_path, capi) if (M, K) == (64, 8) else tcw_tf32_build(tmp_path, capi, M, K)
 
 
 @pytest.mark.parametrize("mode", ["proj", "proj_tf32", "pgd"])
@@ -458,6 +460,94 @@ def test_fp16_split_full_size_sampled(pc, orc, tmp_path):
     assert np.all(res < 1e-4 * math.sqrt(wl.K)) and (fl != 0).mean() < 0.01
 
 
+# Multi-warp split-FP16 builds (projected layer; exact bucket shapes and user-padded
+# builds), forced through an autotune cache entry naming the build.
+TCWH_BUILDS = [  # (M, K, KW, CTAs per SM, exact)
+    (256, 32, 4, 2, True), (128, 16, 2, 6, True), (256, 27, 4, 2, False), (128, 11, 2, 6, False),
+    (64, 29, 4, 4, False), (64, 13, 2, 8, False)]
+
+
+def forced_tcwh(tmp_path, capi, M, K, kw, minb, exact):
+    path = tmp_path / "tune_tcwh.txt"
+    key = f"{8 * kw}x{M}/{kw}x8/jc8/w{kw}/b{minb}/split/tc/f16/{'exact' if exact else 'generic'}"
+    path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|{K}|{M}\t{key}\n")
+    return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
+
+
+def run_tcwh(capi, precoder, kw, H, t, mu, **extra):
+    B, K, M = H.shape
+    plan = precoder.Plan(capi.LAYER_PROJ, len(mu), [(M, K)], max(B, 1), **kw, **extra)
+    assert capi.precode_plan_describe(plan.handle, M, K).startswith("solve_tcwh_kernel")
+    plan.close()
+    return run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **kw, **extra)
+
+
+@pytest.mark.parametrize("M,K,kw,minb,exact", TCWH_BUILDS)
+def test_fp16_multiwarp_parity(pc, orc, tmp_path, M, K, kw, minb, exact):
+    """Rician channels (K-factor 0-10 dB, ULA), T = 10 uniform steps: the FP32
+    tolerances against the FP64 oracle, exact and user-padded builds."""
+    capi, precoder = pc
+    B = 300 if M == 256 else 600
+    H = ch.rician_ula(B, K, M, seed=50 + K)
+    t = ch.targets(B, K)
+    mu = ch.uniform_steps(10, 0.01, 0.1, seed=51)
+    gpu = run_tcwh(capi, precoder, forced_tcwh(tmp_path, capi, M, K, kw, minb, exact), H, t, mu)
+    assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
+    assert np.all(gpu[2] <= 1e-4 * math.sqrt(K))
+
+
+def test_fp16_multiwarp_scales_and_gain_spread(pc, orc, tmp_path):
+    """Channels and targets over 1e-5 .. 1e5 together per instance, and one user
+    1e-4 weaker than the rest in every other instance."""
+    capi, precoder = pc
+    M, K = 128, 16
+    kw = forced_tcwh(tmp_path, capi, M, K, 2, 6, True)
+    sc = 10.0 ** np.random.default_rng(52).uniform(-5, 5, size=200)
+    H = (ch.rayleigh(200, K, M, seed=53) * sc[:, None, None]).astype(np.complex64)
+    H[::2, 5] *= np.float32(1e-4)
+    t = (ch.targets(200, K) * sc[:, None]).astype(np.float32)
+    mu = np.full(8, 0.03, np.float32)
+    gpu = run_tcwh(capi, precoder, kw, H, t, mu)
+    assert np.all(gpu[3] == 0)
+    assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_fp16_multiwarp_flags_and_fp64(pc, orc, tmp_path, eps):
+    """Singular and non-finite instances and ill-conditioned ones on the FP64 path
+    (near-collinear user pairs eps apart: F' = E' G'^{-T} grows with the condition,
+    and the per-warp range check moves powers of two onto the channel operand or,
+    at eps = 1e-4 (condition ~1e8), runs those layers' update as split TF32)."""
+    capi, precoder = pc
+    M, K = 256, 32
+    kw = forced_tcwh(tmp_path, capi, M, K, 4, 2, True)
+    rs = np.random.default_rng(54)
+    H = ch.rayleigh(24, K, M, seed=55)
+    for b in range(8, 20, 2):
+        H[b, 9] = H[b, 4] + (eps * (rs.standard_normal(M) + 1j * rs.standard_normal(M))).astype(np.complex64)
+    H[3, 7] = H[3, 2]    # singular
+    H[5, 1, 9] = np.inf  # non-finite
+    t = ch.targets(24, K)
+    mu = np.full(6, 0.05, np.float32)
+    W, obj, res, fl = run_tcwh(capi, precoder, kw, H, t, mu, cond_threshold=1e3)
+    assert fl[3] & capi.F_SINGULAR and not np.any(W[3]) and obj[3] == 0
+    assert fl[5] & capi.F_NONFINITE
+    assert np.all(fl[8:20:2] == capi.F_FP64_CHOL)
+    ok = [b for b in range(24) if b not in (3, 5)]
+    well = [b for b in ok if not (8 <= b < 20 and b % 2 == 0)]
+    assert np.all(fl[well] == 0)
+    gpu, ref = (W[ok], obj[ok], res[ok], fl[ok]), oracle_ref(orc, 1, H[ok], t[ok], mu)
+    sel = np.isin(ok, well)
+    assert_parity(tuple(x[sel] for x in gpu), tuple(x[sel] for x in ref))
+    assert np.all(np.isfinite(W[ok])) and np.all(np.isfinite(obj[ok]))
+    if eps >= 1e-3:
+        # the conditioning amplifies the rounding of the layers themselves
+        assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
+    # (at eps = 1e-4 the Gram condition is ~1e8: no layer map carried at FP32
+    # precision is accurate there; what is checked is that those instances are
+    # flagged and their outputs stay finite)
+
+
 @pytest.mark.parametrize("build", ["default", "tf32"])
 def test_tensor_core_ill_conditioned_uses_fp64(pc, orc, tmp_path, build):
     """K = 8, M = 64 with one almost collinear user pair in every other instance:
@@ -480,14 +570,28 @@ def test_tensor_core_ill_conditioned_uses_fp64(pc, orc, tmp_path, build):
     assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
 
 
+def tcw_tf32_build(tmp_path, capi, M, K, exact=True):
+    """Plan options that pin a multi-warp bucket of the projected layer to its
+    split-TF32 build (the split-FP16 build is the default there)."""
+    kw = -(-K // 8)
+    minb = {64: {1: 16, 2: 8, 3: 5, 4: 4}, 128: {1: 12, 2: 6, 3: 4, 4: 3},
+            256: {1: 8, 2: 4, 3: 2, 4: 2}}[M][kw]
+    path = tmp_path / "tune_tcw32.txt"
+    path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|{K}|{M}\t"
+                    f"{8 * kw}x{M}/{kw}x8/jc8/w{kw}/b{minb}/split/tc/{'exact' if exact else 'generic'}\n")
+    return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
+
+
 @pytest.mark.parametrize("K,M,B", [(16, 128, 2600), (32, 256, 700)])
-@pytest.mark.parametrize("mode", ["proj", "pgd"])
-def test_tensor_core_large_buckets(pc, orc, K, M, B, mode):
-    """Multi-warp tensor-core build (one CTA of K/8 warps per instance) against the
-    oracle, over more instances than one persistent round, so CTAs take a ragged
-    number of instances."""
+@pytest.mark.parametrize("mode", ["proj", "proj_tf32", "pgd"])
+def test_tensor_core_large_buckets(pc, orc, tmp_path, K, M, B, mode):
+    """Multi-warp tensor-core builds (one CTA of K/8 warps per instance; split FP16
+    by default for the projected layer, split TF32 pinned, split TF32 for the paper
+    layer) against the oracle, over more instances than one persistent round, so
+    CTAs take a ragged number of instances."""
     capi, precoder = pc
-    if mode == "proj":
+    kw = tcw_tf32_build(tmp_path, capi, M, K) if mode == "proj_tf32" else dict(tensor_cores=True)
+    if mode.startswith("proj"):
         H = ch.rician_ula(B, K, M, seed=5)
         t = ch.targets(B, K)
         step, lam, m = ch.uniform_steps(10, 0.01, 0.1, seed=7), None, capi.LAYER_PROJ
@@ -497,13 +601,20 @@ def test_tensor_core_large_buckets(pc, orc, K, M, B, mode):
         L = 1 / ch.paper_eta(K, M)
         step = np.linspace(1 / L, 1 / (2 * L), 10).astype(np.float32)
         lam, m = np.full(10, 1 / 15, np.float32), capi.LAYER_PGD
-    gpu = run_gpu(precoder, m, H, t, step, lam, tensor_cores=True)
-    ref = oracle_ref(orc, 1 if mode == "proj" else 0, H, t, step, lam)
+    plan = precoder.Plan(m, len(step), [(M, K)], B, **kw)
+    name = capi.precode_plan_describe(plan.handle, M, K)
+    plan.close()
+    assert name.startswith("solve_tcwh_kernel" if mode == "proj" else "solve_tcw_kernel"), name
+    gpu = run_gpu(precoder, m, H, t, step, lam, **kw)
+    ref = oracle_ref(orc, 0 if mode == "pgd" else 1, H, t, step, lam)
     assert_parity(gpu, ref)
 
 
-@pytest.mark.parametrize("K,M", [(5, 64), (13, 64), (27, 64), (3, 128), (20, 128), (9, 256), (27, 256)])
-def test_tensor_core_padded_users(pc, orc, K, M):
+@pytest.mark.parametrize("K,M,build", [(5, 64, "default"), (13, 64, "default"), (27, 64, "default"),
+                                       (3, 128, "default"), (20, 128, "default"), (9, 256, "default"),
+                                       (27, 256, "default"), (13, 64, "tf32"), (20, 128, "tf32"),
+                                       (27, 256, "tf32")])
+def test_tensor_core_padded_users(pc, orc, tmp_path, K, M, build):
     """User-padded tensor-core builds (K < KB users at exactly MB antennas): the
     padded rows stay zero and the real users match the oracle."""
     capi, precoder = pc
@@ -511,10 +622,13 @@ def test_tensor_core_padded_users(pc, orc, K, M):
     H = ch.rician_ula(B, K, M, seed=30 + K)
     t = ch.targets(B, K)
     mu = ch.uniform_steps(10, 0.01, 0.1, seed=7)
-    plan = precoder.Plan(capi.LAYER_PROJ, 10, [(M, K)], B, tensor_cores=True)
-    assert capi.precode_plan_describe(plan.handle, M, K).startswith("solve_tcw_kernel")
+    kw = tcw_tf32_build(tmp_path, capi, M, K, exact=False) if build == "tf32" else dict(tensor_cores=True)
+    plan = precoder.Plan(capi.LAYER_PROJ, 10, [(M, K)], B, **kw)
+    name = capi.precode_plan_describe(plan.handle, M, K)
     plan.close()
-    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, tensor_cores=True)
+    # K <= 8 has only split-TF32 padded builds (one warp); 9..32 default to split FP16
+    assert name.startswith("solve_tcwh_kernel" if build == "default" and K > 8 else "solve_tcw_kernel"), name
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **kw)
     ref = oracle_ref(orc, 1, H, t, mu)
     ok = gpu[3] == 0
     assert ok.sum() > B // 2
@@ -524,8 +638,9 @@ def test_tensor_core_padded_users(pc, orc, K, M):
         assert_parity(tuple(x[~ok] for x in gpu), tuple(x[~ok] for x in ref), w_tol=2e-3, obj_tol=2e-4)
 
 
-def test_tensor_core_large_flags_and_fp64(pc, orc):
-    """32 x 256 on the multi-warp build: a singular Gram matrix, a non-finite
+@pytest.mark.parametrize("build", ["default", "tf32"])
+def test_tensor_core_large_flags_and_fp64(pc, orc, tmp_path, build):
+    """32 x 256 on the multi-warp builds: a singular Gram matrix, a non-finite
     input and near-collinear user pairs (FP64 Gauss-Jordan path)."""
     capi, precoder = pc
     rs = np.random.default_rng(8)
@@ -536,7 +651,8 @@ def test_tensor_core_large_flags_and_fp64(pc, orc):
         H[b, 20] = H[b, 11] + (1e-3 * (rs.standard_normal(256) + 1j * rs.standard_normal(256))).astype(np.complex64)
     t = ch.targets(24, 32)
     mu = np.full(4, 0.02, np.float32)
-    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, cond_threshold=1e3, tensor_cores=True)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, cond_threshold=1e3,
+                  **build_kw(tmp_path, capi, build, 256, 32))
     W, obj, res, fl = gpu
     assert fl[3] & capi.F_SINGULAR and fl[3] & capi.F_FP64_CHOL and not np.any(W[3])
     assert fl[5] & capi.F_NONFINITE
@@ -557,7 +673,8 @@ def test_tensor_core_kernels_independent_of_earlier_kernels(pc, tmp_path):
     capi, precoder = pc
     cases = [(capi.LAYER_PROJ, 8, 64, "default"), (capi.LAYER_PROJ, 8, 64, "tf32"),
              (capi.LAYER_PGD, 8, 64, "default"), (capi.LAYER_PROJ, 16, 128, "default"),
-             (capi.LAYER_PROJ, 32, 256, "default"), (capi.LAYER_PROJ, 13, 64, "default")]
+             (capi.LAYER_PROJ, 32, 256, "default"), (capi.LAYER_PROJ, 32, 256, "tf32"),
+             (capi.LAYER_PROJ, 13, 64, "default")]
     runs = {}
     for rep in range(2):
         for mode, K, M, build in (cases if rep == 0 else cases[::-1]):
@@ -566,7 +683,7 @@ def test_tensor_core_kernels_independent_of_earlier_kernels(pc, tmp_path):
             step = ch.uniform_steps(6, 0.01, 0.1, seed=7) if mode == capi.LAYER_PROJ else \
                 np.full(6, ch.paper_eta(K, M), np.float32)
             lam = None if mode == capi.LAYER_PROJ else np.full(6, 1 / 15, np.float32)
-            out = run_gpu(precoder, mode, H, t, step, lam, **build_kw(tmp_path, capi, build))
+            out = run_gpu(precoder, mode, H, t, step, lam, **build_kw(tmp_path, capi, build, M, K))
             if rep == 0:
                 runs[(mode, K, M, build)] = out
             else:
