@@ -396,7 +396,16 @@ def run_bucket(args):
     H = torch.from_numpy(ch.rician_ula(B, K, M, seed=5)).cuda()
     t = torch.ones(B, K, device="cuda")
     mu = torch.from_numpy(ch.uniform_steps(T, 0.01, 0.1, seed=2)).cuda()
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=True)
+    cache = None
+    if args.tf32:  # pin the bucket's split-TF32 tensor-core build
+        kw = -(-K // 8)
+        minb = {64: {1: 16, 2: 8, 3: 5, 4: 4}, 128: {1: 12, 2: 6, 3: 4, 4: 3},
+                256: {1: 8, 2: 4, 3: 2, 4: 2}}[M][kw]
+        cache = os.path.join(tempfile.mkdtemp(), "tune.txt")
+        with open(cache, "w") as f:
+            f.write(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|{K}|{M}\t"
+                    f"{8 * kw}x{M}/{kw}x8/jc8/w{kw}/b{minb}/split/tc/exact\n")
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=True, tune_cache=cache)
     out = (torch.empty_like(H), torch.empty(B, device="cuda"), None,
            torch.empty(B, device="cuda", dtype=torch.int32))
     for _ in range(2):
@@ -459,8 +468,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default kernel variant (no tuning launches; for profiling)")
     ap.add_argument("--tf32", action="store_true",
-                    help="pin the headline shape to the split-TF32 tensor-core build (the "
-                         "split-FP16 build is its default); for profiling and comparison")
+                    help="pin the headline shape (or the --bucket shape) to its split-TF32 "
+                         "tensor-core build (the split-FP16 builds are the defaults); for "
+                         "profiling and comparison")
     ap.add_argument("--bucket", default=None, metavar="MxK",
                     help="profiling aid: solve one uniform bucket of Rician channels (autotuned "
                          "plan), the last solve inside an NVTX range 'prof', print one line, exit")
