@@ -630,7 +630,9 @@ def main():
     line["e2e"] = {"value": world * B / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": int(H.nbytes + t.nbytes + 4 * T),
                    "d2h_bytes_per_step": int(H.nbytes + 3 * 4 * B),
-                   "api": "precode_solve_host (pinned host buffers, chunked copy/compute overlap)"}
+                   "api": "precode_solve_host (pinned host buffers: the zero-copy kernel reads H and "
+                          "writes W over the host link; pageable buffers would take the staged "
+                          "copy pipeline)"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, (lo, oobj) = cpu_baseline(H, t, mu)

@@ -53,6 +53,7 @@ void register_solve_proj(std::vector<Variant>& v);
 void register_solve_tc(std::vector<Variant>& v);
 void register_solve_tch(std::vector<Variant>& v);
 void register_solve_tcwh(std::vector<Variant>& v);
+const void* tch_host_kernel(int nw, int minb);  // host-buffer twin of a split-FP16 K=8 build
 void register_solve_tcw_64(std::vector<Variant>& v);
 void register_solve_tcw_128(std::vector<Variant>& v);
 void register_solve_tcw_256(std::vector<Variant>& v);

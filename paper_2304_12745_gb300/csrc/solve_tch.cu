@@ -15,4 +15,12 @@ void register_solve_tch(std::vector<Variant>& v) {
 #undef X
 }
 
+// The same builds reading H, t and writing W and the outputs with plain loads and
+// stores, for page-locked host buffers mapped into the device's address space.
+const void* tch_host_kernel(int nw, int minb) {
+  if (nw == 4 && minb == 3) return (const void*)&solve_tch_kernel<4, 3, true>;
+  if (nw == 4 && minb == 4) return (const void*)&solve_tch_kernel<4, 4, true>;
+  return nullptr;
+}
+
 }  // namespace precode

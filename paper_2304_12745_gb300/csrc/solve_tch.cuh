@@ -31,7 +31,10 @@
 
 namespace precode {
 
-template <int NW>
+// HOSTIO: the channel is read with plain 16-byte loads (no bulk async copy),
+// so H, W, t and the outputs may live in page-locked host memory mapped into the
+// device's address space (zero-copy over the host link).
+template <int NW, bool HOSTIO = false>
 struct SolveTCH : SolveTC<kModeProj, NW, false> {
   using S = SolveTC<kModeProj, NW, false>;
   using Base = typename S::Base;
@@ -372,7 +375,7 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
       }
     };
     auto issue_copy = [&](int64_t it) {
-      if (c.g != 0 || it >= n_inst) return;
+      if (HOSTIO || c.g != 0 || it >= n_inst) return;
       int64_t inst, h_off, w_off, t_off;
       locate(it, inst, h_off, w_off, t_off);
       fence_proxy_async_smem();
@@ -389,6 +392,16 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
       locate(it, inst, h_off, w_off, t_off);
       __syncwarp();
       if (c.g < KB) c.tks[c.g] = A.t[t_off + c.g];
+      if constexpr (HOSTIO) {  // the instance's channel, 16 bytes per lane and load
+        const float4* src = reinterpret_cast<const float4*>(A.H + h_off);
+        float4* dst = reinterpret_cast<float4*>(c.Hs);
+        float4 v[KB * MB * 8 / 16 / 32];
+#pragma unroll
+        for (int j = 0; j < KB * MB * 8 / 16 / 32; ++j) v[j] = src[L.lane + 32 * j];
+#pragma unroll
+        for (int j = 0; j < KB * MB * 8 / 16 / 32; ++j) dst[L.lane + 32 * j] = v[j];
+        __syncwarp();
+      } else {
       if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
       __syncwarp();
       if (c.misc[0] == 0) {
@@ -405,6 +418,7 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
       }
       if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);
       phase ^= 1u;
+      }
 
       float beta;
       int fl = setup(c, L, A, xf, w, beta);
@@ -461,9 +475,9 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
   }
 };
 
-template <int NW, int MINB>
+template <int NW, int MINB, bool HOSTIO = false>
 __global__ void __launch_bounds__(NW * 32, MINB) solve_tch_kernel(SolveArgs A) {
-  SolveTCH<NW>::run(A);
+  SolveTCH<NW, HOSTIO>::run(A);
 }
 
 }  // namespace precode

@@ -269,6 +269,35 @@ def test_deterministic_and_host_path_identical(pc):
     plan.close()
 
 
+@pytest.mark.parametrize("shared_t", [False, True])
+def test_host_buffers_zero_copy_and_staged_identical(pc, shared_t):
+    """Projected layer at K = 8, M = 64 on its split-FP16 build from host buffers:
+    page-locked buffers take the zero-copy kernel (H read and W written over the
+    host link from inside the kernel), pageable ones the staged copy pipeline; both
+    give bitwise the device solve's outputs (B not a multiple of the chunk)."""
+    capi, precoder = pc
+    B = 5003
+    H = ch.lognormal(B, 8, 64, seed=42)
+    t = ch.targets(1, 8)[0] if shared_t else ch.targets(B, 8)
+    mu = ch.fixed_workload_steps(10)
+    plan = precoder.Plan(capi.LAYER_PROJ, 10, [(64, 8)], B, tensor_cores=True)
+    assert capi.precode_plan_describe(plan.handle, 64, 8).startswith("solve_tch_kernel")
+    a = plan.solve(torch.from_numpy(H).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(mu).cuda())
+    a = [x.cpu() for x in a]
+    for pinned in (True, False):
+        def buf(x):
+            return x.pin_memory() if pinned else x
+        Hh, th = buf(torch.from_numpy(H)), buf(torch.from_numpy(np.ascontiguousarray(t)))
+        Wh = buf(torch.empty(B, 8, 64, dtype=torch.complex64))
+        oh, rh = buf(torch.empty(B)), buf(torch.empty(B))
+        fh = buf(torch.empty(B, dtype=torch.int32))
+        plan.solve_host(Hh, th, torch.from_numpy(mu), None, W=Wh, obj=oh, resid=rh, flags=fh)
+        assert torch.equal(Wh, a[0]) and torch.equal(oh, a[1]), pinned
+        assert torch.equal(rh, a[2]) and torch.equal(fh, a[3]), pinned
+    assert plan.errors() == 0
+    plan.close()
+
+
 def test_fixed_workload_full_size_sampled(pc, orc):
     """The full 65,536-instance batch in the benchmark's launch configuration;
     256 sampled instances against the oracle, all flags clean, all outputs feasible."""
