@@ -153,10 +153,14 @@ precode_status_t precode_solve(precode_plan_t plan, int32_t M, int32_t K, int64_
                                const float* step, const float* lam, void* W, float* obj,
                                float* resid, int32_t* flags, precode_stream_t stream);
 
-/* Same computation from HOST buffers (pinned memory recommended): the batch is
- * split in chunks whose host->device copy, solve and device->host copy are
- * pipelined over the plan's internal streams.  step/lam are HOST arrays [T].
- * Returns after the results are in the host buffers (synchronous). */
+/* Same computation from HOST buffers (pinned memory recommended).  When every
+ * buffer is page-locked host memory mapped into the device's address space and the
+ * shape runs on the split-FP16 K = 8, M = 64 build, one kernel reads H and writes W
+ * and the outputs in the host buffers directly (zero-copy over the host link).
+ * Otherwise the batch is split in chunks whose host->device copy, solve and
+ * device->host copy are pipelined over the plan's internal streams.  Both give the
+ * device solve's results bit for bit.  step/lam are HOST arrays [T].  Returns after
+ * the results are in the host buffers (synchronous). */
 precode_status_t precode_solve_host(precode_plan_t plan, int32_t M, int32_t K, int64_t B,
                                     const void* H, const float* t, int64_t t_stride,
                                     const float* step, const float* lam, void* W, float* obj,
