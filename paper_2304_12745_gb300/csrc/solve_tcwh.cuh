@@ -4,8 +4,13 @@
 // Everything else is the split-TF32 multi-warp kernel's: one CTA of KW warps per
 // instance, warp w owning users 8w .. 8w + 7 over all antennas in the m16n8
 // accumulator order, the raw channel in shared memory (FP32, rows padded by 16
-// bytes; its FP16 halves are formed on the fly), F = E G^{-T} as split-TF32 MMAs,
-// the Gram inverse and the FP64 path, user padding.
+// bytes) for the split-TF32 setup, F = E G^{-T} as split-TF32 MMAs, the Gram
+// inverse and the FP64 path, user padding.  For the layers each channel row is
+// converted once per instance, in place, into 16-byte chunks per antenna pair
+// (Re hi, Im hi, Re lo, Im lo as FP16 pairs), permuted within each group of 8
+// chunks by a row-dependent XOR so that both the residual's reads (8 users x 4
+// antenna pairs per quarter warp) and the update's (4 user pairs x 1 antenna
+// pair) hit 8 distinct bank groups.
 //
 // FP16 covers a narrow exponent range, so the instance is solved in units made
 // of exact powers of two, under which the projected iteration is equivariant:
@@ -55,18 +60,51 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
     return ldexpf(1.f, -ex);
   }
 
-  // E' tile ct of the warp's rows from FP16 halves of W' and of the scaled
-  // channel (split here from the FP32 shared copy), 16 antennas per MMA;
-  // A = (Re W, Im W) rows throughout, products with Re H' into ar, with Im H'
-  // into ai:  E_re = [ar]_g - [ai]_g+8,  E_im = [ai]_g + [ar]_g+8.
-  __device__ __forceinline__ static void e_tile_h(const Lane& L, const float2* Hs, const WT& w,
+  // ---- FP16 chunk layout of the scaled channel
+  static constexpr int RC = RSF / 2;  // chunks per row (MB / 2 + the padding chunk)
+  // bank-group swizzle of row u: user pairs and row parity spread over the 8 groups
+  __device__ __forceinline__ static int hsw(int u) { return ((u >> 1) & 3) | ((u & 1) << 2); }
+  // position within its row of chunk p (antennas 2p, 2p + 1) of row u: bank group
+  // (u RC + pos) mod 8 = (p ^ hsw(u)) mod 8, since MB / 2 is a multiple of 8
+  __device__ __forceinline__ static int chunk_pos(int u, int p) {
+    return (p & ~7) | ((((p ^ hsw(u)) & 7) - u) & 7);
+  }
+
+  // In place: raw FP32 rows -> FP16 chunks.  One thread per (row, group of 8
+  // chunks) reads its group whole before writing it back permuted.
+  __device__ static void to_chunks(const Lane& L, float2* Hs) {
+    constexpr int NG = MB / 16;
+    uint4* const hc = reinterpret_cast<uint4*>(Hs);
+    const float4* const hr = reinterpret_cast<const float4*>(Hs);
+    for (int idx = L.tid; idx < KB * NG; idx += NT) {
+      const int u = idx / NG, g8 = 8 * (idx % NG);
+      float4 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = hr[u * RC + g8 + j];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t rh, rl, ih, il;
+        split_h2(v[j].x, v[j].z, rh, rl);  // Re H', antennas 2p, 2p + 1
+        split_h2(v[j].y, v[j].w, ih, il);  // Im H'
+        hc[u * RC + chunk_pos(u, g8 + j)] = make_uint4(rh, ih, rl, il);
+      }
+    }
+  }
+
+  // E' tile ct of the warp's rows from FP16 halves of W' and the channel chunks,
+  // 16 antennas per MMA; A = (Re W, Im W) rows throughout, products with Re H'
+  // into ar, with Im H' into ai:  E_re = [ar]_g - [ai]_g+8,  E_im = [ai]_g + [ar]_g+8.
+  __device__ __forceinline__ static void e_tile_c(const Lane& L, const float2* Hs, const WT& w,
                                                   int ct, float (&e)[4]) {
     float ar[2][4], ai[2][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int k = 0; k < 4; ++k) ar[i][k] = ai[i][k] = 0.f;
-    const float2* hb = Hs + (8 * ct + L.g) * RSF + 2 * L.q;
+    const int u = 8 * ct + L.g;
+    const uint4* const row = reinterpret_cast<const uint4*>(Hs) + u * RC;
+    const uint4* const r0 = row + chunk_pos(u, L.q);      // blocks s even: pair 4s + q
+    const uint4* const r1 = row + chunk_pos(u, 4 + L.q);  // blocks s odd
 #pragma unroll
     for (int s = 0; s < NS; s += 2) {
       uint32_t ah[4], al[4];
@@ -74,21 +112,15 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
       split_h2_ordered(w[s][2], w[s][3], ah[1], al[1]);          // Im W, block s
       split_h2_ordered(w[s + 1][0], w[s + 1][1], ah[2], al[2]);  // Re W, block s + 1
       split_h2_ordered(w[s + 1][2], w[s + 1][3], ah[3], al[3]);  // Im W, block s + 1
-      const float4 h0 = *reinterpret_cast<const float4*>(hb + 8 * s);
-      const float4 h1 = *reinterpret_cast<const float4*>(hb + 8 * (s + 1));
-      uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
-      split_h2_ordered(h0.x, h0.z, rh0, rl0);  // Re H', block s (antennas 2q, 2q + 1)
-      split_h2_ordered(h1.x, h1.z, rh1, rl1);  // Re H', block s + 1
-      split_h2_ordered(h0.y, h0.w, ih0, il0);  // Im H', block s
-      split_h2_ordered(h1.y, h1.w, ih1, il1);  // Im H', block s + 1
+      const uint4 c0 = r0[4 * s], c1 = r1[4 * s];                // pairs 4s + q, 4s + 4 + q
       float (&r)[4] = ar[(s >> 1) & 1];
       float (&i)[4] = ai[(s >> 1) & 1];
-      mma_f16(r, ah[0], ah[1], ah[2], ah[3], rl0, rl1);
-      mma_f16(i, ah[0], ah[1], ah[2], ah[3], il0, il1);
-      mma_f16(r, al[0], al[1], al[2], al[3], rh0, rh1);
-      mma_f16(i, al[0], al[1], al[2], al[3], ih0, ih1);
-      mma_f16(r, ah[0], ah[1], ah[2], ah[3], rh0, rh1);
-      mma_f16(i, ah[0], ah[1], ah[2], ah[3], ih0, ih1);
+      mma_f16(r, ah[0], ah[1], ah[2], ah[3], c0.z, c1.z);
+      mma_f16(i, ah[0], ah[1], ah[2], ah[3], c0.w, c1.w);
+      mma_f16(r, al[0], al[1], al[2], al[3], c0.x, c1.x);
+      mma_f16(i, al[0], al[1], al[2], al[3], c0.y, c1.y);
+      mma_f16(r, ah[0], ah[1], ah[2], ah[3], c0.x, c1.x);
+      mma_f16(i, ah[0], ah[1], ah[2], ah[3], c0.y, c1.y);
     }
     float r[4], im[4];
 #pragma unroll
@@ -103,11 +135,14 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
   }
 
   // W' -= F' conj(H') with FP16 halves: A from the warp's F' tile kt (rows g:
-  // (-F_re, +F_im), rows g + 8: (-F_im, -F_re) over users 8kt + {0..7}), B = the
-  // conj(H') entries of users 8kt + 2q, 8kt + 2q + 1 at antenna 8nt + g, times xs.
+  // (-F_re, +F_im), rows g + 8: (-F_im, -F_re) over users 8kt + {0..7}); B = the
+  // conj(H') entries of users 8kt + 2q, 8kt + 2q + 1 at antenna 8nt + g, taken from
+  // the two users' chunks with byte permutes (times xs when SCALED).
   template <bool SCALED>
-  __device__ __forceinline__ static void update_h(const Lane& L, const float2* Hs, const float4* ft,
+  __device__ __forceinline__ static void update_c(const Lane& L, const float2* Hs, const float4* ft,
                                                   float xs, WT& w) {
+    const uint32_t sel = (L.g & 1) ? 0x7632u : 0x5410u;  // the antenna's half of each pair
+    const __half2 xs2 = __float2half2_rn(xs);
 #pragma unroll 1
     for (int kt = 0; kt < KW; ++kt) {
       const float4 f = ft[kt * 32 + L.lane];
@@ -115,20 +150,26 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
       split_h2_ordered(f.x, f.y, h01, l01);
       split_h2_ordered(f.z, f.w, h23, l23);
       const uint32_t nh01 = neg_h2(h01), nl01 = neg_h2(l01), nh23 = neg_h2(h23), nl23 = neg_h2(l23);
-      const float2* x0 = Hs + (8 * kt + 2 * L.q) * RSF + L.g;
-      const float2* x1 = x0 + RSF;
+      const int u0 = 8 * kt + 2 * L.q, u1 = u0 + 1;
+      const uint4* const row0 = reinterpret_cast<const uint4*>(Hs) + u0 * RC;
+      const uint4* const row1 = row0 + RC;
+      const int pe = L.g >> 1, po = 4 + (L.g >> 1);  // pair within a group of 8, nt even / odd
+      const uint4* const a0 = row0 + chunk_pos(u0, pe);
+      const uint4* const a1 = row0 + chunk_pos(u0, po);
+      const uint4* const b0 = row1 + chunk_pos(u1, pe);
+      const uint4* const b1 = row1 + chunk_pos(u1, po);
 #pragma unroll
       for (int nt = 0; nt < NS; ++nt) {
-        float2 a = x0[8 * nt], b = x1[8 * nt];
+        const uint4 c0 = (nt & 1) ? a1[8 * (nt >> 1)] : a0[8 * (nt >> 1)];
+        const uint4 c1 = (nt & 1) ? b1[8 * (nt >> 1)] : b0[8 * (nt >> 1)];
+        uint32_t rh = __byte_perm(c0.x, c1.x, sel), ih = __byte_perm(c0.y, c1.y, sel) ^ 0x80008000u;
+        uint32_t rl = __byte_perm(c0.z, c1.z, sel), il = __byte_perm(c0.w, c1.w, sel) ^ 0x80008000u;
         if constexpr (SCALED) {
-          a.x *= xs;
-          a.y *= xs;
-          b.x *= xs;
-          b.y *= xs;
+          rh = h2_bits(__hmul2(*reinterpret_cast<const __half2*>(&rh), xs2));
+          ih = h2_bits(__hmul2(*reinterpret_cast<const __half2*>(&ih), xs2));
+          rl = h2_bits(__hmul2(*reinterpret_cast<const __half2*>(&rl), xs2));
+          il = h2_bits(__hmul2(*reinterpret_cast<const __half2*>(&il), xs2));
         }
-        uint32_t rh, rl, ih, il;
-        split_h2_ordered(a.x, b.x, rh, rl);    // Re conj(H') of users 2q, 2q + 1
-        split_h2_ordered(-a.y, -b.y, ih, il);  // Im conj(H')
         mma_f16(w[nt], nh01, nh23, h23, nh01, rl, il);
         mma_f16(w[nt], nl01, nl23, l23, nl01, rh, ih);
         mma_f16(w[nt], nh01, nh23, h23, nh01, rh, ih);
@@ -136,7 +177,48 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
     }
   }
 
-  // E' tile by tile (FP16), F' = E' G'^{-T} accumulated by split-TF32 MMAs, then
+  // The same update as split TF32 in FP32 range, for an F' beyond the FP16
+  // update's reach: conj(H') rebuilt from the chunks (hi + lo).
+  __device__ __forceinline__ static void update_c_tf32(const Lane& L, const float2* Hs, const float4* ft,
+                                                       WT& w) {
+    const int hsel = L.g & 1;
+    auto part = [&](uint32_t hi, uint32_t lo) {
+      const __half2 a = *reinterpret_cast<const __half2*>(&hi), b = *reinterpret_cast<const __half2*>(&lo);
+      return hsel ? __high2float(a) + __high2float(b) : __low2float(a) + __low2float(b);
+    };
+#pragma unroll 1
+    for (int kt = 0; kt < KW; ++kt) {
+      const float4 f = ft[kt * 32 + L.lane];
+      uint32_t c0h, c0l, c1h, c1l, c2h, c2l, c3h, c3l;
+      split_tf32_ordered(f.x, c0h, c0l);
+      split_tf32_ordered(f.y, c1h, c1l);
+      split_tf32_ordered(f.z, c2h, c2l);
+      split_tf32_ordered(f.w, c3h, c3l);
+      const uint32_t n0h = neg_bits(c0h), n1h = neg_bits(c1h), n2h = neg_bits(c2h), n3h = neg_bits(c3h);
+      const uint32_t n0l = neg_bits(c0l), n1l = neg_bits(c1l), n2l = neg_bits(c2l), n3l = neg_bits(c3l);
+      const int u0 = 8 * kt + 2 * L.q, u1 = u0 + 1;
+      const uint4* const row0 = reinterpret_cast<const uint4*>(Hs) + u0 * RC;
+      const uint4* const row1 = row0 + RC;
+#pragma unroll
+      for (int nt = 0; nt < NS; ++nt) {
+        const int p = 4 * nt + (L.g >> 1);
+        const uint4 c0 = row0[chunk_pos(u0, p)], c1 = row1[chunk_pos(u1, p)];
+        uint32_t r0h, r0l, r1h, r1l, i0h, i0l, i1h, i1l;
+        split_tf32_ordered(part(c0.x, c0.z), r0h, r0l);
+        split_tf32_ordered(part(c1.x, c1.z), r1h, r1l);
+        split_tf32_ordered(-part(c0.y, c0.w), i0h, i0l);
+        split_tf32_ordered(-part(c1.y, c1.w), i1h, i1l);
+        mma_tf32(w[nt], n0h, n2h, n1h, n3h, r0l, r1l);
+        mma_tf32(w[nt], c2h, n0h, c3h, n1h, i0l, i1l);
+        mma_tf32(w[nt], n0l, n2l, n1l, n3l, r0h, r1h);
+        mma_tf32(w[nt], c2l, n0l, c3l, n1l, i0h, i1h);
+        mma_tf32(w[nt], n0h, n2h, n1h, n3h, r0h, r1h);
+        mma_tf32(w[nt], c2h, n0h, c3h, n1h, i0h, i1h);
+      }
+    }
+  }
+
+  // E' tile by tile (FP16 chunks), F' = E' G'^{-T} accumulated by split-TF32 MMAs, then
   // the F' range check of the warp: returns the channel factor xs for the FP16
   // update (1, or 2^s with F' stored scaled by 2^-s), or 0 when F' is beyond
   // what the FP16 update can take (F' stored as is, for the split-TF32 update).
@@ -150,7 +232,7 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
 #pragma unroll 1
     for (int ct = 0; ct < KW; ++ct) {
       float e[4];
-      e_tile_h(L, Hs, w, ct, e);
+      e_tile_c(L, Hs, w, ct, e);
       S::sub_s(L, tks, ct, e);
       uint32_t c0h, c0l, c1h, c1l, c2h, c2l, c3h, c3l;
       split_tf32_ordered(e[0], c0h, c0l);
@@ -200,7 +282,8 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
   }
 
   // ||E||_F^2 over the lane's entries in original units (columns d_k^{-1}, then
-  // the 1 / b applied by the caller); E' from FP16 or (TF32) split-TF32 MMAs
+  // the 1 / b applied by the caller); E' from the FP16 chunks or (TF32) split-TF32
+  // MMAs on the raw channel
   template <bool TF32>
   __device__ __forceinline__ static float residual_ssh(const Lane& L, const float2* Hs, const float* tks,
                                                        const float* dinv, const WT& w) {
@@ -211,7 +294,7 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
       if constexpr (TF32)
         S::template e_tile<false>(L, Hs, w, ct, e);
       else
-        e_tile_h(L, Hs, w, ct, e);
+        e_tile_c(L, Hs, w, ct, e);
       S::sub_s(L, tks, ct, e);
       const float d0 = dinv[8 * ct + 2 * L.q], d1 = dinv[8 * ct + 2 * L.q + 1];
       ss += d0 * d0 * (e[0] * e[0] + e[2] * e[2]) + d1 * d1 * (e[1] * e[1] + e[3] * e[3]);
@@ -394,13 +477,14 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
       for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int k = 0; k < 4; ++k) w[s][k] *= beta;
-      __syncthreads();  // every t' and wred read done
+      __syncthreads();  // every t', wred and raw-channel read done
       if (L.tid < KB) tks[L.tid] *= beta;
+      const bool tf32_layers = (fl & PRECODE_F_FP64_CHOL) != 0;
+      if (!tf32_layers && !singular) to_chunks(L, Hs);
       __syncthreads();
 
       // ---- layers (scaled units)
       const int T = A.T;
-      const bool tf32_layers = (fl & PRECODE_F_FP64_CHOL) != 0;
       float rss = 0.f;
       if (!singular) {
 #pragma unroll 1
@@ -414,11 +498,11 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
           }
           const float xs = residual_fh(L, Hs, gf, tks, w, ft);
           if (xs == 1.f)
-            update_h<false>(L, Hs, ft, 1.f, w);
+            update_c<false>(L, Hs, ft, 1.f, w);
           else if (xs > 0.f)
-            update_h<true>(L, Hs, ft, xs, w);
+            update_c<true>(L, Hs, ft, xs, w);
           else
-            S::update(L, Hs, ft, w);
+            update_c_tf32(L, Hs, ft, w);
         }
         if (A.resid) {
           rss = tf32_layers ? residual_ssh<true>(L, Hs, tks, dinv, w)
