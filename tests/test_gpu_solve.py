@@ -245,6 +245,28 @@ def test_empty_one_and_shared_targets(pc, orc):
     plan.close()
 
 
+@pytest.mark.parametrize("M,K", [(64, 8), (256, 32), (128, 16), (64, 13)])
+def test_fp16_builds_small_batches_and_shared_targets(pc, orc, M, K):
+    """The split-FP16 builds (K = 8 one-warp, multi-warp exact and user-padded) on
+    B = 0, 1 and 3 instances (fewer than one block's worth) with shared targets,
+    T = 1 and T = 4: the oracle's results, each instance independent of the batch."""
+    capi, precoder = pc
+    H = ch.rician_ula(3, K, M, seed=60 + K)
+    t_shared = np.linspace(0.5, 2.0, K).astype(np.float32)
+    for T in (1, 4):
+        mu = ch.uniform_steps(T, 0.01, 0.1, seed=61)
+        plan = precoder.Plan(capi.LAYER_PROJ, T, [(M, K)], 3, tensor_cores=True)
+        assert capi.precode_plan_describe(plan.handle, M, K).startswith(("solve_tch", "solve_tcwh"))
+        md, td = torch.from_numpy(mu).cuda(), torch.from_numpy(t_shared).cuda()
+        plan.solve(torch.empty((0, K, M), dtype=torch.complex64, device="cuda"), td, md)  # no-op
+        W3, o3, r3, f3 = plan.solve(torch.from_numpy(H).cuda(), td, md)
+        W1 = plan.solve(torch.from_numpy(H[1:2]).cuda(), td, md)[0]
+        plan.close()
+        gpu = tuple(x.cpu().numpy() for x in (W3, o3, r3, f3))
+        assert_parity(gpu, oracle_ref(orc, 1, H, np.broadcast_to(t_shared, (3, K)), mu))
+        assert torch.equal(W1[0], W3[1])
+
+
 def test_deterministic_and_host_path_identical(pc):
     capi, precoder = pc
     B = 3000
