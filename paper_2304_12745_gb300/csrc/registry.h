@@ -42,12 +42,14 @@ struct TrainVariant {
   int threads;
   int groups;
   bool tc;  // tensor-core (split TF32) build
+  bool f16 = false;  // the layers' contractions as split-FP16 MMAs (scaled instances)
 };
 
 void register_solve_pgd(std::vector<Variant>& v);
 void register_train_pgd(std::vector<TrainVariant>& v);
 void register_train_proj(std::vector<TrainVariant>& v);
 void register_train_tc(std::vector<TrainVariant>& v);
+void register_train_tch(std::vector<TrainVariant>& v);
 const std::vector<TrainVariant>& train_variants();
 void register_solve_proj(std::vector<Variant>& v);
 void register_solve_tc(std::vector<Variant>& v);

@@ -185,11 +185,22 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
   }
 
   // Per-instance setup: the scaled problem (d_k^{-1} into c.dsc, t' into c.tks),
-  // the X fragments, the H fragments and W^(0)' into w; b into beta.  Returns the
-  // instance flags.
+  // the X fragments, the H fragments and W^(0)' into w; b into beta.  With xraw,
+  // also the unscaled conj(H) B fragments of the TF32 update layout,
+  // (Re X[2q][8nt+g], Re X[2q+1][8nt+g], Im X[2q][8nt+g], Im X[2q+1][8nt+g]) at
+  // [nt][lane], taken before the scaling.  Returns the instance flags.
   __device__ static int setup(Ctx& c, const Lane& L, const SolveArgs& A, uint4* xf, WT& w,
-                              float& beta) {
+                              float& beta, float4* xraw = nullptr) {
     float2* const Hs = c.Hs;
+    if (xraw) {
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float2 h0 = Hs[(2 * L.q) * MB + 8 * nt + L.g];
+        const float2 h1 = Hs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+        xraw[nt * 32 + L.lane] = make_float4(h0.x, h1.x, -h0.y, -h1.y);
+      }
+      __syncwarp();  // read before any lane scales its row
+    }
     // ---- per-user scales: row g of H' = d_g H[g] (in place), t'_g = d_g t_g
     float hm = 0.f;
 #pragma unroll

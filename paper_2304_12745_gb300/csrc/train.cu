@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "api_internal.h"
@@ -15,6 +16,7 @@ const std::vector<TrainVariant>& train_variants() {
     std::vector<TrainVariant> r;
     register_train_pgd(r);
     register_train_proj(r);
+    register_train_tch(r);  // before the TF32 build: the projected layer's default at 8 x 64
     register_train_tc(r);
     return r;
   }();
@@ -43,9 +45,13 @@ __global__ void batch_mean_kernel(const float* __restrict__ part, int64_t B, int
 
 const TrainVariant* pick_train(int mode, int M, int K, bool tensor_cores) {
   const TrainVariant* best = nullptr;
+  // PRECODE_TRAIN_TF32 set: the split-TF32 tensor-core build even where a split-FP16
+  // one exists (comparison and testing)
+  const bool tf32_only = std::getenv("PRECODE_TRAIN_TF32") != nullptr;
   if (tensor_cores)
     for (const auto& v : train_variants())
-      if (v.tc && v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
+      if (v.tc && !(tf32_only && v.f16) && v.mode == mode && v.exact && v.KB == K && v.MB == M)
+        return &v;
   for (const auto& v : train_variants())
     if (!v.tc && v.mode == mode && v.exact && v.KB == K && v.MB == M) return &v;
   for (const auto& v : train_variants()) {

@@ -62,8 +62,9 @@ class UnfoldedTrainer:
                  step_normalised: bool = False, group=None, tensor_cores: bool = True):
         """`group`: a torch.distributed process group whose ranks each train on
         their own batches; gradients are averaged over all ranks every step.
-        `tensor_cores`: use the tensor-core (split TF32) forward + adjoint build
-        where the shape has one (K = 8, M = 64)."""
+        `tensor_cores`: use the tensor-core forward + adjoint build where the
+        shape has one (K = 8, M = 64: split FP16 for the projected layer, split
+        TF32 for the paper layer)."""
         self.mode, self.T, self.K, self.M, self.batch, self.a = mode, T, K, M, batch, a
         self.group = group
         self.plan = Plan(mode, T, [(M, K)], batch, step_normalised=step_normalised,
@@ -79,7 +80,8 @@ class UnfoldedTrainer:
             self.lam = torch.nn.Parameter(torch.tensor(init_lam, dtype=torch.float32,
                                                        device=device))
             params.append(self.lam)
-        self.opt = torch.optim.Adam(params, lr=lr)
+        # one fused kernel per optimiser step on CUDA parameters
+        self.opt = torch.optim.Adam(params, lr=lr, fused=self.step.is_cuda)
         self.steps_done = 0
 
     def project(self):
@@ -95,14 +97,17 @@ class UnfoldedTrainer:
     def loss(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
         return PrecodeLoss.apply(self.step, self.lam, self.plan, H, t, self.a, self.group)
 
-    def train_step(self, H: torch.Tensor, t: torch.Tensor) -> float:
+    def train_step(self, H: torch.Tensor, t: torch.Tensor, sync: bool = True):
+        """One Adam step on batch (H, t).  Returns the batch loss as a float, or
+        with sync=False as a device tensor (no host synchronisation, so steps
+        queue back to back on the stream)."""
         self.opt.zero_grad(set_to_none=True)
         loss = self.loss(H, t)
         loss.backward()
         self.opt.step()
         self.project()
         self.steps_done += 1
-        return float(loss.detach())
+        return float(loss.detach()) if sync else loss.detach()
 
     def make_batch(self, index: int, seed: int, family: str = "rayleigh"):
         """Channels of batch `index` (deterministic in (seed, index))."""

@@ -55,11 +55,15 @@ def _train_step(plan, H, t, step, lam, a):
             None if dl is None else dl.cpu().numpy().astype(np.float64))
 
 
-@pytest.mark.parametrize("K,M,T,tc", [(4, 32, 6, False), (8, 64, 10, False), (8, 64, 10, True)])
-def test_projected_gradient_matches_oracle(orc, K, M, T, tc):
-    """FP32 build, and (tc) the tensor-core build of the forward + adjoint pass."""
+@pytest.mark.parametrize("K,M,T,tc", [(4, 32, 6, False), (8, 64, 10, False), (8, 64, 10, True),
+                                      (8, 64, 10, "tf32")])
+def test_projected_gradient_matches_oracle(orc, monkeypatch, K, M, T, tc):
+    """FP32 build, and the tensor-core builds of the forward + adjoint pass (split
+    FP16 by default; split TF32 with PRECODE_TRAIN_TF32)."""
     from paper_2304_12745_gb300 import capi
     from paper_2304_12745_gb300.precoder import Plan
+    if tc == "tf32":
+        monkeypatch.setenv("PRECODE_TRAIN_TF32", "1")
     B0 = 64
     H = ch.rayleigh(B0, K, M, seed=40 + K).astype(np.complex128)
     H = H.astype(np.complex64).astype(np.complex128)  # the GPU sees complex64
@@ -73,7 +77,7 @@ def test_projected_gradient_matches_oracle(orc, K, M, T, tc):
     ref = [orc.ufproj_grad(H[b], t[b], mu, a) for b in range(B)]
     loss_o = np.mean([r[0] for r in ref])
     g_o = np.mean([r[1] for r in ref], axis=0)
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, tensor_cores=tc)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, tensor_cores=bool(tc))
     loss, g, _ = _train_step(plan, H, t, mu, None, a)
     plan.close()
     assert loss == pytest.approx(loss_o, rel=1e-5)
@@ -108,16 +112,18 @@ def test_paper_layer_gradient_matches_oracle(orc, K, M, tc):
     assert np.allclose(gl, gl_o, rtol=1e-3, atol=1e-3 * np.abs(gl_o).max()), (gl, gl_o)
 
 
-@pytest.mark.parametrize("tc", [False, True])
-def test_gradient_matches_central_differences_of_the_gpu_loss(tc):
+@pytest.mark.parametrize("tc", [False, True, "tf32"])
+def test_gradient_matches_central_differences_of_the_gpu_loss(monkeypatch, tc):
     """Central differences (h = 1e-3) of the GPU's own FP32 batch loss."""
     from paper_2304_12745_gb300 import capi
     from paper_2304_12745_gb300.precoder import Plan
+    if tc == "tf32":
+        monkeypatch.setenv("PRECODE_TRAIN_TF32", "1")
     K, M, T, B = 8, 64, 10, 2048
     H = ch.rayleigh(B, K, M, seed=60)
     t = np.ones((B, K), np.float32)
     mu = ch.uniform_steps(T, 0.02, 0.08, seed=61).astype(np.float64)
-    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, tensor_cores=tc)
+    plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, tensor_cores=bool(tc))
     _, g, _ = _train_step(plan, H, t, mu, None, 1.0)
     h = 1e-3
     for l in (0, 4, 9):
