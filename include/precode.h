@@ -188,6 +188,9 @@ precode_status_t precode_solve_varlen(precode_plan_t plan, int64_t B, const prec
  * plan workspace (allocated on first use, max_instances sized) and the reverse
  * pass recomputes the layer inputs from them; per-instance partial gradients are
  * averaged in FP64 in a fixed order (bitwise reproducible).  flags [B] optional.
+ * With PRECODE_PLAN_TENSOR_CORES at K = 8, M = 64 the forward and adjoint run on
+ * the tensor cores: split FP16 for PROJ, split TF32 for PGD (the environment
+ * variable PRECODE_TRAIN_TF32, when set, selects split TF32 for PROJ as well).
  * EINVAL: B outside [1, max_instances], NULL loss/dstep, PGD without lam/dlam. */
 precode_status_t precode_train_step(precode_plan_t plan, int32_t M, int32_t K, int64_t B,
                                     const void* H, const float* t, int64_t t_stride,
