@@ -501,7 +501,9 @@ precode_status_t precode_plan_describe(precode_plan_t p, int32_t M, int32_t K, c
   if (!p || !buf || len == 0) return fail(PRECODE_EINVAL, "precode_plan_describe: bad argument");
   const Variant* v = p->variant_for(M, K);
   if (!v) return fail(PRECODE_EINVAL, "precode_plan_describe: shape not covered by the plan");
-  if (v->f16 && v->exact && v->KB == 8 && v->MB == 64)
+  if (v->f16 && v->exact && v->KB == 8 && v->MB == 64 && v->mode == PRECODE_LAYER_PGD)
+    std::snprintf(buf, len, "solve_tch_kernel<%d, %d, 0, 0>", v->NW, v->minb);
+  else if (v->f16 && v->exact && v->KB == 8 && v->MB == 64)
     std::snprintf(buf, len, "solve_tch_kernel<%d, %d>", v->NW, v->minb);
   else if (v->f16)
     std::snprintf(buf, len, "solve_tcwh_kernel<%d, %d, %d>", v->NW, v->MB, v->minb);

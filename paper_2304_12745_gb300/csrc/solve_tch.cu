@@ -1,5 +1,5 @@
-// Instantiations of the split-FP16 tensor-core solve kernel (projected layer,
-// K = 8, M = 64).
+// Instantiations of the split-FP16 tensor-core solve kernel (K = 8, M = 64):
+// the projected layer and the paper layer.
 #include "registry.h"
 #include "solve_tch.cuh"
 
@@ -13,6 +13,10 @@ void register_solve_tch(std::vector<Variant>& v) {
   X(4, 3)
   X(4, 4)
 #undef X
+  // the paper layer (one global scale on the channel)
+  v.push_back(Variant{kModePGD, 8, 64, 4, 8, 8, 4, 3, true, true, false,
+                      (const void*)&solve_tch_kernel<4, 3, false, kModePGD>,
+                      SolveTCH<4, false, kModePGD>::SMEM_BYTES, 4 * 32, 4, true, true});
 }
 
 // The same builds reading H, t and writing W and the outputs with plain loads and

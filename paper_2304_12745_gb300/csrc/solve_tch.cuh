@@ -34,9 +34,17 @@ namespace precode {
 // HOSTIO: the channel is read with plain 16-byte loads (no bulk async copy),
 // so H, W, t and the outputs may live in page-locked host memory mapped into the
 // device's address space (zero-copy over the host link).
-template <int NW, bool HOSTIO = false>
-struct SolveTCH : SolveTC<kModeProj, NW, false> {
-  using S = SolveTC<kModeProj, NW, false>;
+//
+// MODE = kModePGD (the paper layer) uses one global power of two on H instead of
+// the per-user scales (its iteration is equivariant under global scaling only):
+// H' = a H, W' = (b / a) W, t' = b t, eta' = eta / a^2, tau' = (b / a) tau, so
+// W^(0)' = (b / a^2) conj(H'), X = conj(H') and E' = b E.  A weak user's channel
+// row may then sit in FP16's subnormals; the rounding that costs is absolute and
+// small against the instance's norms (that user's W row stays of the order of its
+// channel row in this iteration).
+template <int NW, bool HOSTIO = false, int MODE = kModeProj>
+struct SolveTCH : SolveTC<MODE, NW, false> {
+  using S = SolveTC<MODE, NW, false>;
   using Base = typename S::Base;
   using C = typename S::C;
   using Ctx = typename S::Ctx;
@@ -330,6 +338,92 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
     return fl;
   }
 
+  // Paper-layer setup: the scaled problem (t' into c.tks, d_k^{-1} = 1 into
+  // c.dsc), X = conj(H') and the H' fragments, W^(0)' into w; the step factor
+  // (eta' = step invLp), the threshold factor ba (tau' = ba lambda eta'), the output
+  // factors f_out (W, objective) and f_res (residual).
+  __device__ static void setup_pgd(Ctx& c, const Lane& L, const SolveArgs& A, uint4* xf, WT& w,
+                                   float& invLp, float& ba, float& f_out, float& f_res) {
+    float2* const Hs = c.Hs;
+    float hm = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      hm = fmaxf(hm, fmaxf(fmaxf(fabsf(hv.x), fabsf(hv.y)), fmaxf(fabsf(hv.z), fabsf(hv.w))));
+    }
+    hm = warp_max(hm);
+    const float alpha = inv_pow2_of(hm);
+    const float tm = warp_max(fabsf(c.tks[L.lane & 7]));
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      float4* p = reinterpret_cast<float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      const float4 hv = *p;
+      *p = make_float4(alpha * hv.x, alpha * hv.y, alpha * hv.z, alpha * hv.w);
+    }
+    __syncwarp();
+    const float ia2 = 1.f / (alpha * alpha);
+    invLp = ia2;
+    if (A.opts & OPT_STEP_NORMALISED) {  // 1 / Gershgorin bound of G' = a^2 G
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+        w[s][0] = hv.x;
+        w[s][1] = hv.z;
+        w[s][2] = -hv.y;
+        w[s][3] = -hv.w;
+      }
+      float e[4];
+      S::template residual<false>(L, Hs, nullptr, nullptr, w, c.tks, false, e);  // G'^T
+      *reinterpret_cast<float4*>(c.Es + L.g * KB + 2 * L.q) = make_float4(e[0], e[2], e[1], e[3]);
+      __syncwarp();
+      invLp = Base::inv_gershgorin(c);
+    }
+    // W^(0)' = (b / a^2) conj(H') with max(|W^(0)'|, t') in [8, 16)
+    const float beta = 16.f * inv_pow2_of(fmaxf(alpha * hm * ia2, tm));
+    const float c0 = beta * ia2;
+    float4 hv[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      w[s][0] = c0 * hv[s].x;
+      w[s][1] = c0 * hv[s].z;
+      w[s][2] = -c0 * hv[s].y;
+      w[s][3] = -c0 * hv[s].w;
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {  // X = conj(H') over users 2q, 2q + 1 at antenna 8nt + g
+      const float2 h0 = Hs[(2 * L.q) * MB + 8 * nt + L.g];
+      const float2 h1 = Hs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+      uint32_t rh, rl, ih, il;
+      split_h2(h0.x, h1.x, rh, rl);
+      split_h2(-h0.y, -h1.y, ih, il);
+      xf[nt * 32 + L.lane] = make_uint4(rh, ih, rl, il);
+    }
+    __syncwarp();  // every read of the channel (and of the Gershgorin scratch) done
+    if (L.lane < KB) {
+      c.tks[L.lane] *= beta;
+      c.dsc[L.lane] = 1.f;
+    }
+    uint4* const hh = reinterpret_cast<uint4*>(Hs);
+    uint4* const hl = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float4 a = hv[2 * p], b = hv[2 * p + 1];
+      uint32_t rah, ral, rbh, rbl, iah, ial, ibh, ibl;
+      split_h2(a.x, a.z, rah, ral);
+      split_h2(b.x, b.z, rbh, rbl);
+      split_h2(a.y, a.w, iah, ial);
+      split_h2(b.y, b.w, ibh, ibl);
+      hh[p * 32 + L.lane] = make_uint4(rah, rbh, iah, ibh);
+      hl[p * 32 + L.lane] = make_uint4(ral, rbl, ial, ibl);
+    }
+    __syncwarp();
+    ba = beta * alpha;
+    f_out = alpha / beta;
+    f_res = 1.f / beta;
+  }
+
   __device__ static void run(const SolveArgs& A) {
     extern __shared__ __align__(16) unsigned char smem[];
     Ctx c;
@@ -431,10 +525,15 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
       phase ^= 1u;
       }
 
-      float beta;
-      int fl = setup(c, L, A, xf, w, beta);
+      float beta = 1.f, f_out, f_res, invLp = 1.f, ba = 1.f;
+      int fl = 0;
+      if constexpr (MODE == kModeProj) {
+        fl = setup(c, L, A, xf, w, beta);
+        f_out = f_res = 1.f / beta;
+      } else {
+        setup_pgd(c, L, A, xf, w, invLp, ba, f_out, f_res);
+      }
       const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
-      const float f_out = 1.f / beta;
 
       // ---- layers (scaled units)
       const int T = A.T;
@@ -442,11 +541,22 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
       if (!singular) {
 #pragma unroll 1
         for (int l = 0; l < T; ++l) {
-          S::shrink(L, fb, S::colsum(L, nb, w), fmaxf(__ldg(A.step + l), 0.f) * beta, w);
-          residual_h(L, hh, hl, w, e);
-          if (2 * L.q == L.g) e[0] -= c.tks[L.g];
-          if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
-          update_h(L, xf, e, w);
+          if constexpr (MODE == kModeProj) {
+            S::shrink(L, fb, S::colsum(L, nb, w), fmaxf(__ldg(A.step + l), 0.f) * beta, w);
+            residual_h(L, hh, hl, w, e);
+            if (2 * L.q == L.g) e[0] -= c.tks[L.g];
+            if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
+            update_h(L, xf, e, w);
+          } else {  // residual, gradient step, shrink (the paper's order)
+            const float eta = __ldg(A.step + l) * invLp;
+            residual_h(L, hh, hl, w, e);
+            if (2 * L.q == L.g) e[0] -= c.tks[L.g];
+            if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[k] *= eta;
+            update_h(L, xf, e, w);
+            S::shrink(L, fb, S::colsum(L, nb, w), fmaxf(fmaxf(__ldg(A.lam + l), 0.f) * eta, 0.f) * ba, w);
+          }
         }
         if (A.resid) {
           residual_h(L, hh, hl, w, e);
@@ -475,7 +585,7 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
             make_float4(f_out * w[s][0], f_out * w[s][2], f_out * w[s][1], f_out * w[s][3]);
       if (c.g == 0) {
         o *= f_out;
-        const float res = sqrtf(rs) * f_out;
+        const float res = sqrtf(rs) * f_res;
         if (!(o < FLT_MAX) || !(res < FLT_MAX)) fl |= PRECODE_F_NONFINITE;
         if (A.obj) A.obj[inst] = o;
         if (A.resid) A.resid[inst] = res;
@@ -486,9 +596,9 @@ struct SolveTCH : SolveTC<kModeProj, NW, false> {
   }
 };
 
-template <int NW, int MINB, bool HOSTIO = false>
+template <int NW, int MINB, bool HOSTIO = false, int MODE = kModeProj>
 __global__ void __launch_bounds__(NW * 32, MINB) solve_tch_kernel(SolveArgs A) {
-  SolveTCH<NW, HOSTIO>::run(A);
+  SolveTCH<NW, HOSTIO, MODE>::run(A);
 }
 
 }  // namespace precode

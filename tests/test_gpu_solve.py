@@ -205,15 +205,18 @@ def test_pgd_paper_setting_k8_m64(pc, orc):
     assert_parity(gpu, ref)
 
 
-def test_pgd_step_normalised_on_lognormal(pc, orc):
-    """Per-instance eta_l / L_b with the Gershgorin bound L_b = max_k sum_j |G_kj|."""
+@pytest.mark.parametrize("tc", [False, True])
+def test_pgd_step_normalised_on_lognormal(pc, orc, tc):
+    """Per-instance eta_l / L_b with the Gershgorin bound L_b = max_k sum_j |G_kj|
+    (FP32 build; split-FP16 tensor-core build, whose one global channel scale leaves
+    the weak users of 8 dB log-normal gains with small FP16 rows)."""
     capi, precoder = pc
     B, K, M = 200, 8, 64
     H = ch.lognormal(B, K, M, seed=2)
     t = ch.targets(B, K)
     step = np.full(10, 0.9, np.float32)
     lam = np.full(10, 0.5, np.float32)
-    gpu = run_gpu(precoder, capi.LAYER_PGD, H, t, step, lam, step_normalised=True)
+    gpu = run_gpu(precoder, capi.LAYER_PGD, H, t, step, lam, step_normalised=True, tensor_cores=tc)
     Wo = np.zeros_like(H, dtype=np.complex128)
     for b in range(B):
         Hb = H[b].astype(np.complex128)
@@ -342,28 +345,33 @@ def test_fixed_workload_full_size_sampled(pc, orc):
 
 # ---------------------------------------------------------------- tensor-core build (K=8, M=64)
 
-def tf32_build(tmp_path, capi):
-    """Plan options that pin the projected layer at K = 8, M = 64 to the split-TF32
-    build (the split-FP16 build is that shape's default)."""
-    path = tmp_path / "tune_tf32.txt"
-    path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|8|64\t"
+def tf32_build(tmp_path, capi, mode=None):
+    """Plan options that pin K = 8, M = 64 (projected layer, or `mode`) to the
+    split-TF32 build (the split-FP16 builds are that shape's defaults)."""
+    mode = capi.LAYER_PROJ if mode is None else mode
+    path = tmp_path / f"tune_tf32_{mode}.txt"
+    path.write_text(f"{torch.cuda.get_device_name(0)}|{mode}|8|64\t"
                     "8x64/4x8/jc8/w4/b3/split/tc/exact\n")
     return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
 
 
-def build_kw(tmp_path, capi, build, M=64, K=8):
+def build_kw(tmp_path, capi, build, M=64, K=8, mode=None):
     if build != "tf32":
         return dict(tensor_cores=True)
-    return tf32_build(tmp_path, capi) if (M, K) == (64, 8) else tcw_tf32_build(tmp_path, capi, M, K)
+    return tf32_build(tmp_path, capi, mode) if (M, K) == (64, 8) else tcw_tf32_build(tmp_path, capi, M, K)
 
 
-@pytest.mark.parametrize("mode", ["proj", "proj_tf32", "pgd"])
+@pytest.mark.parametrize("mode", ["proj", "proj_tf32", "pgd", "pgd_tf32"])
 def test_tensor_core_variant_parity(pc, orc, tmp_path, mode):
-    """Warp-MMA builds (split FP16 / split TF32 operands): same tolerances as the
-    FP32 build."""
+    """Warp-MMA builds (split FP16 by default, split TF32 pinned): same tolerances
+    as the FP32 build."""
     capi, precoder = pc
     B = 1000
-    kw = tf32_build(tmp_path, capi) if mode == "proj_tf32" else dict(tensor_cores=True)
+    kw = dict(tensor_cores=True)
+    if mode == "proj_tf32":
+        kw = tf32_build(tmp_path, capi)
+    elif mode == "pgd_tf32":
+        kw = tf32_build(tmp_path, capi, capi.LAYER_PGD)
     if mode.startswith("proj"):
         H = ch.lognormal(B, 8, 64, seed=2)
         t = ch.targets(B, 8)
@@ -374,14 +382,14 @@ def test_tensor_core_variant_parity(pc, orc, tmp_path, mode):
         L = 1 / ch.paper_eta(8, 64)
         step = np.linspace(1 / L, 1 / (2 * L), 20).astype(np.float32)
         lam, m = np.full(20, 1 / 15, np.float32), capi.LAYER_PGD
-    if mode == "proj_tf32":
-        plan = precoder.Plan(m, len(step), [(64, 8)], B, **kw)
-        assert capi.precode_plan_describe(plan.handle, 64, 8).startswith("solve_tc_kernel<1")
-        plan.close()
+    plan = precoder.Plan(m, len(step), [(64, 8)], B, **kw)
+    name = capi.precode_plan_describe(plan.handle, 64, 8)
+    plan.close()
+    assert name.startswith("solve_tc_kernel" if mode.endswith("tf32") else "solve_tch_kernel"), name
     gpu = run_gpu(precoder, m, H, t, step, lam, **kw)
-    ref = oracle_ref(orc, 0 if mode == "pgd" else 1, H, t, step, lam)
+    ref = oracle_ref(orc, 0 if mode.startswith("pgd") else 1, H, t, step, lam)
     e, eo = assert_parity(gpu, ref)
-    if mode != "pgd":
+    if mode.startswith("proj"):
         assert np.all(gpu[2] <= 1e-4 * math.sqrt(8))
 
 
@@ -723,7 +731,8 @@ def test_tensor_core_kernels_independent_of_earlier_kernels(pc, tmp_path):
     shared-memory operand is written before it is read."""
     capi, precoder = pc
     cases = [(capi.LAYER_PROJ, 8, 64, "default"), (capi.LAYER_PROJ, 8, 64, "tf32"),
-             (capi.LAYER_PGD, 8, 64, "default"), (capi.LAYER_PROJ, 16, 128, "default"),
+             (capi.LAYER_PGD, 8, 64, "default"), (capi.LAYER_PGD, 8, 64, "tf32"),
+             (capi.LAYER_PROJ, 16, 128, "default"),
              (capi.LAYER_PROJ, 32, 256, "default"), (capi.LAYER_PROJ, 32, 256, "tf32"),
              (capi.LAYER_PROJ, 13, 64, "default")]
     runs = {}
@@ -734,7 +743,7 @@ def test_tensor_core_kernels_independent_of_earlier_kernels(pc, tmp_path):
             step = ch.uniform_steps(6, 0.01, 0.1, seed=7) if mode == capi.LAYER_PROJ else \
                 np.full(6, ch.paper_eta(K, M), np.float32)
             lam = None if mode == capi.LAYER_PROJ else np.full(6, 1 / 15, np.float32)
-            out = run_gpu(precoder, mode, H, t, step, lam, **build_kw(tmp_path, capi, build, M, K))
+            out = run_gpu(precoder, mode, H, t, step, lam, **build_kw(tmp_path, capi, build, M, K, mode))
             if rep == 0:
                 runs[(mode, K, M, build)] = out
             else:
