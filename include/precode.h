@@ -95,11 +95,12 @@ typedef enum {
 #define PRECODE_PLAN_TENSOR_CORES 8u    /* for shapes with a tensor-core build (8x64, 16x128, 32x256) use it:
                                            contractions as warp MMAs on TF32 operands split
                                            in three terms (products accurate to ~2^-21 rel.);
-                                           the projected layer defaults to split-FP16 builds
-                                           at K = 8, M = 64 and for 9..32 users at 64, 128
-                                           or 256 antennas (two FP16 terms per value, ~2^-22
-                                           rel., each instance in exact power-of-two units
-                                           that keep it inside the FP16 range) */
+                                           split-FP16 builds are the defaults for both
+                                           layers at K = 8, M = 64 and for the projected
+                                           layer with 9..32 users at 64, 128 or 256 antennas
+                                           (two FP16 terms per value, ~2^-22 rel., each
+                                           instance in exact power-of-two units that keep
+                                           it inside the FP16 range) */
 
 #define PRECODE_MAX_K 32
 #define PRECODE_MAX_M 256
