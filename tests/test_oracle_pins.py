@@ -423,3 +423,27 @@ def test_paper_layer_gradient_vs_central_differences(orc):
         assert np.allclose(dl, fl, rtol=1e-5, atol=1e-9 * abs(loss)), (dl, fl)
         tested += 1
     assert tested >= 3
+
+
+# --------------------------------------------------------------------------- batch harness
+
+def test_batch_forward_matches_single_instances(orc):
+    """The threaded batch harness runs the unchanged per-instance routines: its W, objective
+    and residual equal single-instance calls for both layers, whatever the thread count."""
+    rs = np.random.default_rng(19)
+    B, K, M, T = 7, 3, 10, 4
+    H = cn(rs, B, K, M)
+    t = rs.uniform(0.5, 2.0, (B, K))
+    eta = np.full(T, ch.paper_eta(K, M))
+    lam = rs.uniform(0.1, 1.0, T)
+    mu = rs.uniform(0.01, 0.1, T)
+    for mode, p1, p2 in ((0, eta, lam), (1, mu, None)):
+        for nthreads in (1, 3):
+            W, obj, res, st = orc.batch_forward(mode, H, t, p1, p2, nthreads=nthreads)
+            assert np.all(st == orc.OK)
+            for b in range(B):
+                Wb = (orc.ufpgd_forward(H[b], t[b], eta, lam) if mode == 0
+                      else orc.ufproj_forward(H[b], t[b], mu)[0])
+                assert np.array_equal(W[b], Wb)
+                assert obj[b] == orc.l21(Wb)
+                assert res[b] == orc.residual_fro(H[b], t[b], Wb)
