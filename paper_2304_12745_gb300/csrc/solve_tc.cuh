@@ -17,7 +17,8 @@
 //     the A fragments of the second;
 //   * the accumulator fragments of the second MMA exactly the lane's W entries.
 // So no data moves between lanes for the contractions; only the per-antenna
-// column norms of the shrink reduce over the 8 lanes of a column (shuffles).
+// column norms of the shrink reduce over the 8 lanes of a column (through shared
+// memory).
 #pragma once
 
 #include "solve.cuh"

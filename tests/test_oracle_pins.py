@@ -352,6 +352,13 @@ def test_feasible_precoder_hits_paper_sum_rate(orc):
     # an infeasible precoder (the paper layer after one step) does not land on it
     W = orc.ufpgd_forward(H[0], t[0], [ch.paper_eta(K, 64)], [1 / 15])
     assert abs(orc.sum_rate(H[0], W, 1.0) - exact) > 0.1
+    # the targets scale with the noise amplitude, t_k = sigma_nu sqrt(gamma_k), so a
+    # feasible precoder meets gamma_k at any sigma_nu (here 0.5 and 3)
+    for sig in (0.5, 3.0):
+        ts = sig * t[1]
+        W = orc.zf(H[1], ts)
+        assert np.allclose(orc.sinr(H[1], W, sig), gamma, rtol=1e-9)
+        assert orc.sum_rate(H[1], W, sig) == pytest.approx(exact, abs=1e-9)
 
 
 def test_pcg_definition(orc):
