@@ -4,7 +4,9 @@
 
 #include <cmath>
 #include <cstdlib>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "api_internal.h"
 #include "train.cuh"
@@ -61,7 +63,16 @@ const TrainVariant* pick_train(int mode, int M, int K, bool tensor_cores) {
   return best;
 }
 
-int train_occupancy(const TrainVariant& v) {
+// Resident blocks per SM, set up and queried once per kernel and device: later
+// steps make no attribute or occupancy calls, so a step can be captured into a
+// CUDA graph after its first eager run.
+int train_occupancy(const TrainVariant& v, int device) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(v.fn, device);
+  const auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
   if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem) !=
       cudaSuccess)
     return 0;
@@ -70,6 +81,7 @@ int train_occupancy(const TrainVariant& v) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, v.fn, v.threads, v.smem) != cudaSuccess)
     return 0;
+  cache[key] = n;
   return n;
 }
 
@@ -119,7 +131,7 @@ extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int3
       return fail(PRECODE_ENOMEM, "precode_train_step: gradient workspace");
     p->part_bytes = part_need;
   }
-  const int occ = train_occupancy(*v);
+  const int occ = train_occupancy(*v, p->device);
   if (occ <= 0) return fail(PRECODE_ECUDA, "precode_train_step: kernel cannot run on this device");
   TrainArgs A{};
   A.s.H = static_cast<const float2*>(H);

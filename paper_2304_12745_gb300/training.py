@@ -59,14 +59,23 @@ class UnfoldedTrainer:
 
     def __init__(self, mode: int, T: int, K: int, M: int, batch: int, *, a: float,
                  lr: float = 1e-3, init_step=None, init_lam=None, device: str = "cuda",
-                 step_normalised: bool = False, group=None, tensor_cores: bool = True):
+                 step_normalised: bool = False, group=None, tensor_cores: bool = True,
+                 graphs: bool = False):
         """`group`: a torch.distributed process group whose ranks each train on
         their own batches; gradients are averaged over all ranks every step.
         `tensor_cores`: use the tensor-core forward + adjoint build where the
         shape has one (K = 8, M = 64: split FP16 for the projected layer, split
-        TF32 for the paper layer)."""
+        TF32 for the paper layer).
+        `graphs`: replay each step (forward + adjoint launch, batch reduction,
+        backward, Adam, projection) as one CUDA graph per resident batch: the
+        first step on a batch runs eagerly and captures the graph, later steps on
+        the same (H, t) tensors replay it.  Single-process trainers only."""
+        if graphs and group is not None:
+            raise ValueError("graphs=True needs a single-process trainer (group=None)")
         self.mode, self.T, self.K, self.M, self.batch, self.a = mode, T, K, M, batch, a
         self.group = group
+        self.graphs = graphs
+        self._graphs = {}
         self.plan = Plan(mode, T, [(M, K)], batch, step_normalised=step_normalised,
                          tensor_cores=tensor_cores)
         L = mp_bound(K, M)
@@ -80,8 +89,9 @@ class UnfoldedTrainer:
             self.lam = torch.nn.Parameter(torch.tensor(init_lam, dtype=torch.float32,
                                                        device=device))
             params.append(self.lam)
-        # one fused kernel per optimiser step on CUDA parameters
-        self.opt = torch.optim.Adam(params, lr=lr, fused=self.step.is_cuda)
+        # one fused kernel per optimiser step on CUDA parameters; with graphs the
+        # step count lives on the device so that the captured update can advance it
+        self.opt = torch.optim.Adam(params, lr=lr, fused=self.step.is_cuda, capturable=graphs)
         self.steps_done = 0
 
     def project(self):
@@ -101,13 +111,42 @@ class UnfoldedTrainer:
         """One Adam step on batch (H, t).  Returns the batch loss as a float, or
         with sync=False as a device tensor (no host synchronisation, so steps
         queue back to back on the stream)."""
+        if self.graphs:
+            loss = self._graphed_step(H, t)
+        else:
+            loss = self._eager_step(H, t)
+        self.steps_done += 1
+        return float(loss) if sync else loss
+
+    def _eager_step(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
         self.opt.zero_grad(set_to_none=True)
         loss = self.loss(H, t)
         loss.backward()
         self.opt.step()
         self.project()
-        self.steps_done += 1
-        return float(loss.detach()) if sync else loss.detach()
+        return loss.detach()
+
+    def _graphed_step(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+        key = (H.data_ptr(), tuple(H.shape), t.data_ptr(), tuple(t.shape))
+        entry = self._graphs.get(key)
+        if entry is not None:
+            graph, loss = entry
+            graph.replay()
+            return loss.clone()
+        # First step on this batch: a real eager step (it also sizes the plan's
+        # workspace and settles the optimiser state), then the capture of the
+        # same step, which records the work without running it.
+        loss = self._eager_step(H, t)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        self.opt.zero_grad(set_to_none=True)
+        with torch.cuda.graph(graph):
+            static_loss = self.loss(H, t)
+            static_loss.backward()
+            self.opt.step()
+            self.project()
+        self._graphs[key] = (graph, static_loss.detach())
+        return loss
 
     def make_batch(self, index: int, seed: int, family: str = "rayleigh"):
         """Channels of batch `index` (deterministic in (seed, index))."""
@@ -126,3 +165,4 @@ class UnfoldedTrainer:
                 self.lam.copy_(s["lam"])
         self.opt.load_state_dict(s["opt"])
         self.steps_done = s["steps_done"]
+        self._graphs.clear()  # captured steps refer to the replaced optimiser state

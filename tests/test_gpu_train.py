@@ -198,3 +198,34 @@ def test_paper_layer_training_reduces_the_cost():
     L = mp_bound(K, M)
     assert torch.all(tr.step >= 1 / (2 * L) - 1e-9) and torch.all(tr.step <= 1 / L + 1e-9)
     assert torch.all(tr.lam >= 0)
+
+
+@pytest.mark.parametrize("mode", ["proj", "pgd"])
+def test_graphed_training_matches_eager(mode):
+    """One CUDA graph per resident batch (first step eager + capture, then replays)
+    follows the eager trainer's trajectory: same losses and parameters, step by step,
+    over batches that alternate; a state load drops the captured steps."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.training import UnfoldedTrainer
+    K, M, T, Bt = 8, 64, 10, 1024
+    layer = capi.LAYER_PROJ if mode == "proj" else capi.LAYER_PGD
+    a = 1.0 if mode == "proj" else 1 / 15
+    t = torch.full((K,), 1.0 if mode == "proj" else math.sqrt(10.0), device="cuda")
+    eager = UnfoldedTrainer(layer, T, K, M, Bt, a=a, lr=2e-3)
+    graphed = UnfoldedTrainer(layer, T, K, M, Bt, a=a, lr=2e-3, graphs=True)
+    batches = [eager.make_batch(i, seed=6) for i in range(3)]
+    for i in range(9):
+        le = eager.train_step(batches[i % 3], t)
+        lg = graphed.train_step(batches[i % 3], t, sync=(i % 2 == 0))
+        lg = float(lg)
+        assert lg == pytest.approx(le, rel=1e-6, abs=0), (i, le, lg)
+        assert torch.allclose(graphed.step, eager.step, rtol=1e-5, atol=0), i
+        if mode == "pgd":
+            assert torch.allclose(graphed.lam, eager.lam, rtol=1e-5, atol=0), i
+    assert len(graphed._graphs) == 3
+    state = graphed.state_dict()
+    graphed.load_state_dict(state)
+    assert len(graphed._graphs) == 0
+    le = eager.train_step(batches[0], t)
+    assert graphed.train_step(batches[0], t) == pytest.approx(le, rel=1e-6, abs=0)
+    assert torch.allclose(graphed.step, eager.step, rtol=1e-5, atol=0)
