@@ -52,16 +52,20 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
   using WT = typename S::WT;
   static constexpr int KB = 8, MB = 64;
   // Per-warp shared memory, two overlaid phases (bytes):
-  //   setup : H (raw channel, scaled in place) | Q / FP64 scratch | G^{-1} (FP64) | Gram
-  //   layers: H hi / lo FP16 fragments (in place) | X fragments | norm partials | factors
+  //   setup : H (raw channel, scaled in place) | H' hi / lo FP16 fragments (written
+  //           first, for the Gram and the layers; FP64 scratch and Q on the FP64
+  //           path, which writes the fragments again) | G^{-1} (FP64) | Gram
+  //   layers: X fragments (over the raw channel) | H' hi / lo fragments | norm
+  //           partials | factors
   //   both  : t, scalars, copy barrier
   static constexpr int H_BYTES = KB * MB * 8;
-  static constexpr int OFF_Q = H_BYTES;                   // setup, 4 KB
+  static constexpr int OFF_Q = H_BYTES;                   // setup (FP64 path), 4 KB
   static constexpr int OFF_RED = OFF_Q + KB * MB * 8;     // setup, 1 KB
   static constexpr int OFF_E = OFF_RED + KB * KB * 16;    // setup, 512 B
-  static constexpr int OFF_HL = H_BYTES / 2;              // layers: lo fragments
-  static constexpr int OFF_XF = H_BYTES;                  // layers, 4 KB
-  static constexpr int OFF_NB = OFF_XF + 4096;            // layers, 2 KB
+  static constexpr int OFF_XF = 0;                        // layers, 4 KB
+  static constexpr int OFF_HH = H_BYTES;                  // setup and layers: hi fragments
+  static constexpr int OFF_HL = H_BYTES + H_BYTES / 2;    //   and lo fragments
+  static constexpr int OFF_NB = 2 * H_BYTES;              // layers, 2 KB
   static constexpr int OFF_FB = OFF_NB + 2048;            // layers, 256 B
   static constexpr int OFF_SC = (OFF_FB + 256 > OFF_E + KB * KB * 8) ? OFF_FB + 256 : OFF_E + KB * KB * 8;
   static constexpr int OFF_BAR = OFF_SC + C::SC_BYTES;
@@ -143,40 +147,51 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
     }
   }
 
-  // Q^T tile nt (the update's X values (Re Q[2q][8nt+g], Re Q[2q+1][8nt+g],
-  // Im Q[2q][8nt+g], Im Q[2q+1][8nt+g])) into qt and W^(0) = tg Q (W's layout)
-  // into wj, as split-TF32 MMAs from the lane's G^{-T} entries gi.
-  __device__ __forceinline__ static void q_tile(const Lane& L, const float2* Hs, const float (&gi)[4],
-                                                float tg, int nt, float (&qt)[4], float (&wj)[4]) {
-    uint32_t gr0h, gr0l, gr1h, gr1l, gi0h, gi0l, gi1h, gi1l;
-    split_tf32(gi[0], gr0h, gr0l);
-    split_tf32(gi[1], gr1h, gr1l);
-    split_tf32(gi[2], gi0h, gi0l);
-    split_tf32(gi[3], gi1h, gi1l);
+  // Q' tile nt into wq (W's layout, rows user g, antennas 8nt + 2q + {0, 1}) and
+  // Q'^T tile nt into qt (the update's X values (Re Q'[2q][8nt+g], Re Q'[2q+1][8nt+g],
+  // Im Q'[2q][8nt+g], Im Q'[2q+1][8nt+g])), as split-FP16 MMAs from the lane's
+  // G'^{-T} entries (g01 = Re, g23 = Im, hi / lo, scaled into FP16's range) and the
+  // scaled channel.  Both products reduce over the users; the channel pair
+  // conj(H'[2q][8nt+g]), conj(H'[2q+1][8nt+g]) is the B operand of the first and the
+  // A operand of the second, the G'^{-T} pair the other way round:
+  //   Q'   = G'^{-T} X:   A = (Re G, Im G, -Im G, Re G) rows,  B = (Re X; Im X);
+  //   Q'^T = X^T G'^{-1}: A = (Re X, Im X, -Im X, Re X) rows,  B = (Re G; Im G).
+  __device__ __forceinline__ static void q_tile_h(const Lane& L, const float2* Hs, uint32_t gh01,
+                                                  uint32_t gl01, uint32_t gh23, uint32_t gl23,
+                                                  int nt, float (&qt)[4], float (&wq)[4]) {
     const float2 h0 = Hs[(2 * L.q) * MB + 8 * nt + L.g];
     const float2 h1 = Hs[(2 * L.q + 1) * MB + 8 * nt + L.g];
-    uint32_t xr0h, xr0l, xr1h, xr1l, xi0h, xi0l, xi1h, xi1l;  // X = conj(H)
-    split_tf32(h0.x, xr0h, xr0l);
-    split_tf32(h1.x, xr1h, xr1l);
-    split_tf32(-h0.y, xi0h, xi0l);
-    split_tf32(-h1.y, xi1h, xi1l);
-    float qq[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t xrh, xrl, xih, xil;  // X = conj(H')
+    split_h2(h0.x, h1.x, xrh, xrl);
+    split_h2(-h0.y, -h1.y, xih, xil);
+    const uint32_t ngh23 = neg_h2(gh23), ngl23 = neg_h2(gl23);
+    const uint32_t nxih = neg_h2(xih), nxil = neg_h2(xil);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) qt[k] = 0.f;
-    mma_tf32(qt, xr0h, xi0h, xr1h, xi1h, gr0l, gr1l);
-    mma_tf32(qq, gr0h, gi0h, gr1h, gi1h, xr0l, xr1l);
-    mma_tf32(qt, xr0l, xi0l, xr1l, xi1l, gr0h, gr1h);
-    mma_tf32(qq, gr0l, gi0l, gr1l, gi1l, xr0h, xr1h);
-    mma_tf32(qt, neg_bits(xi0h), xr0h, neg_bits(xi1h), xr1h, gi0l, gi1l);
-    mma_tf32(qq, neg_bits(gi0h), gr0h, neg_bits(gi1h), gr1h, xi0l, xi1l);
-    mma_tf32(qt, neg_bits(xi0l), xr0l, neg_bits(xi1l), xr1l, gi0h, gi1h);
-    mma_tf32(qq, neg_bits(gi0l), gr0l, neg_bits(gi1l), gr1l, xi0h, xi1h);
-    mma_tf32(qt, xr0h, xi0h, xr1h, xi1h, gr0h, gr1h);
-    mma_tf32(qq, gr0h, gi0h, gr1h, gi1h, xr0h, xr1h);
-    mma_tf32(qt, neg_bits(xi0h), xr0h, neg_bits(xi1h), xr1h, gi0h, gi1h);
-    mma_tf32(qq, neg_bits(gi0h), gr0h, neg_bits(gi1h), gr1h, xi0h, xi1h);
+    for (int k = 0; k < 4; ++k) qt[k] = wq[k] = 0.f;
+    mma_f16(wq, gh01, gh23, ngh23, gh01, xrl, xil);
+    mma_f16(qt, xrh, xih, nxih, xrh, gl01, gl23);
+    mma_f16(wq, gl01, gl23, ngl23, gl01, xrh, xih);
+    mma_f16(qt, xrl, xil, nxil, xrl, gh01, gh23);
+    mma_f16(wq, gh01, gh23, ngh23, gh01, xrh, xih);
+    mma_f16(qt, xrh, xih, nxih, xrh, gh01, gh23);
+  }
+
+  // H' hi / lo B fragments of the residual from the lane's own channel entries hv[s]
+  // (H'[g][8s+2q], H'[g][8s+2q+1]): [pair p][lane] of (Re block 2p, Re block 2p+1,
+  // Im block 2p, Im block 2p+1).
+  __device__ __forceinline__ static void put_h_fragments(const Lane& L, const float4 (&hv)[8],
+                                                         uint4* hh, uint4* hl) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) wj[k] = tg * qq[k];
+    for (int p = 0; p < 4; ++p) {
+      const float4 a = hv[2 * p], b = hv[2 * p + 1];
+      uint32_t rah, ral, rbh, rbl, iah, ial, ibh, ibl;
+      split_h2(a.x, a.z, rah, ral);  // Re H', block 2p
+      split_h2(b.x, b.z, rbh, rbl);  // Re H', block 2p+1
+      split_h2(a.y, a.w, iah, ial);  // Im H', block 2p
+      split_h2(b.y, b.w, ibh, ibl);  // Im H', block 2p+1
+      hh[p * 32 + L.lane] = make_uint4(rah, rbh, iah, ibh);
+      hl[p * 32 + L.lane] = make_uint4(ral, rbl, ial, ibl);
+    }
   }
 
   __device__ __forceinline__ static float warp_max(float v) {
@@ -193,13 +208,16 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
   }
 
   // Per-instance setup: the scaled problem (d_k^{-1} into c.dsc, t' into c.tks),
-  // the X fragments, the H fragments and W^(0)' into w; b into beta.  With xraw,
-  // also the unscaled conj(H) B fragments of the TF32 update layout,
-  // (Re X[2q][8nt+g], Re X[2q+1][8nt+g], Im X[2q][8nt+g], Im X[2q+1][8nt+g]) at
-  // [nt][lane], taken before the scaling.  Returns the instance flags.
+  // the H' fragments (at OFF_HH / OFF_HL), the X fragments (into xf, over the raw
+  // channel) and W^(0)' into w; b into beta.  With xraw, also the unscaled conj(H)
+  // B fragments of the TF32 update layout, (Re X[2q][8nt+g], Re X[2q+1][8nt+g],
+  // Im X[2q][8nt+g], Im X[2q+1][8nt+g]) at [nt][lane], taken before the scaling.
+  // Returns the instance flags.
   __device__ static int setup(Ctx& c, const Lane& L, const SolveArgs& A, uint4* xf, WT& w,
                               float& beta, float4* xraw = nullptr) {
     float2* const Hs = c.Hs;
+    uint4* const hh = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HH);
+    uint4* const hl = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL);
     if (xraw) {
 #pragma unroll
       for (int nt = 0; nt < 8; ++nt) {
@@ -209,50 +227,68 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
       }
       __syncwarp();  // read before any lane scales its row
     }
-    // ---- per-user scales: row g of H' = d_g H[g] (in place), t'_g = d_g t_g
-    float hm = 0.f;
+    // ---- per-user scales on the lane's own entries: row g of H' = d_g H[g] (in
+    // place, for the transposed reads of Q), t'_g = d_g t_g; then the H' fragments
+    // and W = conj(H') for the Gram
+    int fl = 0;
+    float e[4];
+    {
+      float4 hv[8];
+      float hm = 0.f;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
-      hm = fmaxf(hm, fmaxf(fmaxf(fabsf(hv.x), fabsf(hv.y)), fmaxf(fabsf(hv.z), fabsf(hv.w))));
-    }
-    hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, 1));  // the 4 lanes of row g
-    hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, 2));
-    const float dg = inv_pow2_of(hm);
+      for (int s = 0; s < 8; ++s) {
+        hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+        hm = fmaxf(hm, fmaxf(fmaxf(fabsf(hv[s].x), fabsf(hv[s].y)),
+                             fmaxf(fabsf(hv[s].z), fabsf(hv[s].w))));
+      }
+      hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, 1));  // the 4 lanes of row g
+      hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, 2));
+      const float dg = inv_pow2_of(hm);
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      float4* p = reinterpret_cast<float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
-      const float4 hv = *p;
-      *p = make_float4(dg * hv.x, dg * hv.y, dg * hv.z, dg * hv.w);
-    }
-    if (L.q == 0) {
-      c.tks[L.g] *= dg;
-      c.dsc[L.g] = 1.f / dg;
+      for (int s = 0; s < 8; ++s) {
+        hv[s] = make_float4(dg * hv[s].x, dg * hv[s].y, dg * hv[s].z, dg * hv[s].w);
+        *reinterpret_cast<float4*>(Hs + L.g * MB + 8 * s + 2 * L.q) = hv[s];
+        w[s][0] = hv[s].x;
+        w[s][1] = hv[s].z;
+        w[s][2] = -hv[s].y;
+        w[s][3] = -hv[s].w;
+      }
+      put_h_fragments(L, hv, hh, hl);
+      if (L.q == 0) {
+        c.tks[L.g] *= dg;
+        c.dsc[L.g] = 1.f / dg;
+      }
     }
     __syncwarp();
 
-    // ---- Gram, inverse, Q (as the TF32 kernel, on the scaled channel)
-    int fl = 0;
-    float e[4];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const float4 hv = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
-      w[s][0] = hv.x;
-      w[s][1] = hv.z;
-      w[s][2] = -hv.y;
-      w[s][3] = -hv.w;
-    }
-    S::template residual<false>(L, Hs, nullptr, nullptr, w, c.tks, false, e);  // G'^T
+    // ---- Gram G'^T (split FP16, as a layer's residual with W = conj(H')), inverse, Q
+    residual_h(L, hh, hl, w, e);
     float gi[4];
     const bool fast = S::gram_inverse(L, e, A.cond_thr, gi);
     float qt[8][4];
     bool singular = false;
     if (fast) {
-      const float tg = c.tks[L.g];
+      // G'^{-T} into FP16's range by a power of two (undone on the products)
+      float gm = 0.f;
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) q_tile(L, Hs, gi, tg, nt, qt[nt], w[nt]);
+      for (int k = 0; k < 4; ++k) gm = fmaxf(gm, fabsf(gi[k]));
+      const float gsc = inv_pow2_of(warp_max(gm)), igs = 1.f / gsc;
+      uint32_t gh01, gl01, gh23, gl23;
+      split_h2(gsc * gi[0], gsc * gi[1], gh01, gl01);
+      split_h2(gsc * gi[2], gsc * gi[3], gh23, gl23);
+      const float tg = c.tks[L.g] * igs;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        float wq[4];
+        q_tile_h(L, Hs, gh01, gl01, gh23, gl23, nt, qt[nt], wq);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          qt[nt][k] *= igs;
+          w[nt][k] = tg * wq[k];
+        }
+      }
     } else {
-      fl = Base::fp64_inverse(c);
+      fl = Base::fp64_inverse(c);  // its scratch overlays the H' fragments
       singular = (fl & PRECODE_F_SINGULAR) != 0;
       if (!singular) {
         const double2* Gi = reinterpret_cast<const double2*>(c.red);
@@ -287,6 +323,11 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
         w[nt][2] = tg * qv.y;
         w[nt][3] = tg * qv.w;
       }
+      __syncwarp();  // Q read out: the H' fragments again, from the scaled channel
+      float4 hv[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      put_h_fragments(L, hv, hh, hl);
     }
     // ---- range of Q', then the global scale b from W^(0)' and t'
     float qm = 0.f, wm = 0.f;
@@ -308,31 +349,15 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
     for (int s = 0; s < 8; ++s)
 #pragma unroll
       for (int k = 0; k < 4; ++k) w[s][k] = singular ? 0.f : beta * w[s][k];
-    // ---- own channel entries, then the layer buffers over the setup buffers
-    float4 hv[8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
     __syncwarp();  // every read of the raw channel, of Q and of t' done
     if (L.lane < KB) c.tks[L.lane] *= beta;
+    // ---- X fragments over the raw channel
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       uint32_t rh, rl, ih, il;
       split_h2(qt[nt][0], qt[nt][1], rh, rl);
       split_h2(qt[nt][2], qt[nt][3], ih, il);
       xf[nt * 32 + L.lane] = make_uint4(rh, ih, rl, il);
-    }
-    uint4* const hh = reinterpret_cast<uint4*>(Hs);
-    uint4* const hl = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float4 a = hv[2 * p], b = hv[2 * p + 1];
-      uint32_t rah, ral, rbh, rbl, iah, ial, ibh, ibl;
-      split_h2(a.x, a.z, rah, ral);  // Re H', block 2p
-      split_h2(b.x, b.z, rbh, rbl);  // Re H', block 2p+1
-      split_h2(a.y, a.w, iah, ial);  // Im H', block 2p
-      split_h2(b.y, b.w, ibh, ibl);  // Im H', block 2p+1
-      hh[p * 32 + L.lane] = make_uint4(rah, rbh, iah, ibh);
-      hl[p * 32 + L.lane] = make_uint4(ral, rbl, ial, ibl);
     }
     __syncwarp();
     return fl;
@@ -379,18 +404,25 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
       __syncwarp();
       invLp = Base::inv_gershgorin(c);
     }
-    // W^(0)' = (b / a^2) conj(H') with max(|W^(0)'|, t') in [8, 16)
+    // W^(0)' = (b / a^2) conj(H') with max(|W^(0)'|, t') in [8, 16); the H'
+    // fragments at OFF_HH / OFF_HL
     const float beta = 16.f * inv_pow2_of(fmaxf(alpha * hm * ia2, tm));
     const float c0 = beta * ia2;
-    float4 hv[8];
+    {
+      float4 hv[8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
-      w[s][0] = c0 * hv[s].x;
-      w[s][1] = c0 * hv[s].z;
-      w[s][2] = -c0 * hv[s].y;
-      w[s][3] = -c0 * hv[s].w;
+      for (int s = 0; s < 8; ++s) {
+        hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+        w[s][0] = c0 * hv[s].x;
+        w[s][1] = c0 * hv[s].z;
+        w[s][2] = -c0 * hv[s].y;
+        w[s][3] = -c0 * hv[s].w;
+      }
+      put_h_fragments(L, hv,
+                      reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HH),
+                      reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL));
     }
+    uint4 xv[8];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {  // X = conj(H') over users 2q, 2q + 1 at antenna 8nt + g
       const float2 h0 = Hs[(2 * L.q) * MB + 8 * nt + L.g];
@@ -398,26 +430,15 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
       uint32_t rh, rl, ih, il;
       split_h2(h0.x, h1.x, rh, rl);
       split_h2(-h0.y, -h1.y, ih, il);
-      xf[nt * 32 + L.lane] = make_uint4(rh, ih, rl, il);
+      xv[nt] = make_uint4(rh, ih, rl, il);
     }
     __syncwarp();  // every read of the channel (and of the Gershgorin scratch) done
     if (L.lane < KB) {
       c.tks[L.lane] *= beta;
       c.dsc[L.lane] = 1.f;
     }
-    uint4* const hh = reinterpret_cast<uint4*>(Hs);
-    uint4* const hl = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL);
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float4 a = hv[2 * p], b = hv[2 * p + 1];
-      uint32_t rah, ral, rbh, rbl, iah, ial, ibh, ibl;
-      split_h2(a.x, a.z, rah, ral);
-      split_h2(b.x, b.z, rbh, rbl);
-      split_h2(a.y, a.w, iah, ial);
-      split_h2(b.y, b.w, ibh, ibl);
-      hh[p * 32 + L.lane] = make_uint4(rah, rbh, iah, ibh);
-      hl[p * 32 + L.lane] = make_uint4(ral, rbl, ial, ibl);
-    }
+    for (int nt = 0; nt < 8; ++nt) xf[nt * 32 + L.lane] = xv[nt];  // over the raw channel
     __syncwarp();
     ba = beta * alpha;
     f_out = alpha / beta;
@@ -454,7 +475,7 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
     c.wsum = reinterpret_cast<float*>(c.misc + 8);
     c.bar = reinterpret_cast<uint64_t*>(gs + OFF_BAR);
     uint4* const xf = reinterpret_cast<uint4*>(gs + OFF_XF);
-    const uint4* const hh = reinterpret_cast<const uint4*>(gs);
+    const uint4* const hh = reinterpret_cast<const uint4*>(gs + OFF_HH);
     const uint4* const hl = reinterpret_cast<const uint4*>(gs + OFF_HL);
     float* const nb = reinterpret_cast<float*>(gs + OFF_NB);
     float* const fb = reinterpret_cast<float*>(gs + OFF_FB);

@@ -78,7 +78,7 @@ struct TrainTCH {
     c.wsum = reinterpret_cast<float*>(c.misc + 8);
     c.bar = reinterpret_cast<uint64_t*>(gs + SH::OFF_BAR);
     uint4* const xf = reinterpret_cast<uint4*>(gs + SH::OFF_XF);
-    const uint4* const hh = reinterpret_cast<const uint4*>(gs);
+    const uint4* const hh = reinterpret_cast<const uint4*>(gs + SH::OFF_HH);
     const uint4* const hl = reinterpret_cast<const uint4*>(gs + SH::OFF_HL);
     float* const nb = reinterpret_cast<float*>(gs + SH::OFF_NB);
     float* const fb = reinterpret_cast<float*>(gs + SH::OFF_FB);
