@@ -72,10 +72,11 @@ def mma_per_instance(T: int) -> int:
 
 def mma_per_instance_f16(T: int) -> tuple:
     """Warp MMAs the split-FP16 kernel issues for one projected-layer instance:
-    (m16n8k16 FP16, m16n8k8 TF32).  Each 8 x 64 complex contraction of a layer is
-    24 FP16 MMAs (4 antenna-block pairs x Re/Im H x 3 split terms for the residual;
-    8 tiles x 3 for the update); the setup's Gram matrix, Q and Q^T stay split TF32."""
-    return 48 * T + 24, 48 + 96
+    (m16n8k16 FP16, m16n8k8 TF32).  Each 8 x 64 complex contraction is 24 FP16 MMAs
+    (4 antenna-block pairs x Re/Im H x 3 split terms for a residual; 8 tiles x 3 for
+    an update): T layers of two, the final residual, the setup's Gram matrix (one
+    residual) and Q, Q^T (8 tiles x 2 products x 3 terms).  No TF32 MMAs remain."""
+    return 48 * T + 24 + 24 + 48, 0
 
 
 def fp32_peak_tflops() -> float:
@@ -570,9 +571,9 @@ def main():
     plan_kernel_name = capi.precode_plan_describe(plan.handle, M, K)
     roof["kernel"] = plan_kernel_name
     if plan_kernel_name.startswith("solve_tch_kernel"):
-        # layers as split FP16 (m16n8k16), setup as split TF32: issued MMA work as a
-        # share of the dense tensor peaks (FP16 = the measured bf16 peak; TF32 = that
-        # times the nominal ratio 1.1 / 2.25), summed as pipe time
+        # layers and setup as split FP16 (m16n8k16): issued MMA work as a share of the
+        # dense tensor peaks (FP16 = the measured bf16 peak; TF32 = that times the
+        # nominal ratio 1.1 / 2.25), summed as pipe time
         n16, n8 = mma_per_instance_f16(T)
         sec = kern_ms / 1e3
         i16 = n16 * 2 * 16 * 8 * 16 * B / sec / 1e12
