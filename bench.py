@@ -62,6 +62,14 @@ def flops_per_instance(K: int, M: int, T: int, mode: int) -> float:
     return 8.0 * (T * per_layer + setup)
 
 
+def train_flops_per_instance(K: int, M: int, T: int) -> float:
+    """Algorithmic flops of one projected-layer train step per instance: the forward
+    (setup and T layers), the loss residual and its gradient 2 E_T H^* (one K^2 M
+    contraction each) and T reverse layers of two contractions each (g' H'^T, then
+    times Q').  The recomputation from checkpoints is not counted."""
+    return flops_per_instance(K, M, T, 1) + 8.0 * (2 * K * K * M + T * 2 * K * K * M)
+
+
 def mma_per_instance(T: int) -> int:
     """Warp MMAs (m16n8k8) the tensor-core kernel issues for one projected-layer
     instance: 48 per 8 x 64 complex contraction (2 real-form blocks x 8 tiles x 3
@@ -270,10 +278,43 @@ def bench_train(torch, capi):
     ms = e0.elapsed_time(e1) / (steps - nb)
     mu = tr.step.detach().cpu().numpy()
     tr.plan.close()
+    del batches
+    # the train-step launch alone (forward + adjoint kernel and batch reductions) on
+    # 65,536 resident instances, against the FP32 roofline
+    from paper_2304_12745_gb300.precoder import Plan
+    Bk = 65536
+    Hk = torch.from_numpy(ch.rayleigh(Bk, K, M, seed=1)).cuda()
+    tk = torch.ones(Bk, K, device="cuda")
+    muk = torch.from_numpy(ch.fixed_workload_steps(T)).cuda()
+    pk = Plan(capi.LAYER_PROJ, T, [(M, K)], Bk, tensor_cores=True)
+    lk, dk = torch.empty(1, device="cuda"), torch.empty(T, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def kstep():
+        capi.precode_train_step(pk.handle, M, K, Bk, Hk, tk, K, muk, None, 1.0, lk, dk, None,
+                                None, stream.cuda_stream)
+
+    for _ in range(3):
+        kstep()
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(20):
+        kstep()
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / 20
+    pk.close()
+    fpi = train_flops_per_instance(K, M, T)
+    kernel = {"instances": Bk, "ms_per_launch": kms, "instances_per_s": Bk / (kms / 1e3),
+              "flop_per_instance": fpi,
+              "fp32_roofline_frac": fpi * Bk / (kms / 1e3) / 1e12 / fp32_peak_tflops(),
+              "note": "precode_train_step alone (one train kernel + FP64 batch reductions); "
+                      "flops without the checkpoint recomputation"}
     return {"workload": "train: 200 Adam steps x 8,192 instances C^{8x64}, CN(0,1), T=10, lr 1e-3; "
                         "one CUDA graph per resident batch, the last 192 steps timed",
             "instances_per_s": Bt / (ms / 1e3), "ms_per_step": ms, "loss_first": first,
-            "loss_last": last, "mu_learned": [float(x) for x in mu]}, mu
+            "loss_last": last, "mu_learned": [float(x) for x in mu], "kernel": kernel}, mu
 
 
 def bench_paper_setting(torch, capi):
