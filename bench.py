@@ -296,6 +296,9 @@ def bench_train(torch, capi):
 
     for _ in range(3):
         kstep()
+    torch.cuda.nvtx.range_push("prof")  # the launch a profiler captures
+    kstep()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0.record(stream)
@@ -523,12 +526,22 @@ def main():
                     help="profiling aid: solve one uniform bucket of Rician channels (autotuned "
                          "plan), the last solve inside an NVTX range 'prof', print one line, exit")
     ap.add_argument("--bucket-instances", type=int, default=4096)
+    ap.add_argument("--train", action="store_true",
+                    help="run only the training sub-benchmark (the 200 Adam steps, then the "
+                         "train-step launch alone with one launch inside an NVTX range 'prof'), "
+                         "print its line, exit")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.bucket:
         return run_bucket(args)
+    if args.train:
+        import torch
+        from paper_2304_12745_gb300 import capi
+        line, _ = bench_train(torch, capi)
+        print(json.dumps(line))
+        return
 
     import torch
     import torch.distributed as dist
