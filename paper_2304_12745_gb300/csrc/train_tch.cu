@@ -5,8 +5,11 @@
 
 namespace precode {
 
+// 3 blocks per SM: 165 registers without spills (the 2-block build takes 237).  On the
+// 8,192-instance training step it is 5 % faster (more warps for a short persistent
+// loop); on 65,536 resident instances 4 % slower.
 void register_train_tch(std::vector<TrainVariant>& v) {
-  v.push_back(TrainVariant{kModeProj, 8, 64, true, (const void*)&train_tch_kernel<4, 2>,
+  v.push_back(TrainVariant{kModeProj, 8, 64, true, (const void*)&train_tch_kernel<4, 3>,
                            TrainTCH<4>::SMEM_BYTES, 4 * 32, 4, true, true});
 }
 
