@@ -1,8 +1,8 @@
-// Projected-layer solve kernel for K = 8 users, M = 64 antennas with the layers'
-// contractions as split-FP16 warp MMAs (m16n8k16): one warp per instance, the same
-// lane ownership as the TF32 kernel (lane (g, q) holds user g's W at antennas
-// 8s + 2q + {0, 1}), half the MMAs of the TF32 split for the same accuracy, and
-// half its fragment traffic through shared memory.
+// Solve kernel for K = 8 users, M = 64 antennas (projected layer; the paper layer
+// with MODE = kModePGD) with every contraction as split-FP16 warp MMAs (m16n8k16):
+// one warp per instance, the same lane ownership as the TF32 kernel (lane (g, q)
+// holds user g's W at antennas 8s + 2q + {0, 1}), half the MMAs of the TF32 split
+// for the same accuracy, and half its fragment traffic through shared memory.
 //
 // FP16 covers a narrow exponent range, so every instance is solved in scaled
 // units made of exact powers of two, under which the projected iteration is
@@ -22,8 +22,10 @@
 //   E_re = [ar]_g - [ai]_g+8,  E_im = [ai]_g + [ar]_g+8;
 // reduction over users (update W -= E X, k = (Re, Im) x 8 users per MMA):
 //   A rows g: (-E_re, +E_im), rows g+8: (-E_im, -E_re), B = (Re X; Im X).
-// The Gram matrix, its inverse and Q are formed once per instance exactly as in
-// the TF32 kernel (TF32 split MMAs, FP64 path for ill-conditioned instances).
+// Once per instance: the Gram matrix G'^T as a residual with W = conj(H') on the
+// same H' fragments, its Gauss-Jordan inverse in registers as in the TF32 kernel
+// (FP64 path for ill-conditioned instances), then Q' and Q'^T by split-FP16 MMAs
+// (q_tile_h).
 #pragma once
 
 #include "f16mma.cuh"
