@@ -192,6 +192,9 @@ precode_status_t precode_solve_varlen(precode_plan_t plan, int64_t B, const prec
  * With PRECODE_PLAN_TENSOR_CORES at K = 8, M = 64 the forward and adjoint run on
  * the tensor cores: split FP16 for PROJ, split TF32 for PGD (the environment
  * variable PRECODE_TRAIN_TF32, when set, selects split TF32 for PROJ as well).
+ * After a first call with the largest B, later calls allocate nothing and make no
+ * kernel-attribute or occupancy queries, so they may be captured into a CUDA graph
+ * on the given stream.
  * EINVAL: B outside [1, max_instances], NULL loss/dstep, PGD without lam/dlam. */
 precode_status_t precode_train_step(precode_plan_t plan, int32_t M, int32_t K, int64_t B,
                                     const void* H, const float* t, int64_t t_stride,
