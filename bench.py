@@ -17,7 +17,7 @@ Lines printed (rank 0, one JSON line):
   roofline   FP32 FMA-pipe roofline of the solve kernel (the path is
              arithmetic-bound: ~86 flop per HBM byte); on the tensor-core
              kernels also the issued MMA work against the dense tensor peaks
-             (split FP16 layers and split TF32 setup; or all split TF32)
+             (all split FP16; all split TF32 with --tf32)
   cpu_baseline  the FP64 oracle on this host's cores, bounded sample
   pa_gap     relative PA-consumption (||W||_{2,1}) difference GPU vs oracle on
              that sample, and the mean PCG of the GPU output
@@ -25,7 +25,8 @@ Lines printed (rank 0, one JSON line):
              --no-extras): uneven buckets, learning the steps, Poisson serving, and
              the paper's own setting (PGD 5000 iterations vs 20 unfolded layers;
              per-layer PCG of PGD and of the two unfolded layer maps trained here)
-  --impl reference runs the FP64 oracle alone (the CPU comparison arm).
+  --impl reference runs the FP64 oracle alone (the CPU comparison arm); --bucket MxK
+  and --train run one bucket solve or the training line alone (profiling aids).
 """
 from __future__ import annotations
 

@@ -1,0 +1,64 @@
+"""Host-side logic of bench.py: the algorithmic work counts behind the roofline
+fractions, and the parsing of the clock samples taken during the timed region."""
+import os
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_flop_counts():
+    # per complex multiply-add 8 flop; projected layer at (M, K) = (64, 8), T = 10:
+    # 10 layers of two K^2 M contractions, then the setup K^2 M / 2 + K^3 / 6 + K^2 M
+    K, M, T = 8, 64, 10
+    assert bench.flops_per_instance(K, M, T, 1) == pytest.approx(
+        8 * (T * 2 * K * K * M + K * K * M / 2 + K ** 3 / 6 + K * K * M))
+    assert bench.flops_per_instance(K, M, T, 1) == pytest.approx(705194.667, rel=1e-9)
+    assert bench.flops_per_instance(K, M, T, 0) == 8 * T * 2 * K * K * M  # paper layer: no setup
+    # train step: the forward, the loss residual and its gradient, T reverse layers
+    assert bench.train_flops_per_instance(K, M, T) == pytest.approx(1426090.667, rel=1e-9)
+
+
+def test_mma_counts():
+    # split FP16: 24 m16n8k16 per 8 x 64 contraction; two per layer, the final residual,
+    # the Gram matrix (one residual) and Q / Q^T (48)
+    assert bench.mma_per_instance_f16(10) == (48 * 10 + 96, 0)
+    assert bench.mma_per_instance_f16(0) == (96, 0)
+    # split TF32: 48 m16n8k8 per contraction
+    assert bench.mma_per_instance(10) == 96 * 10 + 192
+
+
+def test_fp32_peak():
+    assert bench.fp32_peak_tflops() == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
+
+
+def _summary(lines):
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.path = object(), path  # as if nvidia-smi had written the samples
+    return cs.summary()
+
+
+def test_clock_summary_under_load_and_reasons():
+    idle = "0, 1200, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    busy = "0, {}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {}"
+    s = _summary([idle, busy.format(2070, "Not Active"), busy.format(2055, "Active"),
+                  busy.format(2070, "Not Active"), idle])
+    assert s["samples"] == 5 and s["samples_under_load"] == 3
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    hot = "0, 1500, 2070, 1000.0, 0x0, Not Active, Active, Not Active, Not Active"
+    assert _summary([hot])["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_clock_summary_without_samples():
+    assert _summary(["garbage"]) is None
+    cs = bench.ClockSampler(0)
+    assert cs.summary() is None  # nvidia-smi never started
