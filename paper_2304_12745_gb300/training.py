@@ -57,6 +57,8 @@ def mp_bound(K: int, M: int) -> float:
 class UnfoldedTrainer:
     """Adam over the per-layer parameters of one layer map on one (M, K)."""
 
+    MAX_GRAPHS = 16  # captured steps kept with graphs=True (one per resident batch)
+
     def __init__(self, mode: int, T: int, K: int, M: int, batch: int, *, a: float,
                  lr: float = 1e-3, init_step=None, init_lam=None, device: str = "cuda",
                  step_normalised: bool = False, group=None, tensor_cores: bool = True,
@@ -135,8 +137,13 @@ class UnfoldedTrainer:
             return loss.clone()
         # First step on this batch: a real eager step (it also sizes the plan's
         # workspace and settles the optimiser state), then the capture of the
-        # same step, which records the work without running it.
+        # same step, which records the work without running it.  At most
+        # MAX_GRAPHS batches keep a graph (the oldest is dropped): a caller that
+        # brings a new tensor every step gets eager steps plus a capture each time,
+        # so graphs pay off only for batches that stay resident.
         loss = self._eager_step(H, t)
+        if len(self._graphs) >= self.MAX_GRAPHS:
+            self._graphs.pop(next(iter(self._graphs)))
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         self.opt.zero_grad(set_to_none=True)
