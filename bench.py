@@ -668,7 +668,8 @@ def main():
                        "l2": "inputs larger than L2 (268 MB of H per step), no flush",
                        "parallelism": f"independent shards x{world}"},
             "gpu_launches": args.steps, "roofline": roof, "clocks": clocks,
-            "flags_nonzero": int((flags_np != 0).sum())}
+            "flags_nonzero": int((flags_np != 0).sum()),
+            "fp64_fallbacks": int(((flags_np & capi.F_FP64_CHOL) != 0).sum())}
 
     # end to end through the C ABI with pinned host buffers
     Hh = torch.from_numpy(H).pin_memory()
@@ -706,6 +707,8 @@ def main():
                           Wnp[b].astype(np.complex128)) for b in range(lo, lo + min(n, 256))]
         line["pa_gap"] = {"rel_obj_diff_gpu_vs_oracle_max": float(gap.max()),
                           "rel_obj_diff_gpu_vs_oracle_mean": float(gap.mean()),
+                          "rel_obj_diff_gpu_vs_oracle_p50": float(np.percentile(gap, 50)),
+                          "rel_obj_diff_gpu_vs_oracle_p99": float(np.percentile(gap, 99)),
                           "instances": n, "mean_pcg_gpu": float(np.mean(pcg))}
     plan.close()
     del Hd, W
