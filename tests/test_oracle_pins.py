@@ -175,6 +175,25 @@ def test_single_user_constrained_closed_form(orc):
         assert opt * (1 - 1e-12) <= orc.l21(Wl) <= opt * (1 + 2e-3)
 
 
+def test_diminishing_projected_layers_approach_the_admm_optimum(orc):
+    """Cross-check of the two constrained solvers at K > 1: projected layers with a
+    diminishing shrink (sum mu = inf, sum mu^2 < inf) stay feasible and close in on
+    the ADMM optimum from above as the number of layers grows."""
+    rs = np.random.default_rng(20)
+    for _ in range(3):
+        K, M = 3, 12
+        H = cn(rs, K, M)
+        t = rs.uniform(0.5, 1.5, K)
+        opt = orc.l21(orc.admm_solve(H, t, rho=1.0, tol=1e-13, max_iter=1000000)["W"])
+        gaps = []
+        for n in (2000, 100000):
+            mu = 0.5 * opt / K / np.arange(1, n + 1) ** 0.75
+            W, st = orc.ufproj_forward(H, t, mu)
+            assert st == orc.OK and orc.residual_fro(H, t, W) < 1e-12
+            gaps.append(orc.l21(W) / opt - 1)
+        assert -1e-9 <= gaps[1] < gaps[0] and gaps[1] < 2e-4, gaps
+
+
 def _nullspace(H):
     _, sv, Vh = np.linalg.svd(H)
     return Vh[H.shape[0]:].conj().T  # columns span {x : H x = 0}

@@ -93,6 +93,7 @@ ORDER = [
     ("test_single_user_penalised_closed_form_and_factor_two", {}),
     ("test_penalised_brute_force", {}),
     ("test_single_user_constrained_closed_form", {}),
+    ("test_diminishing_projected_layers_approach_the_admm_optimum", {}),
     ("test_admm_kkt_certificate", {}),
     ("test_constrained_brute_force", dict(K=1, M=2, seed=8)),
     ("test_constrained_brute_force", dict(K=2, M=3, seed=9)),
