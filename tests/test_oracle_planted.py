@@ -153,3 +153,11 @@ def test_planted_mistake_is_caught(tmp_path, case, old, new):
     assert src.count(old) == 1, f"the text to plant '{case}' in must occur exactly once"
     caught = _first_failing_pin(_compile(src.replace(old, new), str(tmp_path)), timeout=600)
     assert caught != "none", f"no pin fails with '{case}' planted"
+
+
+def test_order_lists_every_pin():
+    """Every pin of test_oracle_pins.py takes part in the planted-mistake runs."""
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle_pins as pins
+    names = {n for n in dir(pins) if n.startswith("test_")}
+    assert names == {n for n, _ in ORDER}
