@@ -4,7 +4,8 @@ This module holds no part of the precoder's arithmetic.  It only draws random
 inputs, and it is the one module that both the GPU path and the FP64 oracle's
 tests read their inputs from.  Every draw comes from numpy's counter-based
 Philox generator keyed by an explicit seed, so a batch is reproducible on any
-machine, and a slice of a batch is the same data as the batch it came from.
+machine; for the Rayleigh and log-normal families the first b instances of a batch
+are also the batch of b instances with the same seed.
 
 Channel families (all complex64, layout [B][K][M], row k = user k, column m =
 antenna m, as in Sec. II-A of the paper):
