@@ -44,3 +44,52 @@ def test_instance_descriptor_packing_matches_abi_layout():
     raw = t.view(np.int32).reshape(2, 8)
     assert list(t[1, :3]) == [4096, 4098, 8]
     assert list(raw[0, 6:]) == [64, 8] and list(raw[1, 6:]) == [256, 32]
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "precode.h"
+
+int main(void) {
+  precode_plan_t plan = (precode_plan_t)0;
+  precode_shape_t shape = {64, 8};
+  precode_desc_t d;
+  if (precode_plan(NULL, &plan) != PRECODE_EINVAL) return 1;
+  memset(&d, 0, sizeof d);
+  d.mode = PRECODE_LAYER_PROJ;
+  d.T = 0; /* out of range: rejected before any device call */
+  d.n_shapes = 1;
+  d.shapes = &shape;
+  d.max_instances = 16;
+  if (precode_plan(&d, &plan) != PRECODE_EINVAL || plan != NULL) return 2;
+  if (strstr(precode_last_error(), "T out of range") == NULL) return 3;
+  d.T = 10;
+  d.mode = 7;
+  if (precode_plan(&d, &plan) != PRECODE_EINVAL) return 4;
+  if (strcmp(precode_status_str(PRECODE_OK), "ok") != 0) return 5;
+  if (sizeof(precode_inst_t) != 32 || sizeof(precode_shape_t) != 8) return 6;
+  puts("c-abi ok");
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_library_links_from_c(tmp_path):
+    """include/precode.h compiles as strict C99 with every warning an error, and a C
+    program links against libprecode.so and gets argument errors back without a GPU."""
+    import shutil
+    import subprocess
+    from paper_2304_12745_gb300 import build
+    lib_path = build.build()
+    cc = shutil.which("gcc") or shutil.which("cc")
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib_path)
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-l:" + os.path.basename(lib_path),
+                           "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "c-abi ok", (out.returncode, out.stderr)
