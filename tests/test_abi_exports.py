@@ -69,6 +69,39 @@ int main(void) {
   if (precode_plan(&d, &plan) != PRECODE_EINVAL) return 4;
   if (strcmp(precode_status_str(PRECODE_OK), "ok") != 0) return 5;
   if (sizeof(precode_inst_t) != 32 || sizeof(precode_shape_t) != 8) return 6;
+  /* every entry point rejects a NULL handle or descriptor before touching a device */
+  {
+    float f[16];
+    int32_t fl[2];
+    uint64_t u = 0;
+    char buf[64];
+    precode_inst_t tbl[1];
+    precode_job_t job;
+    precode_result_t res;
+    precode_serve_stats_t st;
+    precode_server_t srv = (precode_server_t)0;
+    memset(&job, 0, sizeof job);
+    memset(tbl, 0, sizeof tbl);
+    if (precode_plan_destroy(NULL) != PRECODE_EINVAL) return 10;
+    if (precode_solve(NULL, 64, 8, 1, f, f, 0, f, NULL, f, f, f, fl, NULL) != PRECODE_EINVAL) return 11;
+    if (precode_solve_host(NULL, 64, 8, 1, f, f, 0, f, NULL, f, f, f, fl) != PRECODE_EINVAL) return 12;
+    if (precode_solve_varlen(NULL, 1, tbl, f, f, f, NULL, f, f, f, fl, NULL) != PRECODE_EINVAL) return 13;
+    if (precode_train_step(NULL, 64, 8, 1, f, f, 0, f, NULL, 1.f, f, f, NULL, fl, NULL) != PRECODE_EINVAL)
+      return 14;
+    if (precode_solve_varlen_static(NULL, 1, tbl, f, f, f, NULL, f, f, f, fl, NULL) != PRECODE_EINVAL)
+      return 15;
+    if (precode_serve_create(NULL, &srv) != PRECODE_EINVAL || srv != NULL) return 16;
+    if (precode_serve_submit(NULL, &job, &u) != PRECODE_EINVAL) return 17;
+    if (precode_serve_poll(NULL, 1, &res) != PRECODE_EINVAL) return 18;
+    if (precode_serve_wait(NULL, 1, 0, &res) != PRECODE_EINVAL) return 19;
+    if (precode_serve_stats(NULL, &st) != PRECODE_EINVAL) return 20;
+    if (precode_serve_reset_stats(NULL) != PRECODE_EINVAL) return 21;
+    if (precode_serve_channel_create(NULL, 64, 8, 1, f, &u) != PRECODE_EINVAL) return 22;
+    if (precode_serve_channel_destroy(NULL, 1) != PRECODE_EINVAL) return 23;
+    if (precode_serve_destroy(NULL) != PRECODE_EINVAL) return 24;
+    if (precode_plan_errors(NULL, &u) != PRECODE_EINVAL) return 25;
+    if (precode_plan_describe(NULL, 64, 8, buf, sizeof buf) != PRECODE_EINVAL) return 26;
+  }
   puts("c-abi ok");
   return 0;
 }
@@ -77,7 +110,8 @@ int main(void) {
 
 def test_header_is_plain_c_and_library_links_from_c(tmp_path):
     """include/precode.h compiles as strict C99 with every warning an error, and a C
-    program links against libprecode.so and gets argument errors back without a GPU."""
+    program links against libprecode.so and gets PRECODE_EINVAL back from every entry
+    point for NULL handles and bad descriptors, without a GPU."""
     import shutil
     import subprocess
     from paper_2304_12745_gb300 import build
