@@ -47,9 +47,37 @@ def test_instance_descriptor_packing_matches_abi_layout():
 
 
 C_PROGRAM = r"""
+#include <pthread.h>
 #include <stdio.h>
 #include <string.h>
 #include "precode.h"
+
+/* precode_last_error() is per thread: two threads fail differently, each reads its own */
+static void* fail_plan(void* arg) {
+  precode_shape_t shape = {64, 8};
+  precode_desc_t d;
+  precode_plan_t plan;
+  int i, ok = 1;
+  (void)arg;
+  memset(&d, 0, sizeof d);
+  d.mode = PRECODE_LAYER_PROJ;
+  d.n_shapes = 1;
+  d.shapes = &shape;
+  d.max_instances = 1;
+  for (i = 0; i < 2000; ++i) {
+    precode_plan(&d, &plan);
+    ok &= strstr(precode_last_error(), "T out of range") != NULL;
+  }
+  return ok ? arg : NULL;
+}
+static void* fail_errors(void* arg) {
+  int i, ok = 1;
+  for (i = 0; i < 2000; ++i) {
+    precode_plan_errors(NULL, NULL);
+    ok &= strstr(precode_last_error(), "precode_plan_errors") != NULL;
+  }
+  return ok ? arg : NULL;
+}
 
 int main(void) {
   precode_plan_t plan = (precode_plan_t)0;
@@ -102,6 +130,22 @@ int main(void) {
     if (precode_plan_errors(NULL, &u) != PRECODE_EINVAL) return 25;
     if (precode_plan_describe(NULL, 64, 8, buf, sizeof buf) != PRECODE_EINVAL) return 26;
   }
+  {
+    pthread_t a, b;
+    void *ra = NULL, *rb = NULL;
+    int tag = 1;
+    pthread_create(&a, NULL, fail_plan, &tag);
+    pthread_create(&b, NULL, fail_errors, &tag);
+    pthread_join(a, &ra);
+    pthread_join(b, &rb);
+    if (ra != &tag || rb != &tag) return 30;
+  }
+  {
+    int c;
+    for (c = PRECODE_OK; c <= PRECODE_ENOTFOUND; ++c)
+      if (precode_status_str((precode_status_t)c) == NULL || precode_status_str((precode_status_t)c)[0] == 0)
+        return 31;
+  }
   puts("c-abi ok");
   return 0;
 }
@@ -121,7 +165,7 @@ def test_header_is_plain_c_and_library_links_from_c(tmp_path):
     src.write_text(C_PROGRAM)
     exe = tmp_path / "abi"
     libdir = os.path.dirname(lib_path)
-    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-pthread",
                            "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
                            "-L", libdir, "-l:" + os.path.basename(lib_path),
                            "-Wl,-rpath," + libdir])
