@@ -171,3 +171,36 @@ def test_header_is_plain_c_and_library_links_from_c(tmp_path):
                            "-Wl,-rpath," + libdir])
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0 and out.stdout.strip() == "c-abi ok", (out.returncode, out.stderr)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets the C
+    compiler gives the header's struct (a mismatch would corrupt arguments silently)."""
+    import json
+    import shutil
+    import subprocess
+    from paper_2304_12745_gb300 import capi
+    pairs = {"Shape": "precode_shape_t", "Desc": "precode_desc_t",
+             "ServeDesc": "precode_serve_desc_t", "Job": "precode_job_t",
+             "Result": "precode_result_t", "ServeStats": "precode_serve_stats_t"}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "precode.h"',
+             "int main(void) {", '  printf("{");']
+    first = True
+    for py, c in pairs.items():
+        for name, _ in getattr(capi, py)._fields_:
+            lines.append(f'  printf("{"" if first else ","}\\"{py}.{name}\\": %zu", offsetof({c}, {name}));')
+            first = False
+        lines.append(f'  printf(",\\"{py}\\": %zu", sizeof({c}));')
+    lines += ['  printf("}\\n");', "  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    cc = shutil.which("gcc") or shutil.which("cc")
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           str(src), "-o", str(exe)])
+    got = json.loads(subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout)
+    for py in pairs:
+        cls = getattr(capi, py)
+        assert got[py] == ctypes.sizeof(cls), py
+        for name, _ in cls._fields_:
+            assert got[f"{py}.{name}"] == getattr(cls, name).offset, (py, name)
