@@ -204,3 +204,46 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[py] == ctypes.sizeof(cls), py
         for name, _ in cls._fields_:
             assert got[f"{py}.{name}"] == getattr(cls, name).offset, (py, name)
+
+
+def _header_params():
+    """{function: [parameter kind]} from the prototypes in include/*.h, a kind being
+    'ptr' or (int|float, bytes)."""
+    scalar = {"int32_t": ("int", 4), "uint32_t": ("int", 4), "int64_t": ("int", 8),
+              "uint64_t": ("int", 8), "size_t": ("int", 8), "float": ("float", 4),
+              "double": ("float", 8)}
+    handles = {"precode_plan_t", "precode_server_t", "precode_stream_t"}
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"precode_status_t\s+(precode_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", src):
+            kinds = []
+            for p in m.group(2).split(","):
+                p = " ".join(p.split())
+                if not p or p == "void":
+                    continue
+                ty = p.rsplit(" ", 1)[0].replace("const ", "").strip()
+                if "*" in p or ty in handles:
+                    kinds.append("ptr")
+                else:
+                    kinds.append(scalar[ty])
+            out[m.group(1)] = kinds
+    return out
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"
+    if t in (ctypes.c_float, ctypes.c_double):
+        return ("float", ctypes.sizeof(t))
+    return ("int", ctypes.sizeof(t))
+
+
+def test_binding_signatures_match_the_prototypes():
+    """Each ctypes signature of the binding has the header prototype's parameter count,
+    and pointer / integer / float kinds and widths, position by position."""
+    from paper_2304_12745_gb300 import capi
+    proto = _header_params()
+    for name, args in capi._SIGS.items():
+        assert name in proto, name
+        assert [_ctypes_kind(a) for a in args] == proto[name], name
