@@ -172,6 +172,12 @@ def cpu_baseline(H, t, mu, budget_s: float = 10.0):
     import oracle
     oracle.build()
     nthreads = os.cpu_count() or 1
+    # one thread first (the per-core rate), then one thread per core
+    n1 = min(len(H), 64)
+    t0 = time.perf_counter()
+    oracle.batch_forward(1, H[:n1].astype(np.complex128), t[:n1].astype(np.float64),
+                         mu.astype(np.float64), nthreads=1)
+    single = n1 / max(time.perf_counter() - t0, 1e-9)
     n0 = min(len(H), 8 * nthreads)
     t0 = time.perf_counter()
     oracle.batch_forward(1, H[:n0].astype(np.complex128), t[:n0].astype(np.float64),
@@ -192,7 +198,8 @@ def cpu_baseline(H, t, mu, budget_s: float = 10.0):
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{done} instances of the workload in order (wrapping), FP64 projected "
-                      f"layers, {nthreads} threads over contiguous ranges, {dt:.1f} s"}, first_obj
+                      f"layers, {nthreads} threads over contiguous ranges, {dt:.1f} s",
+            "single_thread_value": single}, first_obj
 
 
 def bench_uneven(torch, capi, Plan, inst_table):

@@ -62,3 +62,22 @@ def test_clock_summary_without_samples():
     assert _summary(["garbage"]) is None
     cs = bench.ClockSampler(0)
     assert cs.summary() is None  # nvidia-smi never started
+
+
+def test_cpu_baseline_on_a_small_sample():
+    """The oracle leg of the bench: one-thread rate first, then all cores over
+    contiguous ranges; the objectives it hands back are the oracle's own."""
+    import numpy as np
+    import oracle
+    from paper_2304_12745_gb300 import channels as ch
+    H = ch.lognormal(96, 8, 64, seed=2)
+    t = ch.targets(96, 8)
+    mu = ch.fixed_workload_steps(10)
+    cb, (lo, obj) = bench.cpu_baseline(H, t, mu, budget_s=0.3)
+    assert cb["kind"] == "oracle" and cb["unit"] == "precoders/s"
+    assert cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] > 0 and cb["single_thread_value"] > 0 and cb["sample"]
+    n = len(obj)
+    _, ref, _, st = oracle.batch_forward(1, H[lo:lo + n].astype(np.complex128),
+                                         t[lo:lo + n].astype(np.float64), mu.astype(np.float64))
+    assert np.all(st == 0) and np.array_equal(obj, ref)
