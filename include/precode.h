@@ -156,7 +156,7 @@ precode_status_t precode_solve(precode_plan_t plan, int32_t M, int32_t K, int64_
 
 /* Same computation from HOST buffers (pinned memory recommended).  When every
  * buffer is page-locked host memory mapped into the device's address space and the
- * shape runs on the split-FP16 K = 8, M = 64 build, one kernel reads H and writes W
+ * shape runs on the projected layer's split-FP16 K = 8, M = 64 build, one kernel reads H and writes W
  * and the outputs in the host buffers directly (zero-copy over the host link).
  * Otherwise the batch is split in chunks whose host->device copy, solve and
  * device->host copy are pipelined over the plan's internal streams.  Both give the

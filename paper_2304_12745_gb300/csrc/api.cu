@@ -328,12 +328,14 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
     if (e != cudaSuccess) return fail(PRECODE_ENOMEM, "precode_solve_host: params buffer");
   }
   // Zero-copy: when every buffer is page-locked host memory mapped into the
-  // device's address space and the shape runs on a split-FP16 K = 8 build, its
-  // host-buffer twin reads H and writes W over the host link from inside the
-  // kernel (no staging copies; both directions overlap the solve).
+  // device's address space and the shape runs on the projected layer's split-FP16
+  // K = 8 build, its host-buffer twin reads H and writes W over the host link from
+  // inside the kernel (no staging copies; both directions overlap the solve).  The
+  // twins are projected-layer builds: the paper layer takes the staged pipeline.
   {
     const Variant* v = p->variant_for(M, K);
-    const void* hfn = (v->f16 && v->exact && v->KB == 8 && v->MB == 64)
+    const void* hfn = (p->mode == PRECODE_LAYER_PROJ && v->mode == PRECODE_LAYER_PROJ && v->f16 &&
+                       v->exact && v->KB == 8 && v->MB == 64)
                           ? tch_host_kernel(v->NW, v->minb) : nullptr;
     auto mapped = [](const void* ptr, void** dptr) -> bool {
       cudaPointerAttributes a{};
