@@ -530,6 +530,9 @@ def main():
                     help="pin the headline shape (or the --bucket shape) to its split-TF32 "
                          "tensor-core build (the split-FP16 builds are the defaults); for "
                          "profiling and comparison")
+    ap.add_argument("--ffma", action="store_true",
+                    help="run the headline on the FP32 FFMA kernel (no tensor cores); for "
+                         "profiling and comparison")
     ap.add_argument("--bucket", default=None, metavar="MxK",
                     help="profiling aid: solve one uniform bucket of Rician channels (autotuned "
                          "plan), the last solve inside an NVTX range 'prof', print one line, exit")
@@ -574,7 +577,8 @@ def main():
         plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=True, tensor_cores=True,
                     tune_cache=cache)
     else:
-        plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=not args.no_autotune, tensor_cores=True)
+        plan = Plan(capi.LAYER_PROJ, T, [(M, K)], B, autotune=not args.no_autotune,
+                    tensor_cores=not args.ffma)
     Hd = torch.from_numpy(H).cuda()
     td = torch.from_numpy(t).cuda()
     md = torch.from_numpy(mu).cuda()
