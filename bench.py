@@ -514,7 +514,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def _parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
@@ -541,7 +541,11 @@ def main():
                     help="run only the training sub-benchmark (the 200 Adam steps, then the "
                          "train-step launch alone with one launch inside an NVTX range 'prof'), "
                          "print its line, exit")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = _parser().parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

@@ -81,3 +81,22 @@ def test_cpu_baseline_on_a_small_sample():
     _, ref, _, st = oracle.batch_forward(1, H[lo:lo + n].astype(np.complex128),
                                          t[lo:lo + n].astype(np.float64), mu.astype(np.float64))
     assert np.all(st == 0) and np.array_equal(obj, ref)
+
+
+def test_profile_commands_parse():
+    """Every `python bench.py ...` command in profiles/ (continuation lines joined,
+    comments dropped) is a valid invocation of the committed bench, also with the
+    flags the summaries name for reproducing older captures."""
+    import glob
+    import re
+    cmds = []
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*")):
+        text = open(f).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            m = re.search(r"python bench\.py([^#\n]*)", line)
+            if m:
+                cmds.append((os.path.basename(f), m.group(1).split()))
+    assert len(cmds) >= 10
+    for name, argv in cmds:
+        for extra in ([], ["--tf32"], ["--ffma"]):
+            bench._parser().parse_args(argv + extra)  # SystemExit on an unknown flag
