@@ -13,6 +13,7 @@ Functions and the passages they follow:
   pgd_longrun     long-run PGD, Eq. (proxgd), constant eta / lambda
   l21, residual_fro, sinr, sum_rate, zf, pcg   Eq. (effmodel), Sec. VI-B
   ufproj_grad, ufpgd_grad   reverse mode of the unsupervised loss of Sec. V
+  ufproj_grad_supervised, ufpgd_grad_supervised   the same for the supervised loss
 """
 from __future__ import annotations
 
@@ -78,6 +79,8 @@ def _declare(L):
         "orc_penalised_objective": (_d, [_i, _i, _D, _D, _d, _D]),
         "orc_ufproj_grad": (_i, [_i, _i, _D, _D, _i, _D, _d, _D, _D]),
         "orc_ufpgd_grad": (_i, [_i, _i, _D, _D, _i, _D, _D, _d, _D, _D, _D]),
+        "orc_ufproj_grad_loss": (_i, [_i, _i, _D, _D, _i, _D, _d, _D, _D, _D]),
+        "orc_ufpgd_grad_loss": (_i, [_i, _i, _D, _D, _i, _D, _D, _d, _D, _D, _D, _D]),
         "orc_batch_forward": (_i, [_i, _i, _l, _i, _i, _D, _D, _i, _D, _D, _D, _D, _D, _I]),
         "orc_batch_admm": (_i, [_i, _l, _i, _i, _D, _D, _d, _l, _d, _D, _L, _I]),
     }
@@ -262,6 +265,36 @@ def ufpgd_grad(H, t, eta, lam, a: float):
     de, dl = np.zeros(T), np.zeros(T)
     lib().orc_ufpgd_grad(K, M, _p(H), _p(_r(t)), T, _p(eta), _p(lam), a, ctypes.byref(loss),
                          _p(de), _p(dl))
+    return loss.value, de, dl
+
+
+def ufproj_grad_supervised(H, t, mu, Wgt):
+    """(loss, dloss/dmu) for the supervised loss ||W_T - W_gt||_F^2 (Sec. V)."""
+    H, K, M = _shape(H)
+    mu = _r(mu)
+    T = len(mu)
+    Wgt = _c(Wgt)
+    assert Wgt.shape == (K, M)
+    loss = ctypes.c_double(0.0)
+    dmu = np.zeros(T)
+    st = lib().orc_ufproj_grad_loss(K, M, _p(H), _p(_r(t)), T, _p(mu), 0.0, _p(Wgt),
+                                    ctypes.byref(loss), _p(dmu))
+    if st != OK:
+        raise np.linalg.LinAlgError("Gram matrix singular")
+    return loss.value, dmu
+
+
+def ufpgd_grad_supervised(H, t, eta, lam, Wgt):
+    """(loss, dloss/deta, dloss/dlam) for ||W_T - W_gt||_F^2 through the paper layers."""
+    H, K, M = _shape(H)
+    eta, lam = _r(eta), _r(lam)
+    T = len(eta)
+    Wgt = _c(Wgt)
+    assert Wgt.shape == (K, M)
+    loss = ctypes.c_double(0.0)
+    de, dl = np.zeros(T), np.zeros(T)
+    lib().orc_ufpgd_grad_loss(K, M, _p(H), _p(_r(t)), T, _p(eta), _p(lam), 0.0, _p(Wgt),
+                              ctypes.byref(loss), _p(de), _p(dl))
     return loss.value, de, dl
 
 

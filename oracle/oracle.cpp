@@ -27,8 +27,8 @@
 //   O4  orc_pgd_longrun       long-run PGD of Eq. (proxgd) with fixed eta, lambda.
 //   O5  metrics               ||W||_{2,1} (Eq. effmodel), residual, SINR, R_sum,
 //                             ZF precoder and PCG (Sec. VI-B).
-//   O6  gradients             reverse mode of the unsupervised loss (Sec. V)
-//                             through both layer maps.
+//   O6  gradients             reverse mode of the unsupervised and the supervised
+//                             loss (Sec. V) through both layer maps.
 //
 // Readings of the paper taken here (each also listed in the design notes):
 //   * the gradient of f(W) = ||H W^T - S||_F^2 is the Wirtinger derivative
@@ -453,14 +453,27 @@ double orc_penalised_objective(int K, int M, const double* H, const double* t, d
 
 // Unsupervised loss of Sec. V with weight a on the l2,1 term:
 //   loss(W_T) = a*||W_T||_{2,1} + ||H W_T^T - S||_F^2.
+// Supervised loss of Sec. V (the MSE to a ground-truth precoder W_gt):
+//   loss(W_T) = ||W_T - W_gt||_F^2.
 // Gradients are w.r.t. real parameters; a complex gradient G_W stands for
 // dloss/dRe(W) + i dloss/dIm(W), with inner product <A,B> = Re sum conj(A) B.
 
 namespace {
 
-// dloss/dW at the output: a*w_m/||w_m|| (0 on zero columns) + 2 (W H^T - S) H^*
+// dloss/dW at the output.  Unsupervised (Wgt == nullptr): a*w_m/||w_m|| (0 on zero
+// columns) + 2 (W H^T - S) H^*.  Supervised: 2 (W - W_gt).
 void loss_and_grad(int K, int M, const cd* H, const double* t, double a, const cd* W,
-                   double* loss, cd* G) {
+                   double* loss, cd* G, const cd* Wgt = nullptr) {
+  if (Wgt) {
+    double s = 0.0;
+    for (int i = 0; i < K * M; ++i) {
+      const cd d = W[i] - Wgt[i];
+      s += std::norm(d);
+      G[i] = 2.0 * d;
+    }
+    *loss = s;
+    return;
+  }
   std::vector<cd> E(K * K);
   residual_matrix(K, M, W, H, t, E.data());
   *loss = a * l21(K, M, W) + fro2(K * K, E.data());
@@ -506,8 +519,10 @@ double shrink_backward(int K, int M, const cd* V, double tau, cd* G) {
 // Gradient of the loss after T projected layers w.r.t. mu[0..T-1].
 // The projection X -> P_A(X) is affine with a self-adjoint linear part
 // X -> X - (X H^T) G^{-T} H^*, so its adjoint applies that same map.
-int orc_ufproj_grad(int K, int M, const double* H, const double* t, int T, const double* mu,
-                    double a, double* loss, double* dmu) {
+// Wgt (K x M complex, or NULL): the supervised loss's label; NULL selects the
+// unsupervised loss with weight a.
+int orc_ufproj_grad_loss(int K, int M, const double* H, const double* t, int T, const double* mu,
+                         double a, const double* Wgt, double* loss, double* dmu) {
   const int n = K * M;
   const cd* h = as_c(H);
   std::vector<cd> trace((size_t)(T + 1) * n);
@@ -518,7 +533,7 @@ int orc_ufproj_grad(int K, int M, const double* H, const double* t, int T, const
   gram(K, M, h, Gm.data());
   cholesky(K, Gm.data(), L.data());
   std::vector<cd> g(n), E(K * K), Y(K * K);
-  loss_and_grad(K, M, h, t, a, W.data(), loss, g.data());
+  loss_and_grad(K, M, h, t, a, W.data(), loss, g.data(), Wgt ? as_c(Wgt) : nullptr);
   std::vector<double> zeros(K, 0.0);
   for (int l = T - 1; l >= 0; --l) {
     // through the linear part of the projection: g <- g - (g H^T) G^{-T} H^*
@@ -531,16 +546,23 @@ int orc_ufproj_grad(int K, int M, const double* H, const double* t, int T, const
   return ORC_OK;
 }
 
-// Gradient of the loss after T paper layers w.r.t. eta[] and lam[] (W^(0) = H^*).
-int orc_ufpgd_grad(int K, int M, const double* H, const double* t, int T, const double* eta,
-                   const double* lam, double a, double* loss, double* deta, double* dlam) {
+int orc_ufproj_grad(int K, int M, const double* H, const double* t, int T, const double* mu,
+                    double a, double* loss, double* dmu) {
+  return orc_ufproj_grad_loss(K, M, H, t, T, mu, a, nullptr, loss, dmu);
+}
+
+// Gradient of the loss after T paper layers w.r.t. eta[] and lam[] (W^(0) = H^*);
+// Wgt as for orc_ufproj_grad_loss.
+int orc_ufpgd_grad_loss(int K, int M, const double* H, const double* t, int T, const double* eta,
+                        const double* lam, double a, const double* Wgt, double* loss,
+                        double* deta, double* dlam) {
   const int n = K * M;
   const cd* h = as_c(H);
   std::vector<cd> trace((size_t)(T + 1) * n), W(n);
   ufpgd_forward(K, M, h, t, T, eta, lam, nullptr, W.data(), trace.data());
   std::vector<cd> g(n), E(K * K), V(n), EH(n), GE(K * K);
   std::vector<double> zeros(K, 0.0);
-  loss_and_grad(K, M, h, t, a, W.data(), loss, g.data());
+  loss_and_grad(K, M, h, t, a, W.data(), loss, g.data(), Wgt ? as_c(Wgt) : nullptr);
   for (int l = T - 1; l >= 0; --l) {
     const cd* Win = trace.data() + (size_t)l * n;
     // recompute V = W - eta E H^* and EH = E H^*
@@ -558,6 +580,11 @@ int orc_ufpgd_grad(int K, int M, const double* H, const double* t, int T, const 
     sub_times_Hconj(K, M, GE.data(), h, eta[l], g.data());
   }
   return ORC_OK;
+}
+
+int orc_ufpgd_grad(int K, int M, const double* H, const double* t, int T, const double* eta,
+                   const double* lam, double a, double* loss, double* deta, double* dlam) {
+  return orc_ufpgd_grad_loss(K, M, H, t, T, eta, lam, a, nullptr, loss, deta, dlam);
 }
 
 // ------------------------------------------------------------------ batch harness

@@ -451,6 +451,59 @@ def test_paper_layer_gradient_vs_central_differences(orc):
     assert tested >= 3
 
 
+def test_supervised_loss_gradients(orc):
+    """Supervised cost of Sec. V, ||W_T - W_gt||_F^2: its value is the squared
+    distance of the forward output to the label (definition); at parameters whose
+    own output is the label the loss and every gradient vanish (a minimum); and
+    the reverse mode agrees with central differences through both layer maps."""
+    rs = np.random.default_rng(23)
+    K, M, T = 4, 12, 4
+    # projected layer
+    tested = 0
+    for trial in range(30):
+        H = cn(rs, K, M)
+        t = np.ones(K)
+        mu = rs.uniform(0.01, 0.1, T)
+        if _min_kink_distance_proj(orc, H, t, mu) < 4e-3:
+            continue
+        Wref = orc.ufproj_forward(H, t, rs.uniform(0.01, 0.1, T))[0]
+        loss, g = orc.ufproj_grad_supervised(H, t, mu, Wref)
+        W = orc.ufproj_forward(H, t, mu)[0]
+        assert abs(loss - np.linalg.norm(W - Wref) ** 2) <= 1e-12 * max(loss, 1.0)
+        gfd = _fd(lambda m: orc.ufproj_grad_supervised(H, t, m, Wref)[0], mu, h=1e-6)
+        assert np.allclose(g, gfd, rtol=1e-5, atol=1e-7 * abs(loss)), (g, gfd)
+        l0, g0 = orc.ufproj_grad_supervised(H, t, mu, W)
+        assert l0 == 0.0 and np.all(g0 == 0.0)
+        tested += 1
+    assert tested >= 3
+    # paper layer
+    eta0 = ch.paper_eta(K, M)
+    tested = 0
+    for trial in range(12):
+        H = cn(rs, K, M)
+        t = np.ones(K)
+        eta = eta0 * rs.uniform(0.5, 1.0, T)
+        lam = rs.uniform(0.5, 3.0, T)
+        _, tr = orc.ufpgd_forward(H, t, eta, lam, trace=True)
+        dmin = np.inf
+        for l in range(T):
+            V = tr[l] - eta[l] * ((tr[l] @ H.T - np.diag(t)) @ H.conj())
+            dmin = min(dmin, np.abs(np.linalg.norm(V, axis=0) - lam[l] * eta[l]).min())
+        if dmin < 5e-3:
+            continue
+        Wref = orc.ufpgd_forward(H, t, eta0 * rs.uniform(0.5, 1.0, T), rs.uniform(0.5, 3.0, T))
+        loss, de, dl = orc.ufpgd_grad_supervised(H, t, eta, lam, Wref)
+        assert abs(loss - np.linalg.norm(tr[T] - Wref) ** 2) <= 1e-12 * max(loss, 1.0)
+        fe = _fd(lambda e: orc.ufpgd_grad_supervised(H, t, e, lam, Wref)[0], eta, h=1e-6)
+        fl = _fd(lambda x: orc.ufpgd_grad_supervised(H, t, eta, x, Wref)[0], lam, h=1e-3)
+        assert np.allclose(de, fe, rtol=1e-5, atol=1e-8 * abs(loss) / eta0), (de, fe)
+        assert np.allclose(dl, fl, rtol=1e-5, atol=1e-9 * abs(loss)), (dl, fl)
+        l0, d0e, d0l = orc.ufpgd_grad_supervised(H, t, eta, lam, tr[T])
+        assert l0 == 0.0 and np.all(d0e == 0.0) and np.all(d0l == 0.0)
+        tested += 1
+    assert tested >= 3
+
+
 # --------------------------------------------------------------------------- batch harness
 
 def test_batch_forward_matches_single_instances(orc):

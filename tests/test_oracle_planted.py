@@ -48,6 +48,9 @@ PLANTED = [
      "prox_l21(K, M, Z.data(), rho);"),
     ("shrink adjoint sign", "c2 = tau / (r * r * r) * vg;", "c2 = -tau / (r * r * r) * vg;"),
     ("loss gradient without factor 2", "G[k * M + m] = 2.0 * s;", "G[k * M + m] = s;"),
+    ("supervised gradient without factor 2", "      G[i] = 2.0 * d;", "      G[i] = d;"),
+    ("supervised gradient with the label's sign", "      const cd d = W[i] - Wgt[i];",
+     "      const cd d = W[i] + Wgt[i];"),
     ("paper-layer d/deta drops the threshold term", "deta[l] = -gv_eh + lam[l] * dtau;",
      "deta[l] = -gv_eh;"),
     ("projected-layer adjoint one layer off",
@@ -88,6 +91,7 @@ ORDER = [
     ("test_prox_l21_is_the_proximal_map", {}),
     ("test_projected_layer_gradient_vs_central_differences", {}),
     ("test_paper_layer_gradient_vs_central_differences", {}),
+    ("test_supervised_loss_gradients", {}),
     ("test_square_channel_leaves_no_freedom", {}),
     ("test_feasible_precoder_hits_paper_sum_rate", {}),
     ("test_single_user_penalised_closed_form_and_factor_two", {}),
