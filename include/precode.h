@@ -66,8 +66,11 @@ typedef enum {
 
 /* per-instance flag bits (int32 flags[b]) */
 #define PRECODE_F_FP64_CHOL 1   /* PROJ: equilibrated Gram condition estimate above the
-                                   threshold (or FP32 pivot failed): Gram, Cholesky and
-                                   G^{-1} were redone in FP64 */
+                                   threshold (or FP32 pivot failed): the Gram matrix was
+                                   factorised in FP64 (G = L D L^H) and the layers ran in
+                                   the orthonormal basis U = D^{-1/2} L^{-1} H of the
+                                   channel's row space, targets S~ = D^{-1/2} L^{-1} S
+                                   (the same projection, free of G^{-1}'s rounding) */
 #define PRECODE_F_SINGULAR 2    /* PROJ: Gram not positive definite even in FP64
                                    (rank(H) < K): W set to 0, obj 0, resid ||S||_F.
                                    The split-FP16 build (K = 8, M = 64) also sets it when
@@ -76,7 +79,8 @@ typedef enum {
                                    accuracy, met only on the FP64 path) */
 #define PRECODE_F_NONFINITE 4   /* NaN/Inf met in the input or the output objective */
 #define PRECODE_F_TIMEOUT 8     /* the device-side wait for this instance's channel copy
-                                   ran out (about 1 s); W not written */
+                                   ran out (about 1 s, or the limit set by
+                                   precode_plan_set_debug); W not written */
 #define PRECODE_F_INVALID 16    /* uneven batch: descriptor rejected (shape outside every
                                    plan bucket, odd M, K > M for PROJ, negative or odd
                                    offset); W not written */
@@ -116,8 +120,11 @@ typedef struct {
   int32_t n_shapes;              /* shapes the plan prepares (buckets); >= 1 */
   const precode_shape_t* shapes; /* host array [n_shapes]; 1 <= K <= 32, K <= M <= 256, M even */
   int64_t max_instances;         /* largest B any call will pass (sizes plan workspace) */
-  double cond_threshold;         /* PROJ: FP64 fallback when max(d)/min(d) of the
-                                    equilibrated Cholesky pivots exceeds it; <= 0 -> 1e3 */
+  double cond_threshold;         /* PROJ: FP64 path when max(d)/min(d) of the
+                                    equilibrated Cholesky pivots exceeds it; <= 0 -> 16.
+                                    The FP32 setup's error grows like a few x 2^-24 x
+                                    that estimate (about 1e-5 relative at 16 on the
+                                    largest bucket); the FP64 path's does not grow */
   uint32_t flags;                /* PRECODE_PLAN_* */
   int32_t device;                /* CUDA device ordinal the plan lives on */
   const char* tune_cache;        /* autotune cache file (read/written), NULL = none */
@@ -202,15 +209,35 @@ precode_status_t precode_train_step(precode_plan_t plan, int32_t M, int32_t K, i
                                     float* dstep, float* dlam, int32_t* flags,
                                     precode_stream_t stream);
 
+/* Supervised variant of precode_train_step (Sec. V, supervised cost): the loss
+ * is the mean over the batch of the MSE to known ground-truth precoders,
+ *     mean_b ||W_T - W_gt||_F^2,
+ * and its gradient at the output is 2 (W_T - W_gt); everything else (layers,
+ * adjoint, checkpoints, FP64 batch reduction, parameter gradients of zero for
+ * parameters at or below zero) is as in precode_train_step.  W_gt: DEVICE
+ * complex64 [B][K][M] in W's layout (16-byte aligned), e.g. long-run solutions of
+ * Eq. (optim1) computed offline.  An instance whose Gram matrix is singular has
+ * W_T = 0 and contributes ||W_gt||_F^2.  EINVAL: NULL W_gt, plus the conditions
+ * of precode_train_step. */
+precode_status_t precode_train_step_supervised(precode_plan_t plan, int32_t M, int32_t K,
+                                               int64_t B, const void* H, const float* t,
+                                               int64_t t_stride, const void* W_gt,
+                                               const float* step, const float* lam, float* loss,
+                                               float* dstep, float* dlam, int32_t* flags,
+                                               precode_stream_t stream);
+
 /* Uneven-batch solve that allocates no device memory (the paper has no
  * counterpart: this is a deployment variant of precode_solve_varlen).  For
  * callers that may not call cudaMalloc on their processing path, such as a
  * real-time baseband loop that reserves all memory at start-up, or a host
  * application whose memory manager owns the device.  No plan is needed: `desc`
  * gives mode, T, the shapes (buckets), cond_threshold, device and flags
- * (PRECODE_PLAN_STEP_NORMALISED only; AUTOTUNE or GRAPHS -> EINVAL); its
- * max_instances is ignored.  Arguments and results are those of
- * precode_solve_varlen, with the default kernel variant of each shape.
+ * (PRECODE_PLAN_STEP_NORMALISED only; AUTOTUNE, GRAPHS or TENSOR_CORES ->
+ * EINVAL); its max_instances is ignored.  Arguments and results are those of
+ * precode_solve_varlen with a plan made without flags: the default (FP32)
+ * kernel variant of each shape, bit for bit.  A copy wait that runs out is
+ * reported only in the instance's flags (PRECODE_F_TIMEOUT): there is no plan
+ * whose error counter it could add to.
  * Scratch (bucket instance lists, counters, timeout counter) is one fixed
  * array inside the library, about 2 MiB, that every GPU loading the library
  * holds until exit.  Limits: B <= PRECODE_STATIC_MAX_INSTANCES and at most
@@ -312,6 +339,25 @@ precode_status_t precode_serve_destroy(precode_server_t s);
 /* Number of device-side wait timeouts recorded by the plan's kernels since the
  * plan was created (synchronises the plan's device).  0 in normal operation. */
 precode_status_t precode_plan_errors(precode_plan_t plan, uint64_t* count);
+
+/* Failure-detection aid (the paper has no counterpart).  wait_limit_ns sets the
+ * limit of each device-side wait of the plan's kernels for an instance's channel
+ * copy (0 restores the default of about 1 s).  inject_copy_stall != 0 makes the
+ * plan's later launches (solve, uneven solve, train step; not the zero-copy host
+ * kernel) issue no channel copy at all, so that every such wait runs out: the
+ * waiting group or block then reports PRECODE_F_TIMEOUT in the flags of the
+ * instance it was about to solve, adds to precode_plan_errors, waits once more
+ * (bounded) and ends without writing W; instances it had not reached keep
+ * whatever their output buffers held.  Nothing faults or hangs: no copy is in
+ * flight.  This lets a caller exercise its timeout handling without a GPU fault;
+ * inject 0 restores normal operation.  A CUDA graph the plan captured earlier
+ * (PRECODE_PLAN_GRAPHS) is re-armed with these settings at its next launch.
+ * The allocation side has its own aid: with PRECODE_INJECT_ENOMEM=N in the
+ * environment, the library's N-th device or page-locked allocation counted from
+ * the moment the variable took its current value fails (PRECODE_ENOMEM).
+ * EINVAL: NULL plan. */
+precode_status_t precode_plan_set_debug(precode_plan_t plan, uint64_t wait_limit_ns,
+                                        int32_t inject_copy_stall);
 
 /* Writes the kernel the plan runs for (M, K) into buf (NUL-terminated, as the
  * profiler names it, e.g. "solve_kernel<1, 8, 64, ...>").  EINVAL if the plan

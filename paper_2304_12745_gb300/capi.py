@@ -80,10 +80,13 @@ _SIGS = {
     "precode_solve": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_solve_host": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_plan_errors": [_vp, ctypes.POINTER(ctypes.c_uint64)],
+    "precode_plan_set_debug": [_vp, ctypes.c_uint64, _i32],
     "precode_plan_describe": [_vp, _i32, _i32, ctypes.c_char_p, ctypes.c_size_t],
     "precode_solve_varlen": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "precode_train_step": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, ctypes.c_float, _vp,
                            _vp, _vp, _vp, _vp],
+    "precode_train_step_supervised": [_vp, _i32, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
+                                      _vp, _vp, _vp, _vp],
     "precode_serve_create": [ctypes.POINTER(ServeDesc), ctypes.POINTER(_vp)],
     "precode_serve_submit": [_vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)],
     "precode_serve_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(Result)],
@@ -180,6 +183,13 @@ def precode_train_step(plan, M, K, B, H, t, t_stride, step, lam, a, loss, dstep,
           "precode_train_step")
 
 
+def precode_train_step_supervised(plan, M, K, B, H, t, t_stride, W_gt, step, lam, loss, dstep,
+                                  dlam, flags, stream):
+    check(LIB.precode_train_step_supervised(plan, M, K, B, ptr(H), ptr(t), t_stride, ptr(W_gt),
+                                            ptr(step), ptr(lam), ptr(loss), ptr(dstep), ptr(dlam),
+                                            ptr(flags), stream), "precode_train_step_supervised")
+
+
 def precode_serve_create(mode, T, step, lam, shapes, n_slots=4, max_batch_instances=16384,
                          device_mem_budget=0, device=0, cond_threshold=0.0, flags=0) -> int:
     arr = (Shape * len(shapes))(*[Shape(int(m), int(k)) for (m, k) in shapes])
@@ -247,3 +257,8 @@ def precode_plan_errors(plan) -> int:
     n = ctypes.c_uint64(0)
     check(LIB.precode_plan_errors(plan, ctypes.byref(n)), "precode_plan_errors")
     return n.value
+
+
+def precode_plan_set_debug(plan, wait_limit_ns: int, inject_copy_stall: bool):
+    check(LIB.precode_plan_set_debug(plan, int(wait_limit_ns), 1 if inject_copy_stall else 0),
+          "precode_plan_set_debug")

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -25,6 +26,42 @@ precode_status_t fail(precode_status_t st, const std::string& msg) {
 
 precode_status_t cuda_fail(cudaError_t e, const char* what) {
   return fail(PRECODE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Allocation-failure injection (PRECODE_INJECT_ENOMEM=N): true for the N-th call
+// since the variable took its current value.
+static bool inject_enomem() {
+  static std::mutex mu;
+  static std::string seen;
+  static long long calls = 0;
+  const char* v = std::getenv("PRECODE_INJECT_ENOMEM");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!v || !*v) {
+    seen.clear();
+    return false;
+  }
+  if (seen != v) {
+    seen = v;
+    calls = 0;
+  }
+  const long long n = std::atoll(v);
+  return n > 0 && ++calls == n;
+}
+
+cudaError_t dev_alloc(void** ptr, size_t bytes) {
+  if (inject_enomem()) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
+cudaError_t pinned_alloc(void** ptr, size_t bytes) {
+  if (inject_enomem()) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(ptr, bytes);
 }
 
 const std::vector<Variant>& variants() {
@@ -225,7 +262,7 @@ precode_status_t precode_plan(const precode_desc_t* d, precode_plan_t* out) {
     p->T = d->T;
     p->device = d->device;
     p->max_instances = d->max_instances;
-    p->cond_thr = d->cond_threshold > 0 ? (float)d->cond_threshold : 1e3f;
+    p->cond_thr = d->cond_threshold > 0 ? (float)d->cond_threshold : kDefaultCondThreshold;
     p->flags = d->flags;
     DeviceGuard g(p->device);
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -242,7 +279,7 @@ precode_status_t precode_plan(const precode_desc_t* d, precode_plan_t* out) {
       p->shapes.push_back(s);
       p->chosen.push_back(v);
     }
-    e = cudaMalloc(&p->d_err, sizeof(unsigned long long));
+    e = dev_alloc(&p->d_err, sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(PRECODE_ENOMEM, "precode_plan: device allocation");
     e = cudaMemset(p->d_err, 0, sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(e, "precode_plan: memset");
@@ -300,7 +337,8 @@ precode_status_t precode_solve(precode_plan_t p, int32_t M, int32_t K, int64_t B
   A.M = M;
   A.T = p->T;
   A.cond_thr = p->cond_thr;
-  A.opts = (p->flags & PRECODE_PLAN_STEP_NORMALISED) ? OPT_STEP_NORMALISED : 0u;
+  A.opts = p->kernel_opts();
+  A.wait_ns = p->wait_ns;
   A.err = p->d_err;
   return launch_variant(*v, p->device, p->num_sms, A, B, (cudaStream_t)stream);
 }
@@ -324,7 +362,7 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
   DeviceGuard g(p->device);
   cudaError_t e;
   if (!p->dparams) {
-    e = cudaMalloc(&p->dparams, sizeof(float) * 2 * p->T);
+    e = dev_alloc(&p->dparams, sizeof(float) * 2 * p->T);
     if (e != cudaSuccess) return fail(PRECODE_ENOMEM, "precode_solve_host: params buffer");
   }
   // Zero-copy: when every buffer is page-locked host memory mapped into the
@@ -380,7 +418,8 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
       A.M = M;
       A.T = p->T;
       A.cond_thr = p->cond_thr;
-      A.opts = (p->flags & PRECODE_PLAN_STEP_NORMALISED) ? OPT_STEP_NORMALISED : 0u;
+      A.opts = p->kernel_opts();
+      A.wait_ns = p->wait_ns;
       A.err = p->d_err;
       const int64_t grid = std::max<int64_t>(
           1, std::min<int64_t>((int64_t)occ * p->num_sms, (B + v->groups - 1) / v->groups));
@@ -410,8 +449,8 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
     p->chunk = std::max<int64_t>(chunk, p->chunk);
     p->chunk_elems = std::max<size_t>((size_t)chunk * n, p->chunk_elems);
     for (int i = 0; i < precode_plan_s::kPipe; ++i) {
-      if (cudaMalloc(&p->dH[i], p->chunk_elems * 8) != cudaSuccess ||
-          cudaMalloc(&p->dW[i], p->chunk_elems * 8) != cudaSuccess)
+      if (dev_alloc(&p->dH[i], p->chunk_elems * 8) != cudaSuccess ||
+          dev_alloc(&p->dW[i], p->chunk_elems * 8) != cudaSuccess)
         return fail(PRECODE_ENOMEM, "precode_solve_host: staging buffers");
       if (!p->hstream[i] &&
           cudaStreamCreateWithFlags(&p->hstream[i], cudaStreamNonBlocking) != cudaSuccess)
@@ -425,7 +464,7 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
   if (t_elems > p->t_cap) {
     cudaFree(p->dt_all);
     p->dt_all = nullptr;
-    if (cudaMalloc(&p->dt_all, (size_t)t_elems * 4) != cudaSuccess)
+    if (dev_alloc(&p->dt_all, (size_t)t_elems * 4) != cudaSuccess)
       return fail(PRECODE_ENOMEM, "precode_solve_host: target buffer");
     p->t_cap = t_elems;
   }
@@ -435,9 +474,9 @@ precode_status_t precode_solve_host(precode_plan_t p, int32_t M, int32_t K, int6
     cudaFree(p->dfl_all);
     p->dobj_all = p->dres_all = nullptr;
     p->dfl_all = nullptr;
-    if (cudaMalloc(&p->dobj_all, (size_t)B * 4) != cudaSuccess ||
-        cudaMalloc(&p->dres_all, (size_t)B * 4) != cudaSuccess ||
-        cudaMalloc(&p->dfl_all, (size_t)B * 4) != cudaSuccess)
+    if (dev_alloc(&p->dobj_all, (size_t)B * 4) != cudaSuccess ||
+        dev_alloc(&p->dres_all, (size_t)B * 4) != cudaSuccess ||
+        dev_alloc(&p->dfl_all, (size_t)B * 4) != cudaSuccess)
       return fail(PRECODE_ENOMEM, "precode_solve_host: output buffers");
     p->out_cap = B;
   }
@@ -518,6 +557,15 @@ precode_status_t precode_plan_describe(precode_plan_t p, int32_t M, int32_t K, c
     std::snprintf(buf, len, "solve_kernel<%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d>", v->mode,
                   v->KB, v->MB, v->GK, v->GM, v->JC, v->exact ? 1 : 0, v->NW, v->minb,
                   v->split ? 1 : 0, v->db ? 1 : 0);
+  return PRECODE_OK;
+}
+
+precode_status_t precode_plan_set_debug(precode_plan_t p, uint64_t wait_limit_ns,
+                                        int32_t inject_copy_stall) {
+  if (!p) return fail(PRECODE_EINVAL, "precode_plan_set_debug: NULL plan");
+  std::lock_guard<std::mutex> lk(p->mu);
+  p->wait_ns = wait_limit_ns;
+  p->stall_copy = inject_copy_stall != 0;
   return PRECODE_OK;
 }
 

@@ -16,6 +16,21 @@ namespace precode {
 precode_status_t fail(precode_status_t st, const std::string& msg);
 precode_status_t cuda_fail(cudaError_t e, const char* what);
 
+// Every device and page-locked host allocation of the library goes through these
+// two.  Test aid: with PRECODE_INJECT_ENOMEM=N (N >= 1) in the environment, the
+// N-th allocation counted from the moment the variable took its current value
+// fails with cudaErrorMemoryAllocation without reaching the CUDA allocator.
+cudaError_t dev_alloc(void** ptr, size_t bytes);
+cudaError_t pinned_alloc(void** ptr, size_t bytes);
+template <class T>
+cudaError_t dev_alloc(T** ptr, size_t bytes) {
+  return dev_alloc(reinterpret_cast<void**>(ptr), bytes);
+}
+template <class T>
+cudaError_t pinned_alloc(T** ptr, size_t bytes) {
+  return pinned_alloc(reinterpret_cast<void**>(ptr), bytes);
+}
+
 class DeviceGuard {
  public:
   explicit DeviceGuard(int dev);
@@ -86,6 +101,16 @@ struct precode_plan_s {
   cudaEvent_t hev[kPipe + 1] = {};
   float* dparams = nullptr;  // [2][T]
   std::mutex mu;
+  // test aid (precode_plan_set_debug): limit of the kernels' channel-copy waits
+  // (0 = the default) and copy-stall injection
+  uint64_t wait_ns = 0;
+  bool stall_copy = false;
+
+  // Kernel option bits of this plan's launches.
+  uint32_t kernel_opts() const {
+    return ((flags & PRECODE_PLAN_STEP_NORMALISED) ? precode::OPT_STEP_NORMALISED : 0u) |
+           (stall_copy ? precode::OPT_STALL_COPY : 0u);
+  }
 
   // Variant serving (M, K): the plan shape's own variant, else the smallest
   // generic bucket of the plan that holds the shape (nullptr if none).

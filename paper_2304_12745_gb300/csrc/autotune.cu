@@ -79,10 +79,10 @@ precode_status_t autotune_plan(precode_plan_t p, const char* cache_path) {
     const int T = p->T;
     float2 *H = nullptr, *W = nullptr;
     float *t = nullptr, *prm = nullptr;
-    if (cudaMalloc(&H, (size_t)B * K * M * 8) != cudaSuccess ||
-        cudaMalloc(&W, (size_t)B * K * M * 8) != cudaSuccess ||
-        cudaMalloc(&t, (size_t)K * 4) != cudaSuccess ||
-        cudaMalloc(&prm, (size_t)2 * T * 4) != cudaSuccess) {
+    if (dev_alloc(&H, (size_t)B * K * M * 8) != cudaSuccess ||
+        dev_alloc(&W, (size_t)B * K * M * 8) != cudaSuccess ||
+        dev_alloc(&t, (size_t)K * 4) != cudaSuccess ||
+        dev_alloc(&prm, (size_t)2 * T * 4) != cudaSuccess) {
       cudaFree(H);
       cudaFree(W);
       cudaFree(t);

@@ -18,8 +18,17 @@ struct InstDesc {
 };
 static_assert(sizeof(InstDesc) == sizeof(precode_inst_t), "descriptor layout matches the ABI");
 
+// Default FP64-path threshold on the equilibrated Gram condition estimate
+// max(d) / min(d).  The FP32 setup's error grows like (a few) x 2^-24 x that
+// estimate; at 16 the FP32 path stays well inside 1e-4 (W) and 1e-5 (objective)
+// of the FP64 oracle on every kernel family, and everything above takes the FP64
+// path (Gram factorised in FP64, layers in an orthonormal basis of the channel's
+// row space), whose error does not grow with the conditioning.
+constexpr float kDefaultCondThreshold = 16.f;
+
 enum : uint32_t {
   OPT_STEP_NORMALISED = 1u,  // PGD: eta_l / (max_k sum_j |G_kj|)
+  OPT_STALL_COPY = 2u,       // test aid: issue no channel copy, so every copy wait runs out
 };
 
 struct SolveArgs {
@@ -40,6 +49,7 @@ struct SolveArgs {
   const int32_t* index;   // this bucket's instance ids (device)
   const int32_t* count;   // this bucket's instance count (device)
   unsigned long long* err;  // device counter of wait timeouts
+  uint64_t wait_ns;         // limit of one channel-copy wait (0: the default, 1 s)
 };
 
 }  // namespace precode

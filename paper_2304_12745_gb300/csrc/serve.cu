@@ -369,11 +369,11 @@ precode_status_t precode_serve_create(const precode_serve_desc_t* d, precode_ser
   if (e != cudaSuccess) return cuda_fail(e, "precode_serve_create: memory query");
   size_t budget = d->device_mem_budget > 0 ? (size_t)d->device_mem_budget : freeb / 2;
   if (budget > freeb) return fail(PRECODE_ENOMEM, "precode_serve_create: budget above free memory");
-  if (cudaMalloc(&s->arena_base, budget) != cudaSuccess)
+  if (dev_alloc(&s->arena_base, budget) != cudaSuccess)
     return fail(PRECODE_ENOMEM, "precode_serve_create: arena");
   s->arena.init(budget);
-  if (cudaMalloc(&s->d_step, 4 * d->T) != cudaSuccess ||
-      cudaMalloc(&s->d_lam, 4 * d->T) != cudaSuccess)
+  if (dev_alloc(&s->d_step, 4 * d->T) != cudaSuccess ||
+      dev_alloc(&s->d_lam, 4 * d->T) != cudaSuccess)
     return fail(PRECODE_ENOMEM, "precode_serve_create: parameters");
   cudaMemcpy(s->d_step, d->step, 4 * d->T, cudaMemcpyHostToDevice);
   cudaMemcpy(s->d_lam, d->lam ? d->lam : d->step, 4 * d->T, cudaMemcpyHostToDevice);
@@ -389,7 +389,9 @@ precode_status_t precode_serve_create(const precode_serve_desc_t* d, precode_ser
   pd.device = d->device;
   const int64_t cap = s->desc.max_batch_instances;
   for (int i = 0; i < s->desc.n_slots; ++i) {
-    auto sl = std::make_unique<Slot>();
+    // owned by the server from here on, so that a failure below frees what the slot holds
+    s->slots.push_back(std::make_unique<Slot>());
+    Slot* sl = s->slots.back().get();
     precode_status_t st = precode_plan(&pd, &sl->plan);
     if (st != PRECODE_OK) return st;
     if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -398,16 +400,15 @@ precode_status_t precode_serve_create(const precode_serve_desc_t* d, precode_ser
     // the plan's bucket workspace now, not at the first launch (allocation stalls)
     st = ensure_workspace(sl->plan);
     if (st != PRECODE_OK) return st;
-    if (cudaMallocHost(&sl->h_tbl, sizeof(precode_inst_t) * cap) != cudaSuccess ||
-        cudaMallocHost(&sl->h_obj, 4 * cap) != cudaSuccess ||
-        cudaMallocHost(&sl->h_resid, 4 * cap) != cudaSuccess ||
-        cudaMallocHost(&sl->h_flags, 4 * cap) != cudaSuccess ||
-        cudaMalloc(&sl->d_tbl, sizeof(precode_inst_t) * cap) != cudaSuccess ||
-        cudaMalloc(&sl->d_obj, 4 * cap) != cudaSuccess ||
-        cudaMalloc(&sl->d_resid, 4 * cap) != cudaSuccess ||
-        cudaMalloc(&sl->d_flags, 4 * cap) != cudaSuccess)
+    if (pinned_alloc(&sl->h_tbl, sizeof(precode_inst_t) * cap) != cudaSuccess ||
+        pinned_alloc(&sl->h_obj, 4 * cap) != cudaSuccess ||
+        pinned_alloc(&sl->h_resid, 4 * cap) != cudaSuccess ||
+        pinned_alloc(&sl->h_flags, 4 * cap) != cudaSuccess ||
+        dev_alloc(&sl->d_tbl, sizeof(precode_inst_t) * cap) != cudaSuccess ||
+        dev_alloc(&sl->d_obj, 4 * cap) != cudaSuccess ||
+        dev_alloc(&sl->d_resid, 4 * cap) != cudaSuccess ||
+        dev_alloc(&sl->d_flags, 4 * cap) != cudaSuccess)
       return fail(PRECODE_ENOMEM, "precode_serve_create: slot buffers");
-    s->slots.push_back(std::move(sl));
   }
   precode_server_t raw = s.get();
   for (auto& sl : s->slots) sl->waiter = std::thread(slot_loop, raw, sl.get());

@@ -37,6 +37,11 @@ constexpr int kModePGD = 0;
 constexpr int kModeProj = 1;
 constexpr uint64_t kCopyWaitNs = 1000000000ull;  // 1 s bound on one channel copy
 
+// Limit of one channel-copy wait for this launch (the plan may shorten it).
+__device__ __forceinline__ uint64_t copy_wait_ns(const SolveArgs& A) {
+  return A.wait_ns ? A.wait_ns : kCopyWaitNs;
+}
+
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 template <int MODE, int KB, int MB, int GK, int GM, int JC_, int NW, bool DB = false>
@@ -76,7 +81,9 @@ struct SolveCfg {
   static constexpr int RED_BYTES = align_up(TPI * RS * 4, 16);
   static constexpr int E_OFF = RED_OFF + RED_BYTES;
   static constexpr int E_BYTES = KB * KB * 8;
-  static constexpr int NRM_OFF = E_OFF + E_BYTES;
+  static constexpr int ST_OFF = E_OFF + E_BYTES;  // S~^T of the FP64 path's orthonormal basis
+  static constexpr int ST_BYTES = MODE == kModeProj ? KB * KB * 8 : 0;
+  static constexpr int NRM_OFF = ST_OFF + ST_BYTES;
   static constexpr int NRM_BYTES = WPG > 1 ? WPG * GM * NA * 4 : 0;
   static constexpr int SC_OFF = NRM_OFF + NRM_BYTES;  // t[KB] dsc[KB] piv[KB] misc[8] wsum[WPG]
   static constexpr int SC_BYTES = align_up((3 * KB + 8 + WPG) * 4, 16);
@@ -185,11 +192,17 @@ struct SolveKernel {
     return (f & 1) ? e[f / (2 * JC)][(f >> 1) % JC].y : e[f / (2 * JC)][(f >> 1) % JC].x;
   }
 
+  // S~^T [KB][KB] of an instance solved in the orthonormal basis (the buffer after E).
+  __device__ __forceinline__ static float2* st_buf(const Ctx& c) {
+    return reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(c.Es) + C::E_BYTES);
+  }
+
   // Sum the partials of the GM threads of this user row; the reduced entries
-  // (minus S on the diagonal when SUB_S, times `scale`) go to Es[k][j].
+  // (minus the target when SUB_S: S on the diagonal, or all of S~^T when the
+  // instance runs in the orthonormal basis (BASIS); times `scale`) go to Es[k][j].
   // Returns the sum of squares of the entries this thread wrote.
   __device__ __forceinline__ static float reduce(const Ctx& c, const EReg& e, int jc,
-                                                 float scale, bool sub_s) {
+                                                 float scale, bool sub_s, bool basis = false) {
     float* row = c.red + (c.a * GM + c.b) * RS;
 #pragma unroll
     for (int s = 0; s < GM; ++s) {
@@ -248,7 +261,11 @@ struct SolveKernel {
       const int k = user(c, u);
       const int j = jc * JC + jj;
       float v = acc[q];
-      if (sub_s && (f & 1) == 0 && j == k && k < Kd(c)) v -= c.tks[k];
+      if (basis) {
+        v -= reinterpret_cast<const float*>(st_buf(c))[(k * KB + j) * 2 + (f & 1)];
+      } else if (sub_s && (f & 1) == 0 && j == k && k < Kd(c)) {
+        v -= c.tks[k];
+      }
       v *= scale;
       ssq = fmaf(v, v, ssq);
       acc[q] = v;
@@ -349,7 +366,10 @@ struct SolveKernel {
   // in place by Gauss-Jordan elimination without pivoting, every thread owning
   // fixed entries; its pivots are the LDL^H pivots d_p, so max(d)/min(d) is the
   // condition estimate that decides the FP64 fallback.  Writes Q to Qs and
-  // W^(0) = S Q into w.  Returns the instance flags.
+  // W^(0) = S Q into w.  Returns the instance flags.  On the FP64 path the layers
+  // run in an orthonormal basis of the channel's row space with BASIS
+  // (setup_proj_fp64_basis), else through Q formed in FP64 (setup_proj_fp64).
+  template <bool BASIS = false>
   __device__ static int setup_proj(Ctx& c, WReg& w, float cond_thr) {
     const int K = Kd(c), M = Md(c);
     constexpr int NE = (KB * KB + TPI - 1) / TPI;  // matrix entries per thread
@@ -411,7 +431,8 @@ struct SolveKernel {
       cur = nxt;
       nxt = tmp;
     }
-    if (fail || dmax > cond_thr * dmin) return setup_proj_fp64(c, w);
+    if (fail || dmax > cond_thr * dmin)
+      return BASIS ? setup_proj_fp64_basis(c, w) : setup_proj_fp64(c, w);
     // G^{-T} = D (D G^T D)^{-1} D  -> Es
 #pragma unroll
     for (int r = 0; r < NE; ++r) {
@@ -468,16 +489,15 @@ struct SolveKernel {
     gsync(c);
   }
 
-  // FP64 Gram, LDL^H and inverse (no equilibration; a pivot below 1e-12 times
-  // its Gram diagonal entry means rank(H) < K).  G^{-1} goes to the reduction
-  // buffer (double2, K x K with row stride KB) unless the flags say singular.
-  __device__ static int fp64_inverse(Ctx& c) {
+  // FP64 Gram matrix of the channel rows and its LDL^H factorisation (no
+  // equilibration; a pivot below 1e-12 times its Gram diagonal entry means
+  // rank(H) < K), in the FP64 scratch of the Q area: G[i][j] (j < i) holds
+  // L[i][j] d_j, pv[i] = 1 / d_i.  Returns the instance flags.
+  __device__ static int fp64_ldl(Ctx& c) {
     const int K = Kd(c), M = Md(c);
     double2* G = reinterpret_cast<double2*>(c.Qs);
-    double2* U = G + KB * KB;
-    double* orig = reinterpret_cast<double*>(U + KB * KB);
+    double* orig = reinterpret_cast<double*>(G + 2 * KB * KB);
     double* pv = orig + KB;
-    double2* Gi = reinterpret_cast<double2*>(c.red);
     for (int idx = c.g; idx < K * K; idx += TPI) {
       const int i = idx / K, j = idx - i * K;
       if (j > i) continue;
@@ -521,21 +541,42 @@ struct SolveKernel {
     }
     if (c.g < K) pv[c.g] = 1.0 / G[c.g * KB + c.g].x;
     gsync(c);
+    return fl;
+  }
+
+  // Li = L^{-1} (unit lower triangular, row stride KB) from fp64_ldl's factors.
+  __device__ static void fp64_linv(Ctx& c, double2* Li) {
+    const int K = Kd(c);
+    const double2* G = reinterpret_cast<const double2*>(c.Qs);
+    const double* pv = reinterpret_cast<const double*>(G + 2 * KB * KB) + KB;
     if (c.g < K) {
       const int col = c.g;
-      U[col * KB + col] = make_double2(1.0, 0.0);
+      Li[col * KB + col] = make_double2(1.0, 0.0);
       for (int i = col + 1; i < K; ++i) {
         double sr = 0.0, si = 0.0;
         for (int p = col; p < i; ++p) {
-          const double2 a = G[i * KB + p], x = U[p * KB + col];
+          const double2 a = G[i * KB + p], x = Li[p * KB + col];
           const double ar = a.x * pv[p], ai = a.y * pv[p];
           sr += ar * x.x - ai * x.y;
           si += ar * x.y + ai * x.x;
         }
-        U[i * KB + col] = make_double2(-sr, -si);
+        Li[i * KB + col] = make_double2(-sr, -si);
       }
     }
     gsync(c);
+  }
+
+  // FP64 Gram, LDL^H and inverse.  G^{-1} goes to the reduction buffer (double2,
+  // K x K with row stride KB) unless the flags say singular.
+  __device__ static int fp64_inverse(Ctx& c) {
+    const int K = Kd(c);
+    const int fl = fp64_ldl(c);
+    if (fl & PRECODE_F_SINGULAR) return fl;
+    double2* G = reinterpret_cast<double2*>(c.Qs);
+    double2* U = G + KB * KB;
+    const double* pv = reinterpret_cast<const double*>(G + 2 * KB * KB) + KB;
+    double2* Gi = reinterpret_cast<double2*>(c.red);
+    fp64_linv(c, U);
     for (int idx = c.g; idx < K * K; idx += TPI) {
       const int i = idx / K, j = idx - i * K;
       double sr = 0.0, si = 0.0;
@@ -547,6 +588,103 @@ struct SolveKernel {
       }
       Gi[i * KB + j] = make_double2(sr, si);
     }
+    gsync(c);
+    return fl;
+  }
+
+  // FP64 Gram factorisation and an orthonormal basis of the channel's row space.
+  // With G = H H^H = L D L^H (FP64) the rows of
+  //   U = D^{-1/2} L^{-1} H      (K x M, U U^H = I)
+  // span the same space as H's, and H W^T = S becomes U W^T = S~ with the lower
+  // triangular S~ = D^{-1/2} L^{-1} S.  The projection onto that set is
+  //   P(X) = X - (X U^T - S~^T) conj(U),
+  // the same map as X - (X H^T - S) G^{-T} H^*, but rounding U to FP32 perturbs
+  // an orthogonal projector by O(u) whatever the conditioning of H, whereas
+  // Q = G^{-T} H^* in FP32 carries O(u sqrt(cond G)) into every layer and the
+  // residual's cancellation error is amplified by 1 / sigma_min(H).  Writes U
+  // over the channel in Hs, conj(U) into Qs and S~^T ([KB][KB], zero outside
+  // K x K) into St, all from FP64 sums rounded once; L^{-1} uses the reduction
+  // buffer and d^{-1/2} the E buffer.  Returns the instance flags (FP64_CHOL,
+  // plus SINGULAR / NONFINITE, in which case nothing is written).
+  __device__ static int fp64_basis(Ctx& c, float2* St) {
+    const int K = Kd(c), M = Md(c);
+    const int fl = fp64_ldl(c);
+    if (fl & PRECODE_F_SINGULAR) return fl;
+    double2* Li = reinterpret_cast<double2*>(c.red);
+    fp64_linv(c, Li);
+    double* isd = reinterpret_cast<double*>(c.Es);  // d_i^{-1/2}
+    {
+      const double* pv = reinterpret_cast<const double*>(reinterpret_cast<double2*>(c.Qs) + 2 * KB * KB) + KB;
+      if (c.g < K) isd[c.g] = sqrt(pv[c.g]);
+    }
+    gsync(c);  // the FP64 scratch in the Q area is read out
+    for (int idx = c.g; idx < K * M; idx += TPI) {
+      const int i = idx / M, m = idx - i * M;
+      double ur = 0.0, ui = 0.0;
+      for (int p = 0; p <= i; ++p) {
+        const double2 l = Li[i * KB + p];
+        const float2 h = c.Hs[p * M + m];
+        ur += l.x * h.x - l.y * h.y;
+        ui += l.x * h.y + l.y * h.x;
+      }
+      c.Qs[idx] = make_float2((float)(ur * isd[i]), (float)(-ui * isd[i]));  // conj(U)
+    }
+    for (int idx = c.g; idx < KB * KB; idx += TPI) {
+      const int k = idx / KB, j = idx - k * KB;
+      float2 v = make_float2(0.f, 0.f);
+      if (k < K && j < K && k <= j) {  // S~^T[k][j] = S~[j][k] = d_j^{-1/2} Li[j][k] t_k
+        const double2 l = Li[j * KB + k];
+        const double sc = isd[j] * (double)c.tks[k];
+        v = make_float2((float)(l.x * sc), (float)(l.y * sc));
+      }
+      St[idx] = v;
+    }
+    gsync(c);  // U complete: it replaces the channel
+    for (int idx = c.g; idx < K * M; idx += TPI) {
+      const float2 q = c.Qs[idx];
+      c.Hs[idx] = make_float2(q.x, -q.y);
+    }
+    gsync(c);
+    return fl;
+  }
+
+  // FP64 path of the projected-layer setup in the orthonormal basis (fp64_basis):
+  // S~^T into st_buf, misc[2] set (the layers subtract S~^T and the final residual
+  // reads the channel again) and W^(0) = S~^T conj(U) (the ZF precoder) into w.
+  // Returns the instance flags.
+  __device__ static int setup_proj_fp64_basis(Ctx& c, WReg& w) {
+    const int K = Kd(c), M = Md(c);
+    float2* const St = st_buf(c);
+    const int fl = fp64_basis(c, St);
+    if (fl & PRECODE_F_SINGULAR) {
+#pragma unroll
+      for (int u = 0; u < UPT; ++u)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) w[u][q] = mkc<CT>(0.f, 0.f);
+      return fl;
+    }
+    // W^(0) = S~^T conj(U) on own entries (the rows of U are orthonormal: no
+    // cancellation in these sums)
+#pragma unroll
+    for (int u = 0; u < UPT; ++u)
+#pragma unroll
+      for (int q = 0; q < NA; ++q) w[u][q] = mkc<CT>(0.f, 0.f);
+    for (int j = 0; j < K; ++j) {
+      float2 sj[UPT];
+#pragma unroll
+      for (int u = 0; u < UPT; ++u) sj[u] = St[user(c, u) * KB + j];
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        if (!pok(c, i)) continue;
+        const float4 v = *reinterpret_cast<const float4*>(c.Qs + j * M + 2 * pair(c, i));
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+          cmac(w[u][2 * i], sj[u], make_float2(v.x, v.y));
+          cmac(w[u][2 * i + 1], sj[u], make_float2(v.z, v.w));
+        }
+      }
+    }
+    if (c.g == 0) c.misc[2] = 1;
     gsync(c);
     return fl;
   }
@@ -665,7 +803,7 @@ struct SolveKernel {
     };
     // one bulk async copy of instance `it`'s channel into channel buffer q
     auto issue_copy = [&](int64_t it, int q) {
-      if (c.g != 0 || it >= n_inst) return;
+      if (c.g != 0 || it >= n_inst || (A.opts & OPT_STALL_COPY)) return;
       int64_t inst, h_off, w_off, t_off;
       int Kr, Mr;
       locate(it, inst, h_off, w_off, t_off, Kr, Mr);
@@ -691,7 +829,8 @@ struct SolveKernel {
       // ---- wait for this instance's channel (its copy was issued earlier)
       gsync(c);  // every thread of the group is done with the previous instance
       if (c.g < K) c.tks[c.g] = A.t[t_off + c.g];
-      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs) ? 1 : 0;
+      if (c.g == 0) c.misc[2] = 0;  // not (yet) in the orthonormal basis
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar + cur, par, copy_wait_ns(A)) ? 1 : 0;
       gsync(c);
       if (c.misc[0] == 0) {
         // the copy did not land in time: report, then wait (bounded) for it
@@ -699,7 +838,7 @@ struct SolveKernel {
         if (c.g == 0) {
           atomicAdd(A.err, 1ull);
           if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
-          c.misc[1] = mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs) ? 1 : 0;
+          c.misc[1] = mbar_wait_bounded(c.bar + cur, par, copy_wait_ns(A)) ? 1 : 0;
         }
         gsync(c);
         if (c.misc[1] == 0) return;
@@ -707,7 +846,7 @@ struct SolveKernel {
         issue_copy(it + NHB * stride, cur);
         continue;
       }
-      if (c.g != 0) mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs);  // already complete
+      if (c.g != 0) mbar_wait_bounded(c.bar + cur, par, copy_wait_ns(A));  // already complete
       phases ^= 1u << cur;
 
       // ---- steps -1 .. T of one instance.  Step -1 (Gram, when needed) and
@@ -735,16 +874,32 @@ struct SolveKernel {
           }
         }
         rs = 0.f;
+        // the final residual of an instance solved in the orthonormal basis is
+        // taken against the channel itself, read again from global memory
+        const float2* X = c.Hs;
+        bool basis = false;
+        if constexpr (MODE == kModeProj) {
+          if (c.misc[2]) {
+            if (s == T) {
+              int64_t i0, ho, wo, to;
+              int k0, m0;
+              locate(it, i0, ho, wo, to, k0, m0);
+              X = A.H + ho;
+            } else {
+              basis = true;
+            }
+          }
+        }
 #pragma unroll 1
         for (int jc = 0; jc < NJC; ++jc) {
-          partials(c, w, c.Hs, jc, e);
-          rs += reduce(c, e, jc, scale, s >= 0);
+          partials(c, w, X, jc, e);
+          rs += reduce(c, e, jc, scale, s >= 0, basis);
         }
         if (s < 0) {
           // Es = sum_m conj(H_km) H_jm = G^T
           gsync(c);
           if constexpr (MODE == kModeProj) {
-            fl = setup_proj(c, w, A.cond_thr);
+            fl = setup_proj<true>(c, w, A.cond_thr);
             if (fl & PRECODE_F_SINGULAR) break;
           } else {
             invL = inv_gershgorin(c);  // w still holds W^(0) = H^*

@@ -32,6 +32,9 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
   using C = typename Base::C;
   using Ctx = typename Base::Ctx;
   static constexpr int KB = 8, MB = 64;
+  // antenna tiles per update batch (4 independent MMA chains; 2 keeps the paper
+  // layer's build inside its 128 registers)
+  static constexpr int UG = MODE == kModeProj ? 4 : 2;
   static constexpr int NHB = C::NHB;
   // Per-warp shared memory, two overlaid phases (bytes):
   //   setup : H (raw channel) | Q / FP64 scratch | Gauss-Jordan buffers | Gram
@@ -49,12 +52,13 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
   static constexpr int OFF_LO = OFF_XF + 8192;                // layers, 4 KB (PRE)
   static constexpr int OFF_NB = OFF_LO + (PRE ? H_BYTES : 0); // layers, 2 KB
   static constexpr int OFF_FB = OFF_NB + 2048;                // layers, 256 B
-  static constexpr int OFF_SC = OFF_FB + 256;
+  static constexpr int OFF_ST = OFF_FB + 256;                 // S~^T of the FP64 path, 512 B
+  static constexpr int OFF_SC = OFF_ST + KB * KB * 8;
   static constexpr int OFF_BAR = OFF_SC + C::SC_BYTES;
   static constexpr int OFF_H1 = align_up(OFF_BAR + 8 * NHB, 16);
   static constexpr int GROUP_STRIDE = OFF_H1 + (DB ? H_BYTES : 0);
   static constexpr int SMEM_BYTES = C::GROUPS * GROUP_STRIDE;
-  static_assert(OFF_E + KB * KB * 8 <= OFF_SC, "setup buffers stay clear of the scalars");
+  static_assert(OFF_E + KB * KB * 8 <= OFF_ST, "setup buffers stay clear of S~^T and the scalars");
   static_assert(C::GROUPS == NW, "one instance per warp");
 
   struct Lane {
@@ -215,31 +219,59 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
     const uint32_t n0l = neg_bits(c0l), n1l = neg_bits(c1l), n2l = neg_bits(c2l),
                    n3l = neg_bits(c3l);
 #pragma unroll
-    for (int nt0 = 0; nt0 < 8; nt0 += 4) {
-      float4 xh[4], xl[4];
+    for (int nt0 = 0; nt0 < 8; nt0 += UG) {
+      float4 xh[UG], xl[UG];
+      float d[UG][4];  // the product from zero, added to W rounded (see SolveTCH::update_h)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < UG; ++u) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[u][k] = 0.f;
         xh[u] = xf[((nt0 + u) * 2 + 0) * 32 + L.lane];
         xl[u] = xf[((nt0 + u) * 2 + 1) * 32 + L.lane];
       }
+      if constexpr (MODE == kModeProj) {  // into W directly (see SolveTCH::update_h)
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(w[nt0 + u], n0h, n2h, n1h, n3h, __float_as_uint(xl[u].x), __float_as_uint(xl[u].y));
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(w[nt0 + u], n0h, n2h, n1h, n3h, __float_as_uint(xl[u].x), __float_as_uint(xl[u].y));
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(w[nt0 + u], n0l, n2l, n1l, n3l, __float_as_uint(xh[u].x), __float_as_uint(xh[u].y));
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(w[nt0 + u], n0l, n2l, n1l, n3l, __float_as_uint(xh[u].x), __float_as_uint(xh[u].y));
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(w[nt0 + u], c2h, n0h, c3h, n1h, __float_as_uint(xl[u].z), __float_as_uint(xl[u].w));
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(w[nt0 + u], c2h, n0h, c3h, n1h, __float_as_uint(xl[u].z), __float_as_uint(xl[u].w));
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(w[nt0 + u], c2l, n0l, c3l, n1l, __float_as_uint(xh[u].z), __float_as_uint(xh[u].w));
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(w[nt0 + u], c2l, n0l, c3l, n1l, __float_as_uint(xh[u].z), __float_as_uint(xh[u].w));
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(w[nt0 + u], n0h, n2h, n1h, n3h, __float_as_uint(xh[u].x), __float_as_uint(xh[u].y));
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(w[nt0 + u], n0h, n2h, n1h, n3h, __float_as_uint(xh[u].x), __float_as_uint(xh[u].y));
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        mma_tf32(w[nt0 + u], c2h, n0h, c3h, n1h, __float_as_uint(xh[u].z), __float_as_uint(xh[u].w));
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(w[nt0 + u], c2h, n0h, c3h, n1h, __float_as_uint(xh[u].z), __float_as_uint(xh[u].w));
+      } else {
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(d[u], n0h, n2h, n1h, n3h, __float_as_uint(xl[u].x), __float_as_uint(xl[u].y));
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(d[u], n0l, n2l, n1l, n3l, __float_as_uint(xh[u].x), __float_as_uint(xh[u].y));
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(d[u], c2h, n0h, c3h, n1h, __float_as_uint(xl[u].z), __float_as_uint(xl[u].w));
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(d[u], c2l, n0l, c3l, n1l, __float_as_uint(xh[u].z), __float_as_uint(xh[u].w));
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(d[u], n0h, n2h, n1h, n3h, __float_as_uint(xh[u].x), __float_as_uint(xh[u].y));
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+          mma_tf32(d[u], c2h, n0h, c3h, n1h, __float_as_uint(xh[u].z), __float_as_uint(xh[u].w));
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) w[nt0 + u][k] += d[u][k];
+      }
     }
   }
 
@@ -369,8 +401,14 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
   // fragments of the update layout, (Re X[2q][8nt+g], Re X[2q+1][8nt+g],
   // Im X[2q][8nt+g], Im X[2q+1][8nt+g]) at [nt][lane].  Returns the instance
   // flags; invL: the paper layer's step normalisation.
+  // With BASIS, FP64-path instances of the projected layer run in an orthonormal
+  // basis of the channel's row space (Base::fp64_basis: U over the raw channel,
+  // X = conj(U), S~^T at OFF_ST, *basis_out set); else their Q is formed in FP64.
+  template <bool BASIS = false>
   __device__ static int setup(Ctx& c, const Lane& L, const SolveArgs& A, float4* xf, float4* hlo,
-                              WT& w, float& invL, float4* xraw) {
+                              WT& w, float& invL, float4* xraw, bool* basis_out = nullptr) {
+    bool basis = false;
+    float2* const St = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(c.Qs) - OFF_Q + OFF_ST);
     float e[4];
     // ---- setup: lane's own conj(H) entries (user g, antennas 8s + 2q + h)
     int fl = 0;
@@ -391,6 +429,9 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       if (fast) {
         // xf lies outside the raw channel, which the other lanes still read
         q_mma(L, c.Hs, gi, c.tks[L.g], xf, w);
+      } else if constexpr (BASIS) {
+        fl = Base::fp64_basis(c, St);  // U over the channel, conj(U) into Qs, S~^T
+        basis = !(fl & PRECODE_F_SINGULAR);
       } else {
         fl = Base::fp64_inverse(c);  // G^{-1} in FP64 into the reduction buffer
         if (!(fl & PRECODE_F_SINGULAR)) {
@@ -501,15 +542,34 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
           for (int nt = 4; nt < 8; ++nt)
             put_x(nt, singular ? z : c.Qs[(2 * L.q) * MB + 8 * nt + L.g],
                   singular ? z : c.Qs[(2 * L.q + 1) * MB + 8 * nt + L.g], 1.f);
-          const float tg = c.tks[L.g];  // W^(0) = S Q
+          if (basis) {  // W^(0) = S~^T conj(U) (the ZF precoder), row g; Qs = conj(U)
 #pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            const float4 qv = singular ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                       : *reinterpret_cast<const float4*>(c.Qs + L.g * MB + 8 * s + 2 * L.q);
-            w[s][0] = tg * qv.x;
-            w[s][1] = tg * qv.z;
-            w[s][2] = tg * qv.y;
-            w[s][3] = tg * qv.w;
+            for (int s = 0; s < 8; ++s)
+#pragma unroll
+              for (int k = 0; k < 4; ++k) w[s][k] = 0.f;
+#pragma unroll 1
+            for (int j = 0; j < KB; ++j) {
+              const float2 sj = St[L.g * KB + j];
+#pragma unroll
+              for (int s = 0; s < 8; ++s) {
+                const float4 qv = *reinterpret_cast<const float4*>(c.Qs + j * MB + 8 * s + 2 * L.q);
+                w[s][0] += sj.x * qv.x - sj.y * qv.y;
+                w[s][1] += sj.x * qv.z - sj.y * qv.w;
+                w[s][2] += sj.x * qv.y + sj.y * qv.x;
+                w[s][3] += sj.x * qv.w + sj.y * qv.z;
+              }
+            }
+          } else {
+            const float tg = c.tks[L.g];  // W^(0) = S Q
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const float4 qv = singular ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                         : *reinterpret_cast<const float4*>(c.Qs + L.g * MB + 8 * s + 2 * L.q);
+              w[s][0] = tg * qv.x;
+              w[s][1] = tg * qv.z;
+              w[s][2] = tg * qv.y;
+              w[s][3] = tg * qv.w;
+            }
           }
           float2 x0[4], x1[4];
 #pragma unroll
@@ -524,6 +584,7 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       }
     }
     __syncwarp();
+    if (basis_out) *basis_out = basis;
     return fl;
   }
 
@@ -581,7 +642,7 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       }
     };
     auto issue_copy = [&](int64_t it, int qb) {
-      if (c.g != 0 || it >= n_inst) return;
+      if (c.g != 0 || it >= n_inst || (A.opts & OPT_STALL_COPY)) return;
       int64_t inst, h_off, w_off, t_off;
       locate(it, inst, h_off, w_off, t_off);
       fence_proxy_async_smem();
@@ -604,13 +665,13 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       const uint32_t par = (phases >> cur) & 1u;
       __syncwarp();
       if (c.g < KB) c.tks[c.g] = A.t[t_off + c.g];
-      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs) ? 1 : 0;
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar + cur, par, copy_wait_ns(A)) ? 1 : 0;
       __syncwarp();
       if (c.misc[0] == 0) {
         if (c.g == 0) {
           atomicAdd(A.err, 1ull);
           if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
-          c.misc[1] = mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs) ? 1 : 0;
+          c.misc[1] = mbar_wait_bounded(c.bar + cur, par, copy_wait_ns(A)) ? 1 : 0;
         }
         __syncwarp();
         if (c.misc[1] == 0) return;
@@ -618,11 +679,12 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
         issue_copy(it + NHB * stride, cur);
         continue;
       }
-      if (c.g != 0) mbar_wait_bounded(c.bar + cur, par, kCopyWaitNs);
+      if (c.g != 0) mbar_wait_bounded(c.bar + cur, par, copy_wait_ns(A));
       phases ^= 1u << cur;
 
       float invL;
-      const int fl0 = setup(c, L, A, xf, hlo, w, invL, nullptr);
+      bool basis = false;  // FP64 path: the layers run in an orthonormal basis
+      const int fl0 = setup<MODE == kModeProj>(c, L, A, xf, hlo, w, invL, nullptr, &basis);
       int fl = fl0;
       const bool singular = (fl & PRECODE_F_SINGULAR) != 0;
 
@@ -634,7 +696,15 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
         for (int l = 0; l < T; ++l) {
           if constexpr (MODE == kModeProj) {
             shrink(L, fb, colsum(L, nb, w), fmaxf(__ldg(A.step + l), 0.f), w);
-            residual<PRE>(L, c.Hs, hhi, hlo, w, c.tks, true, e);
+            residual<PRE>(L, c.Hs, hhi, hlo, w, c.tks, !basis, e);
+            if (basis) {  // S~^T[g][2q], S~^T[g][2q + 1]
+              const float4 v = *reinterpret_cast<const float4*>(
+                  reinterpret_cast<const float2*>(reinterpret_cast<const unsigned char*>(c.tks) - OFF_SC + OFF_ST) + L.g * KB + 2 * L.q);
+              e[0] -= v.x;
+              e[1] -= v.z;
+              e[2] -= v.y;
+              e[3] -= v.w;
+            }
             update(L, xf, e, w);
           } else {
             const float eta = __ldg(A.step + l) * invL;
@@ -646,6 +716,29 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
           }
         }
         if (A.resid) {
+          if (basis) {  // against the channel itself, from global memory
+            int64_t i0, ho, wo, to;
+            locate(it, i0, ho, wo, to);
+            __syncwarp();  // every lane is done with U's fragments
+#pragma unroll 1
+            for (int s = 0; s < 8; ++s) {
+              const float4 v = *reinterpret_cast<const float4*>(A.H + ho + L.g * MB + 8 * s + 2 * L.q);
+              if constexpr (PRE) {  // hi / lo fragments (Hr0, Hr1, Hi0, Hi1)
+                uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+                split_tf32(v.x, h0, l0);
+                split_tf32(v.z, h1, l1);
+                split_tf32(v.y, h2, l2);
+                split_tf32(v.w, h3, l3);
+                const_cast<float4*>(hhi)[s * 32 + L.lane] =
+                    make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(h2), __uint_as_float(h3));
+                hlo[s * 32 + L.lane] =
+                    make_float4(__uint_as_float(l0), __uint_as_float(l1), __uint_as_float(l2), __uint_as_float(l3));
+              } else {
+                *reinterpret_cast<float4*>(c.Hs + L.g * MB + 8 * s + 2 * L.q) = v;
+              }
+            }
+            __syncwarp();
+          }
           residual<PRE>(L, c.Hs, hhi, hlo, w, c.tks, true, e);
           rs = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + e[3] * e[3];
 #pragma unroll

@@ -53,6 +53,9 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
   using Lane = typename S::Lane;
   using WT = typename S::WT;
   static constexpr int KB = 8, MB = 64;
+  // antenna tiles per update batch (4 independent MMA chains; 2 keeps the paper
+  // layer's build inside its 128 registers)
+  static constexpr int UG = MODE == kModeProj ? 4 : 2;
   // Per-warp shared memory, two overlaid phases (bytes):
   //   setup : H (raw channel, scaled in place) | H' hi / lo FP16 fragments (written
   //           first, for the Gram and the layers; FP64 scratch and Q on the FP64
@@ -69,7 +72,8 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
   static constexpr int OFF_HL = H_BYTES + H_BYTES / 2;    //   and lo fragments
   static constexpr int OFF_NB = 2 * H_BYTES;              // layers, 2 KB
   static constexpr int OFF_FB = OFF_NB + 2048;            // layers, 256 B
-  static constexpr int OFF_SC = (OFF_FB + 256 > OFF_E + KB * KB * 8) ? OFF_FB + 256 : OFF_E + KB * KB * 8;
+  static constexpr int OFF_ST = OFF_FB + 256;             // S~^T of the FP64 path, 512 B
+  static constexpr int OFF_SC = (OFF_ST + 512 > OFF_E + KB * KB * 8) ? OFF_ST + 512 : OFF_E + KB * KB * 8;
   static constexpr int OFF_BAR = OFF_SC + C::SC_BYTES;
   static constexpr int GROUP_STRIDE = align_up(OFF_BAR + 8, 16);
   static constexpr int SMEM_BYTES = NW * GROUP_STRIDE;
@@ -128,7 +132,15 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
   }
 
   // W -= E X with the FP16 X fragments (xf: [tile][lane] of (Re X hi, Im X hi,
-  // Re X lo, Im X lo) pairs over users 2q, 2q+1 at antenna 8nt + g).
+  // Re X lo, Im X lo) pairs over users 2q, 2q+1 at antenna 8nt + g).  The tensor
+  // cores' FP32 accumulation does not round to nearest: adding each update to W
+  // inside the MMA shrinks W's magnitude by about half an ulp per layer, a drift
+  // that grows linearly with the number of layers (1.5e-4 relative after the
+  // classical PGD's 5,000 layers).  The paper layer, which runs thousands of
+  // layers as the classical PGD, therefore accumulates the product from zero and
+  // adds it to W with a rounded FP32 add.  The projected layer (tens of layers)
+  // keeps the MMA's own accumulation into W (the extra adds and accumulators cost
+  // 6 % of its time): its drift is below T 2^-24 relative.
   __device__ __forceinline__ static void update_h(const Lane& L, const uint4* xf, const float (&e)[4],
                                                   WT& w) {
     uint32_t h01, l01, h23, l23;
@@ -136,16 +148,34 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
     split_h2(e[2], e[3], h23, l23);
     const uint32_t nh01 = neg_h2(h01), nl01 = neg_h2(l01), nh23 = neg_h2(h23), nl23 = neg_h2(l23);
 #pragma unroll
-    for (int nt0 = 0; nt0 < 8; nt0 += 4) {
-      uint4 x[4];
+    for (int nt0 = 0; nt0 < 8; nt0 += UG) {
+      uint4 x[UG];
+      float d[UG][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = xf[(nt0 + u) * 32 + L.lane];
+      for (int u = 0; u < UG; ++u) {
+        x[u] = xf[(nt0 + u) * 32 + L.lane];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) mma_f16(w[nt0 + u], nh01, nh23, h23, nh01, x[u].z, x[u].w);
+        for (int k = 0; k < 4; ++k) d[u][k] = 0.f;
+      }
+      if constexpr (MODE == kModeProj) {  // into W directly (see above)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) mma_f16(w[nt0 + u], nl01, nl23, l23, nl01, x[u].x, x[u].y);
+        for (int u = 0; u < UG; ++u) mma_f16(w[nt0 + u], nh01, nh23, h23, nh01, x[u].z, x[u].w);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) mma_f16(w[nt0 + u], nh01, nh23, h23, nh01, x[u].x, x[u].y);
+        for (int u = 0; u < UG; ++u) mma_f16(w[nt0 + u], nl01, nl23, l23, nl01, x[u].x, x[u].y);
+#pragma unroll
+        for (int u = 0; u < UG; ++u) mma_f16(w[nt0 + u], nh01, nh23, h23, nh01, x[u].x, x[u].y);
+      } else {
+#pragma unroll
+        for (int u = 0; u < UG; ++u) mma_f16(d[u], nh01, nh23, h23, nh01, x[u].z, x[u].w);
+#pragma unroll
+        for (int u = 0; u < UG; ++u) mma_f16(d[u], nl01, nl23, l23, nl01, x[u].x, x[u].y);
+#pragma unroll
+        for (int u = 0; u < UG; ++u) mma_f16(d[u], nh01, nh23, h23, nh01, x[u].x, x[u].y);
+#pragma unroll
+        for (int u = 0; u < UG; ++u)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) w[nt0 + u][k] += d[u][k];
+      }
     }
   }
 
@@ -215,8 +245,11 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
   // B fragments of the TF32 update layout, (Re X[2q][8nt+g], Re X[2q+1][8nt+g],
   // Im X[2q][8nt+g], Im X[2q+1][8nt+g]) at [nt][lane], taken before the scaling.
   // Returns the instance flags.
+  // With BASIS, FP64-path instances run in an orthonormal basis of the channel's
+  // row space (S~^T at OFF_ST, `basis` set); else their Q is formed in FP64.
+  template <bool BASIS = false>
   __device__ static int setup(Ctx& c, const Lane& L, const SolveArgs& A, uint4* xf, WT& w,
-                              float& beta, float4* xraw = nullptr) {
+                              float& beta, float4* xraw = nullptr, bool* basis_out = nullptr) {
     float2* const Hs = c.Hs;
     uint4* const hh = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HH);
     uint4* const hl = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL);
@@ -268,7 +301,7 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
     float gi[4];
     const bool fast = S::gram_inverse(L, e, A.cond_thr, gi);
     float qt[8][4];
-    bool singular = false;
+    bool singular = false, basis = false;
     if (fast) {
       // G'^{-T} into FP16's range by a power of two (undone on the products)
       float gm = 0.f;
@@ -289,6 +322,46 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
           w[nt][k] = tg * wq[k];
         }
       }
+    } else if constexpr (BASIS) {
+      // FP64 path in an orthonormal basis of the scaled channel's row space: U
+      // replaces H' (rows of unit norm, inside FP16's range), X = conj(U) and the
+      // layers subtract S~^T (Base::fp64_basis; its scratch overlays the H'
+      // fragments, which are written again from U)
+      float2* const St = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Hs) + OFF_ST);
+      fl = Base::fp64_basis(c, St);
+      singular = (fl & PRECODE_F_SINGULAR) != 0;
+      basis = !singular;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float2 x0 = singular ? make_float2(0.f, 0.f) : Hs[(2 * L.q) * MB + 8 * nt + L.g];
+        const float2 x1 = singular ? make_float2(0.f, 0.f) : Hs[(2 * L.q + 1) * MB + 8 * nt + L.g];
+        qt[nt][0] = x0.x;
+        qt[nt][1] = x1.x;
+        qt[nt][2] = -x0.y;
+        qt[nt][3] = -x1.y;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[nt][k] = 0.f;
+      }
+      if (!singular) {  // W^(0) = S~^T conj(U) (the ZF precoder), row g
+#pragma unroll 1
+        for (int j = 0; j < KB; ++j) {
+          const float2 sj = St[L.g * KB + j];
+#pragma unroll
+          for (int nt = 0; nt < 8; ++nt) {
+            const float4 u = *reinterpret_cast<const float4*>(Hs + j * MB + 8 * nt + 2 * L.q);
+            // += sj * conj(u)
+            w[nt][0] += sj.x * u.x + sj.y * u.y;
+            w[nt][1] += sj.x * u.z + sj.y * u.w;
+            w[nt][2] += sj.y * u.x - sj.x * u.y;
+            w[nt][3] += sj.y * u.z - sj.x * u.w;
+          }
+        }
+      }
+      __syncwarp();  // U read out: the fragments from it
+      float4 hv[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) hv[s] = *reinterpret_cast<const float4*>(Hs + L.g * MB + 8 * s + 2 * L.q);
+      put_h_fragments(L, hv, hh, hl);
     } else {
       fl = Base::fp64_inverse(c);  // its scratch overlays the H' fragments
       singular = (fl & PRECODE_F_SINGULAR) != 0;
@@ -353,6 +426,14 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
       for (int k = 0; k < 4; ++k) w[s][k] = singular ? 0.f : beta * w[s][k];
     __syncwarp();  // every read of the raw channel, of Q and of t' done
     if (L.lane < KB) c.tks[L.lane] *= beta;
+    if (basis) {  // S~^T in the same units as t'
+      float2* const St = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(Hs) + OFF_ST);
+      for (int idx = L.lane; idx < KB * KB; idx += 32) {
+        const float2 v = St[idx];
+        St[idx] = make_float2(beta * v.x, beta * v.y);
+      }
+    }
+    if (basis_out) *basis_out = basis;
     // ---- X fragments over the raw channel
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
@@ -503,7 +584,7 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
       }
     };
     auto issue_copy = [&](int64_t it) {
-      if (HOSTIO || c.g != 0 || it >= n_inst) return;
+      if (HOSTIO || c.g != 0 || it >= n_inst || (A.opts & OPT_STALL_COPY)) return;
       int64_t inst, h_off, w_off, t_off;
       locate(it, inst, h_off, w_off, t_off);
       fence_proxy_async_smem();
@@ -530,13 +611,13 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
         for (int j = 0; j < KB * MB * 8 / 16 / 32; ++j) dst[L.lane + 32 * j] = v[j];
         __syncwarp();
       } else {
-      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A)) ? 1 : 0;
       __syncwarp();
       if (c.misc[0] == 0) {
         if (c.g == 0) {
           atomicAdd(A.err, 1ull);
           if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
-          c.misc[1] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+          c.misc[1] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A)) ? 1 : 0;
         }
         __syncwarp();
         if (c.misc[1] == 0) return;
@@ -544,14 +625,15 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
         issue_copy(it + stride);
         continue;
       }
-      if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);
+      if (c.g != 0) mbar_wait_bounded(c.bar, phase, copy_wait_ns(A));
       phase ^= 1u;
       }
 
       float beta = 1.f, f_out, f_res, invLp = 1.f, ba = 1.f;
       int fl = 0;
+      bool basis = false;  // FP64 path: the layers run in an orthonormal basis
       if constexpr (MODE == kModeProj) {
-        fl = setup(c, L, A, xf, w, beta);
+        fl = setup<true>(c, L, A, xf, w, beta, nullptr, &basis);
         f_out = f_res = 1.f / beta;
       } else {
         setup_pgd(c, L, A, xf, w, invLp, ba, f_out, f_res);
@@ -567,8 +649,17 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
           if constexpr (MODE == kModeProj) {
             S::shrink(L, fb, S::colsum(L, nb, w), fmaxf(__ldg(A.step + l), 0.f) * beta, w);
             residual_h(L, hh, hl, w, e);
-            if (2 * L.q == L.g) e[0] -= c.tks[L.g];
-            if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
+            if (basis) {  // S~^T[g][2q], S~^T[g][2q + 1]
+              const float4 v = *reinterpret_cast<const float4*>(
+                  reinterpret_cast<const float2*>(smem + c.gid * GROUP_STRIDE + OFF_ST) + L.g * KB + 2 * L.q);
+              e[0] -= v.x;
+              e[1] -= v.z;
+              e[2] -= v.y;
+              e[3] -= v.w;
+            } else {
+              if (2 * L.q == L.g) e[0] -= c.tks[L.g];
+              if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
+            }
             update_h(L, xf, e, w);
           } else {  // residual, gradient step, shrink (the paper's order)
             const float eta = __ldg(A.step + l) * invLp;
@@ -582,6 +673,18 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
           }
         }
         if (A.resid) {
+          if (basis) {  // against the channel itself: its H' fragments from global memory
+            const float dg = 1.f / c.dsc[L.g];  // a power of two: exact
+            float4 hv[8];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+              const float4 v = *reinterpret_cast<const float4*>(A.H + h_off + L.g * MB + 8 * s + 2 * L.q);
+              hv[s] = make_float4(dg * v.x, dg * v.y, dg * v.z, dg * v.w);
+            }
+            __syncwarp();
+            put_h_fragments(L, hv, const_cast<uint4*>(hh), const_cast<uint4*>(hl));
+            __syncwarp();
+          }
           residual_h(L, hh, hl, w, e);
           if (2 * L.q == L.g) e[0] -= c.tks[L.g];
           if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];

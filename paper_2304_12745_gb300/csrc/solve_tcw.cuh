@@ -143,6 +143,17 @@ struct SolveTCW {
     }
   }
 
+  // Subtract the full target S~^T (rows 8w + g, columns 8ct + 2q, 8ct + 2q + 1) of
+  // an instance solved in the orthonormal basis (St: [KB][KB] float2, natural).
+  __device__ __forceinline__ static void sub_st(const Lane& L, const float2* St, int ct,
+                                                float (&e)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(St + (8 * L.w + L.g) * KB + 8 * ct + 2 * L.q);
+    e[0] -= v.x;
+    e[1] -= v.z;
+    e[2] -= v.y;
+    e[3] -= v.w;
+  }
+
   // ----------------------------------------------------------------- update
   // W[8w+g][:] -= F X with X = conj(H): for each user tile kt the warp's F tile
   // (A operand, from shared memory, split here), then every antenna tile nt with
@@ -189,7 +200,7 @@ struct SolveTCW {
   // the warp's ft.  Returns sum |E|^2 over the lane's entries.
   __device__ __forceinline__ static float residual_f(const Lane& L, const float2* Hs, const float4* gf,
                                                      const float* tks, float eta, const WT& w,
-                                                     float4* ft) {
+                                                     float4* ft, const float2* St = nullptr) {
     float fa[KW][4];
 #pragma unroll
     for (int i = 0; i < KW; ++i)
@@ -200,7 +211,10 @@ struct SolveTCW {
     for (int ct = 0; ct < KW; ++ct) {
       float e[4];
       e_tile<false>(L, Hs, w, ct, e);
-      sub_s(L, tks, ct, e);
+      if (St)
+        sub_st(L, St, ct, e);
+      else
+        sub_s(L, tks, ct, e);
       ss += e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + e[3] * e[3];
       if constexpr (MODE == kModeProj) {
         uint32_t c0h, c0l, c1h, c1l, c2h, c2l, c3h, c3l;
@@ -483,6 +497,148 @@ struct SolveTCW {
     return fl;
   }
 
+  // FP64 path in an orthonormal basis of the channel's row space.  With
+  // G = H H^H = L D L^H (FP64; a pivot below 1e-12 of its Gram diagonal means
+  // rank(H) < K) the rows of U = D^{-1/2} L^{-1} H are orthonormal and span H's
+  // row space, and H W^T = S becomes U W^T = S~ with S~ = D^{-1/2} L^{-1} S.  The
+  // projection onto it is X - (X U^T - S~^T) conj(U): the layers' map with U in
+  // place of the channel, the identity in place of G^{-T} and S~^T in place of S.
+  // Rounding U to FP32 perturbs that orthogonal projector by O(u) at any
+  // conditioning, while G^{-T} rounded to FP32 perturbs the projector by
+  // O(u cond G), which the layers amplify once u cond G nears 1.  Writes U over
+  // the channel rows (in place, one thread per antenna column), S~^T into Es
+  // (natural [KB][KB]) and the identity's B fragments into gf.  Padded users
+  // (K <= k < KB) have zero channel rows and targets and get a unit pivot, so
+  // their rows of U and of S~ stay zero.  Returns the instance flags.
+  __device__ static int basis_fp64(const Lane& L, int K, float2* Hs, float2* Es, float4* gf,
+                                   double2* A, double* piv, double* ipv, double* orig,
+                                   const float* tks) {
+    for (int idx = L.tid; idx < KB * KB; idx += NT) {
+      const int i = idx / KB, j = idx % KB;
+      if (j > i) continue;
+      double sr = 0.0, si = 0.0;  // sum_m H_im conj(H_jm)
+      for (int m = 0; m < MB; ++m) {
+        const float2 x = Hs[i * RSF + m], y = Hs[j * RSF + m];
+        sr += (double)x.x * y.x + (double)x.y * y.y;
+        si += (double)x.y * y.x - (double)x.x * y.y;
+      }
+      A[i * KB + j] = make_double2(sr, si);
+    }
+    __syncthreads();
+    if (L.tid >= K && L.tid < KB) A[L.tid * KB + L.tid] = make_double2(1.0, 0.0);  // padded users
+    __syncthreads();
+    if (L.tid < KB) orig[L.tid] = A[L.tid * KB + L.tid].x;
+    __syncthreads();
+    int fl = PRECODE_F_FP64_CHOL;
+    bool singular = false;
+#pragma unroll 1
+    for (int p = 0; p < KB; ++p) {  // right-looking LDL^H on the lower triangle
+      const double d = A[p * KB + p].x;
+      if (!(d > 1e-12 * orig[p]) || !(d < DBL_MAX)) {
+        singular = true;
+        break;
+      }
+      const double inv = 1.0 / d;
+      const int R = KB - 1 - p;
+      for (int idx = L.tid; idx < R * R; idx += NT) {
+        const int i = p + 1 + idx / R, l = p + 1 + idx % R;
+        if (l > i) continue;
+        const double2 aip = A[i * KB + p], alp = A[l * KB + p];
+        const double ar = aip.x * inv, ai = aip.y * inv;
+        double2 v = A[i * KB + l];
+        v.x -= ar * alp.x + ai * alp.y;  // a conj(b)
+        v.y -= ai * alp.x - ar * alp.y;
+        A[i * KB + l] = v;
+      }
+      __syncthreads();
+    }
+    if (singular) {
+      for (int k = 0; k < KB; ++k)
+        if (!(orig[k] < DBL_MAX) || orig[k] != orig[k]) fl |= PRECODE_F_NONFINITE;
+      __syncthreads();
+      return fl | PRECODE_F_SINGULAR;
+    }
+    if (L.tid < KB) {
+      piv[L.tid] = A[L.tid * KB + L.tid].x;
+      ipv[L.tid] = 1.0 / A[L.tid * KB + L.tid].x;
+    }
+    __syncthreads();
+    // U by forward substitution L Y = H, column by column in FP64, then D^{-1/2}
+#pragma unroll 1
+    for (int m = L.tid; m < MB; m += NT) {
+      double yr[KB], yi[KB];
+#pragma unroll 1
+      for (int i = 0; i < KB; ++i) {
+        const float2 h = Hs[i * RSF + m];
+        double sr = h.x, si = h.y;
+#pragma unroll 1
+        for (int p = 0; p < i; ++p) {
+          const double2 a = A[i * KB + p];  // L[i][p] d_p
+          const double lr = a.x * ipv[p], li = a.y * ipv[p];
+          sr -= lr * yr[p] - li * yi[p];
+          si -= lr * yi[p] + li * yr[p];
+        }
+        yr[i] = sr;
+        yi[i] = si;
+      }
+#pragma unroll 1
+      for (int i = 0; i < KB; ++i) {
+        const double sc = 1.0 / sqrt(piv[i]);
+        Hs[i * RSF + m] = make_float2((float)(yr[i] * sc), (float)(yi[i] * sc));
+      }
+    }
+    // S~^T[k][i] = S~[i][k]: forward substitution of t_k e_k
+#pragma unroll 1
+    for (int k = L.tid; k < KB; k += NT) {
+      double yr[KB], yi[KB];
+#pragma unroll 1
+      for (int i = 0; i < KB; ++i) {
+        double sr = (i == k) ? (double)tks[k] : 0.0, si = 0.0;
+#pragma unroll 1
+        for (int p = k; p < i; ++p) {
+          const double2 a = A[i * KB + p];
+          const double lr = a.x * ipv[p], li = a.y * ipv[p];
+          sr -= lr * yr[p] - li * yi[p];
+          si -= lr * yi[p] + li * yr[p];
+        }
+        yr[i] = sr;
+        yi[i] = si;
+      }
+#pragma unroll 1
+      for (int i = 0; i < KB; ++i) {
+        const double sc = 1.0 / sqrt(piv[i]);
+        Es[k * KB + i] = i < k ? make_float2(0.f, 0.f)
+                               : make_float2((float)(yr[i] * sc), (float)(yi[i] * sc));
+      }
+    }
+    __syncthreads();  // the FP64 scratch is read out: the identity's fragments go over it
+    for (int idx = L.tid; idx < KW * KW * 32; idx += NT) {
+      const int kt = idx / (KW * 32), cp = (idx / 32) % KW, ln = idx % 32;
+      const int gg = ln >> 2, qq = ln & 3;
+      gf[idx] = make_float4(8 * kt + 2 * qq == 8 * cp + gg ? 1.f : 0.f,
+                            8 * kt + 2 * qq + 1 == 8 * cp + gg ? 1.f : 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    return fl;
+  }
+
+  // The instance's channel rows again from global memory (over U, after the
+  // layers of an instance solved in the orthonormal basis), each row times
+  // rs[k] when rs is given (a power of two: exact).
+  __device__ static void reload_channel(const Lane& L, int K, const float2* Hg, float2* Hs,
+                                        const float* rs = nullptr) {
+    for (int idx = L.tid; idx < K * (MB / 2); idx += NT) {
+      const int k = idx / (MB / 2), m2 = idx % (MB / 2);
+      float4 v = *reinterpret_cast<const float4*>(Hg + k * MB + 2 * m2);
+      if (rs) {
+        const float f = rs[k];
+        v = make_float4(f * v.x, f * v.y, f * v.z, f * v.w);
+      }
+      *reinterpret_cast<float4*>(Hs + k * RSF + 2 * m2) = v;
+    }
+    __syncthreads();
+  }
+
   // ---------------------------------------------------------------- kernel
   __device__ static void run(const SolveArgs& A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -535,7 +691,7 @@ struct SolveTCW {
     };
     // the channel's K rows, each to its padded shared-memory row
     auto issue_copy = [&](int64_t it) {
-      if (L.tid != 0 || it >= n_inst) return;
+      if (L.tid != 0 || it >= n_inst || (A.opts & OPT_STALL_COPY)) return;
       int64_t inst, h_off, w_off, t_off;
       int K;
       locate(it, inst, h_off, w_off, t_off, K);
@@ -551,13 +707,13 @@ struct SolveTCW {
       int K;
       locate(it, inst, h_off, w_off, t_off, K);
       if (L.tid < KB) tks[L.tid] = L.tid < K ? A.t[t_off + L.tid] : 0.f;
-      if (L.tid == 0) misc[0] = mbar_wait_bounded(bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (L.tid == 0) misc[0] = mbar_wait_bounded(bar, phase, copy_wait_ns(A)) ? 1 : 0;
       __syncthreads();
       if (misc[0] == 0) {
         if (L.tid == 0) {
           atomicAdd(A.err, 1ull);
           if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
-          misc[1] = mbar_wait_bounded(bar, phase, kCopyWaitNs) ? 1 : 0;
+          misc[1] = mbar_wait_bounded(bar, phase, copy_wait_ns(A)) ? 1 : 0;
         }
         __syncthreads();
         if (misc[1] == 0) return;
@@ -566,7 +722,7 @@ struct SolveTCW {
         issue_copy(it + gridDim.x);
         continue;
       }
-      if (L.tid != 0) mbar_wait_bounded(bar, phase, kCopyWaitNs);  // completed: returns at once
+      if (L.tid != 0) mbar_wait_bounded(bar, phase, copy_wait_ns(A));  // completed: returns at once
       phase ^= 1u;
       if (K < KB) {  // padded users: zero channel rows
         for (int idx = L.tid; idx < (KB - K) * MB; idx += NT)
@@ -592,23 +748,28 @@ struct SolveTCW {
           __syncthreads();
         }
       }
-      bool singular = false;
+      bool singular = false, basis = false;
       if constexpr (MODE == kModeProj) {
         if (!gj_fp32(L, Es, dsc, rowp, colp, A.cond_thr)) {
-          fl = gj_fp64(L, K, Hs, Es, A64, r64, c64, o64);
+          fl = basis_fp64(L, K, Hs, Es, gf, A64, reinterpret_cast<double*>(r64),
+                          reinterpret_cast<double*>(c64), o64, tks);
           singular = (fl & PRECODE_F_SINGULAR) != 0;
+          basis = !singular;
         }
         if (!singular) {
-          // G^{-T} as B fragments, then W^(0) = S G^{-T} conj(H) = 0 - F0 conj(H)
-          // with F0 = -S G^{-T} (the warp's rows)
-          for (int idx = L.tid; idx < KW * KW * 32; idx += NT) {
-            const int kt = idx / (KW * 32), cp = (idx / 32) % KW, ln = idx % 32;
-            const int gg = ln >> 2, qq = ln & 3;
-            const float2 m0 = Es[(8 * kt + 2 * qq) * KB + 8 * cp + gg];
-            const float2 m1 = Es[(8 * kt + 2 * qq + 1) * KB + 8 * cp + gg];
-            gf[idx] = make_float4(m0.x, m1.x, m0.y, m1.y);
+          // G^{-T} as B fragments (the basis path wrote the identity's), then
+          // W^(0) = S G^{-T} conj(H) = 0 - F0 conj(H) with F0 = -S G^{-T} (the warp's
+          // rows; S~^T conj(U) with F0 = -S~^T in the basis)
+          if (!basis) {
+            for (int idx = L.tid; idx < KW * KW * 32; idx += NT) {
+              const int kt = idx / (KW * 32), cp = (idx / 32) % KW, ln = idx % 32;
+              const int gg = ln >> 2, qq = ln & 3;
+              const float2 m0 = Es[(8 * kt + 2 * qq) * KB + 8 * cp + gg];
+              const float2 m1 = Es[(8 * kt + 2 * qq + 1) * KB + 8 * cp + gg];
+              gf[idx] = make_float4(m0.x, m1.x, m0.y, m1.y);
+            }
           }
-          const float tg = tks[8 * L.w + L.g];
+          const float tg = basis ? 1.f : tks[8 * L.w + L.g];
 #pragma unroll 1
           for (int kt = 0; kt < KW; ++kt) {
             const float4 v =
@@ -657,7 +818,7 @@ struct SolveTCW {
           if constexpr (MODE == kModeProj) {
             shrink(L, np, fb, par, fmaxf(__ldg(A.step + l), 0.f), w);
             par ^= 1;
-            residual_f(L, Hs, gf, tks, 1.f, w, ft);
+            residual_f(L, Hs, gf, tks, 1.f, w, ft, basis ? Es : nullptr);
             update(L, Hs, ft, w);
           } else {
             const float eta = __ldg(A.step + l) * invL;
@@ -668,6 +829,10 @@ struct SolveTCW {
           }
         }
         if (A.resid) {
+          if (basis) {  // against the channel itself
+            __syncthreads();
+            reload_channel(L, K, A.H + h_off, Hs);
+          }
           rss = residual_ss(L, Hs, tks, w);
 #pragma unroll
           for (int msk = 1; msk < 32; msk <<= 1) rss += __shfl_xor_sync(FULL, rss, msk);

@@ -354,7 +354,7 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
       }
     };
     auto issue_copy = [&](int64_t it) {
-      if (L.tid != 0 || it >= n_inst) return;
+      if (L.tid != 0 || it >= n_inst || (A.opts & OPT_STALL_COPY)) return;
       int64_t inst, h_off, w_off, t_off;
       int K;
       locate(it, inst, h_off, w_off, t_off, K);
@@ -370,13 +370,13 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
       int K;
       locate(it, inst, h_off, w_off, t_off, K);
       if (L.tid < KB) tks[L.tid] = L.tid < K ? A.t[t_off + L.tid] : 0.f;
-      if (L.tid == 0) misc[0] = mbar_wait_bounded(bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (L.tid == 0) misc[0] = mbar_wait_bounded(bar, phase, copy_wait_ns(A)) ? 1 : 0;
       __syncthreads();
       if (misc[0] == 0) {
         if (L.tid == 0) {
           atomicAdd(A.err, 1ull);
           if (A.flags) A.flags[inst] = PRECODE_F_TIMEOUT;
-          misc[1] = mbar_wait_bounded(bar, phase, kCopyWaitNs) ? 1 : 0;
+          misc[1] = mbar_wait_bounded(bar, phase, copy_wait_ns(A)) ? 1 : 0;
         }
         __syncthreads();
         if (misc[1] == 0) return;
@@ -385,7 +385,7 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
         issue_copy(it + gridDim.x);
         continue;
       }
-      if (L.tid != 0) mbar_wait_bounded(bar, phase, kCopyWaitNs);  // completed: returns at once
+      if (L.tid != 0) mbar_wait_bounded(bar, phase, copy_wait_ns(A));  // completed: returns at once
       phase ^= 1u;
       if (K < KB) {  // padded users: zero channel rows
         for (int idx = L.tid; idx < (KB - K) * MB; idx += NT)
@@ -432,20 +432,26 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
         if (L.tid >= K && L.tid < KB) Es[L.tid * KB + L.tid] = make_float2(1.f, 0.f);
         __syncthreads();
       }
-      bool singular = false;
+      bool singular = false, basis = false;
       if (!S::gj_fp32(L, Es, dsc, rowp, colp, A.cond_thr)) {
-        fl = S::gj_fp64(L, K, Hs, Es, A64, r64, c64, o64);
+        // FP64 path: the layers run split TF32 in an orthonormal basis of the
+        // (scaled) channel's row space, S~^T in Es (S::basis_fp64)
+        fl = S::basis_fp64(L, K, Hs, Es, gf, A64, reinterpret_cast<double*>(r64),
+                           reinterpret_cast<double*>(c64), o64, tks);
         singular = (fl & PRECODE_F_SINGULAR) != 0;
+        basis = !singular;
       }
       if (!singular) {
-        for (int idx = L.tid; idx < KW * KW * 32; idx += NT) {
-          const int kt = idx / (KW * 32), cp = (idx / 32) % KW, ln = idx % 32;
-          const int gg = ln >> 2, qq = ln & 3;
-          const float2 m0 = Es[(8 * kt + 2 * qq) * KB + 8 * cp + gg];
-          const float2 m1 = Es[(8 * kt + 2 * qq + 1) * KB + 8 * cp + gg];
-          gf[idx] = make_float4(m0.x, m1.x, m0.y, m1.y);
+        if (!basis) {
+          for (int idx = L.tid; idx < KW * KW * 32; idx += NT) {
+            const int kt = idx / (KW * 32), cp = (idx / 32) % KW, ln = idx % 32;
+            const int gg = ln >> 2, qq = ln & 3;
+            const float2 m0 = Es[(8 * kt + 2 * qq) * KB + 8 * cp + gg];
+            const float2 m1 = Es[(8 * kt + 2 * qq + 1) * KB + 8 * cp + gg];
+            gf[idx] = make_float4(m0.x, m1.x, m0.y, m1.y);
+          }
         }
-        const float tg = tks[8 * L.w + L.g];
+        const float tg = basis ? 1.f : tks[8 * L.w + L.g];
 #pragma unroll 1
         for (int kt = 0; kt < KW; ++kt) {
           const float4 v =
@@ -459,6 +465,7 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
           for (int k = 0; k < 4; ++k) w[s][k] = 0.f;
         S::update(L, Hs, ft, w);  // W^(0)' = S' G'^{-T} conj(H') (split TF32)
       }
+      // with the basis, the global scale b scales W^(0)' and S~^T alike (below)
       // ---- the global scale b: max(|W^(0)'|, t') into [8, 16)
       float wm = fabsf(tks[L.lane % KB]);
 #pragma unroll
@@ -479,6 +486,11 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
         for (int k = 0; k < 4; ++k) w[s][k] *= beta;
       __syncthreads();  // every t', wred and raw-channel read done
       if (L.tid < KB) tks[L.tid] *= beta;
+      if (basis)
+        for (int idx = L.tid; idx < KB * KB; idx += NT) {
+          const float2 v = Es[idx];
+          Es[idx] = make_float2(beta * v.x, beta * v.y);
+        }
       const bool tf32_layers = (fl & PRECODE_F_FP64_CHOL) != 0;
       if (!tf32_layers && !singular) to_chunks(L, Hs);
       __syncthreads();
@@ -492,7 +504,7 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
           S::shrink(L, np, fb, par, fmaxf(__ldg(A.step + l), 0.f) * beta, w);
           par ^= 1;
           if (tf32_layers) {
-            S::residual_f(L, Hs, gf, tks, 1.f, w, ft);
+            S::residual_f(L, Hs, gf, tks, 1.f, w, ft, basis ? Es : nullptr);
             S::update(L, Hs, ft, w);
             continue;
           }
@@ -505,6 +517,12 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
             update_c_tf32(L, Hs, ft, w);
         }
         if (A.resid) {
+          if (basis) {  // against the channel itself, scaled per user again (H' = D H)
+            __syncthreads();
+            if (L.tid < KB) dsc[L.tid] = 1.f / dinv[L.tid];
+            __syncthreads();
+            S::reload_channel(L, K, A.H + h_off, Hs, dsc);
+          }
           rss = tf32_layers ? residual_ssh<true>(L, Hs, tks, dinv, w)
                             : residual_ssh<false>(L, Hs, tks, dinv, w);
 #pragma unroll

@@ -91,11 +91,13 @@ int train_occupancy(const TrainVariant& v, int device) {
 
 using namespace precode;
 
-extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int32_t K, int64_t B,
-                                               const void* H, const float* t, int64_t t_stride,
-                                               const float* step, const float* lam, float a,
-                                               float* loss, float* dstep, float* dlam,
-                                               int32_t* flags, precode_stream_t stream) {
+// Forward + adjoint launch and batch reductions shared by the unsupervised
+// (wgt == nullptr, weight a) and the supervised (labels wgt) train steps.
+static precode_status_t train_step_impl(precode_plan_t p, int32_t M, int32_t K, int64_t B,
+                                        const void* H, const float* t, int64_t t_stride,
+                                        const float* step, const float* lam, float a,
+                                        const void* wgt, float* loss, float* dstep, float* dlam,
+                                        int32_t* flags, precode_stream_t stream) {
   if (!p) return fail(PRECODE_EINVAL, "precode_train_step: NULL plan");
   if (B < 1 || B > p->max_instances)
     return fail(PRECODE_EINVAL, "precode_train_step: B outside [1, max_instances]");
@@ -105,6 +107,8 @@ extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int3
   if (p->mode == PRECODE_LAYER_PGD && (!lam || !dlam))
     return fail(PRECODE_EINVAL, "precode_train_step: lam and dlam required for the paper layer");
   if ((uintptr_t)H & 15) return fail(PRECODE_EINVAL, "precode_train_step: H must be 16-byte aligned");
+  if ((uintptr_t)wgt & 15)
+    return fail(PRECODE_EINVAL, "precode_train_step_supervised: W_gt must be 16-byte aligned");
   if (t_stride != 0 && t_stride < K) return fail(PRECODE_EINVAL, "precode_train_step: t_stride < K");
   const TrainVariant* v = pick_train(p->mode, M, K, (p->flags & PRECODE_PLAN_TENSOR_CORES) != 0);
   if (!v) return fail(PRECODE_EINVAL, "precode_train_step: no train kernel holds the shape");
@@ -119,7 +123,7 @@ extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int3
     cudaFree(p->d_cp);
     p->d_cp = nullptr;
     p->cp_bytes = 0;
-    if (cudaMalloc(&p->d_cp, cp_need) != cudaSuccess)
+    if (dev_alloc(&p->d_cp, cp_need) != cudaSuccess)
       return fail(PRECODE_ENOMEM, "precode_train_step: checkpoint workspace");
     p->cp_bytes = cp_need;
   }
@@ -127,7 +131,7 @@ extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int3
     cudaFree(p->d_part);
     p->d_part = nullptr;
     p->part_bytes = 0;
-    if (cudaMalloc(&p->d_part, part_need) != cudaSuccess)
+    if (dev_alloc(&p->d_part, part_need) != cudaSuccess)
       return fail(PRECODE_ENOMEM, "precode_train_step: gradient workspace");
     p->part_bytes = part_need;
   }
@@ -145,9 +149,11 @@ extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int3
   A.s.M = M;
   A.s.T = T;
   A.s.cond_thr = p->cond_thr;
-  A.s.opts = (p->flags & PRECODE_PLAN_STEP_NORMALISED) ? OPT_STEP_NORMALISED : 0u;
+  A.s.opts = p->kernel_opts();
+  A.s.wait_ns = p->wait_ns;
   A.s.err = p->d_err;
   A.a = a;
+  A.wgt = static_cast<const float2*>(wgt);
   A.cp = p->d_cp;
   A.cp_every = cpe;
   A.ncp = ncp;
@@ -166,4 +172,22 @@ extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int3
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "precode_train_step: batch reduction launch");
   return PRECODE_OK;
+}
+
+extern "C" precode_status_t precode_train_step(precode_plan_t p, int32_t M, int32_t K, int64_t B,
+                                               const void* H, const float* t, int64_t t_stride,
+                                               const float* step, const float* lam, float a,
+                                               float* loss, float* dstep, float* dlam,
+                                               int32_t* flags, precode_stream_t stream) {
+  return train_step_impl(p, M, K, B, H, t, t_stride, step, lam, a, nullptr, loss, dstep, dlam,
+                         flags, stream);
+}
+
+extern "C" precode_status_t precode_train_step_supervised(
+    precode_plan_t p, int32_t M, int32_t K, int64_t B, const void* H, const float* t,
+    int64_t t_stride, const void* W_gt, const float* step, const float* lam, float* loss,
+    float* dstep, float* dlam, int32_t* flags, precode_stream_t stream) {
+  if (!W_gt) return fail(PRECODE_EINVAL, "precode_train_step_supervised: NULL W_gt");
+  return train_step_impl(p, M, K, B, H, t, t_stride, step, lam, 0.f, W_gt, loss, dstep, dlam,
+                         flags, stream);
 }

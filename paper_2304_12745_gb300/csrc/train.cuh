@@ -1,10 +1,12 @@
 // Forward + reverse (adjoint) pass of T unfolded layers per instance, for
-// learning the per-layer parameters (Sec. V, learning rule and unsupervised
-// cost).  Loss per instance:  a ||W_T||_{2,1} + ||H W_T^T - S||_F^2.
+// learning the per-layer parameters (Sec. V, learning rule).  Loss per instance:
+// the unsupervised cost  a ||W_T||_{2,1} + ||H W_T^T - S||_F^2, or with labels
+// (TrainArgs::wgt) the supervised cost  ||W_T - W_gt||_F^2.
 //
 // Gradients are taken w.r.t. real parameters; a complex gradient g stands for
 // dloss/dRe(W) + i dloss/dIm(W) with <A, B> = Re sum conj(A) B.  Reverse rules:
 //   output:     g = a w_m/||w_m|| (non-zero columns) + 2 (W H^T - S) H^*
+//               (supervised: g = 2 (W - W_gt))
 //   projection: W = X - (X H^T - S) Q has the self-adjoint linear part
 //               X -> X - (X H^T) Q, so g <- g - (g H^T) Q
 //   paper step: V = W - eta (W H^T - S) H^* has the self-adjoint linear part
@@ -24,7 +26,8 @@ namespace precode {
 
 struct TrainArgs {
   SolveArgs s;      // H, t, t_stride, step, lam, B, K, M, T, cond_thr, opts, err, flags
-  float a;          // weight of ||W_T||_{2,1} in the loss
+  float a;          // weight of ||W_T||_{2,1} in the unsupervised loss
+  const float2* wgt;  // supervised loss: labels W_gt [B][K][M] (W's layout), else nullptr
   float2* cp;       // checkpoints [B][ncp][KB*MB] (bucket-sized slots)
   int cp_every;     // checkpoint interval c
   int ncp;          // checkpoints per instance = ceil(T / c)
@@ -252,20 +255,20 @@ struct TrainKernel : SolveKernel<MODE, KB, MB, GK, GM, JC_, EXACT, NW, true, fal
       float* part = A.part + inst * PW;
 
       gsync_all(c);
-      if (c.g == 0) {
+      if (c.g == 0 && !(A.s.opts & OPT_STALL_COPY)) {
         fence_proxy_async_smem();
         const uint32_t bytes = (uint32_t)(K * M) * 8u;
         mbar_arrive_expect_tx(c.bar, bytes);
         bulk_g2s(c.Hs, A.s.H + h_off, bytes, c.bar);
       }
       if (c.g < K) c.tks[c.g] = A.s.t[t_off + c.g];
-      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s)) ? 1 : 0;
       Base::gsync(c);
       if (c.misc[0] == 0) {
         if (c.g == 0) {
           atomicAdd(A.s.err, 1ull);
           if (A.s.flags) A.s.flags[inst] = PRECODE_F_TIMEOUT;
-          c.misc[1] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+          c.misc[1] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s)) ? 1 : 0;
         }
         Base::gsync(c);
         for (int j = c.g; j < PW; j += TPI) part[j] = 0.f;
@@ -273,7 +276,7 @@ struct TrainKernel : SolveKernel<MODE, KB, MB, GK, GM, JC_, EXACT, NW, true, fal
         phase ^= 1;
         continue;
       }
-      if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);
+      if (c.g != 0) mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s));
       phase ^= 1;
 
       // ---- setup: W^(0)
@@ -292,9 +295,17 @@ struct TrainKernel : SolveKernel<MODE, KB, MB, GK, GM, JC_, EXACT, NW, true, fal
           invL = Base::inv_gershgorin(c);
         }
       }
-      if (fl & PRECODE_F_SINGULAR) {
+      if (fl & PRECODE_F_SINGULAR) {  // W_T = 0: ||S||_F^2, or ||W_gt||_F^2 with labels
         float s2 = 0.f;
-        for (int k = 0; k < K; ++k) s2 += c.tks[k] * c.tks[k];
+        if (A.wgt) {
+          for (int idx = c.g; idx < K * M; idx += TPI) {
+            const float2 lb = A.wgt[h_off + idx];
+            s2 += lb.x * lb.x + lb.y * lb.y;
+          }
+          s2 = group_sum(c, s2);
+        } else {
+          for (int k = 0; k < K; ++k) s2 += c.tks[k] * c.tks[k];
+        }
         for (int j = c.g; j < PW; j += TPI) part[j] = (j == 0) ? s2 : 0.f;
         if (c.g == 0 && A.s.flags) A.s.flags[inst] = fl;
         continue;
@@ -308,6 +319,27 @@ struct TrainKernel : SolveKernel<MODE, KB, MB, GK, GM, JC_, EXACT, NW, true, fal
       }
 
       // ---- loss and its gradient at W_T
+      if (A.wgt) {  // supervised: ||W_T - W_gt||_F^2, g = 2 (W_T - W_gt)
+        float s2 = 0.f;
+#pragma unroll
+        for (int u = 0; u < UPT; ++u)
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            float4 lb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (Base::uok(c, u) && Base::pok(c, i))
+              lb = *reinterpret_cast<const float4*>(A.wgt + h_off + (int64_t)Base::user(c, u) * M +
+                                                   2 * Base::pair(c, i));
+            else
+              lb = make_float4(w[u][2 * i].x, w[u][2 * i].y, w[u][2 * i + 1].x, w[u][2 * i + 1].y);
+            const float d0 = w[u][2 * i].x - lb.x, d1 = w[u][2 * i].y - lb.y;
+            const float d2 = w[u][2 * i + 1].x - lb.z, d3 = w[u][2 * i + 1].y - lb.w;
+            s2 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            g[u][2 * i] = mkc<CT>(2.f * d0, 2.f * d1);
+            g[u][2 * i + 1] = mkc<CT>(2.f * d2, 2.f * d3);
+          }
+        const float lsum = group_sum(c, s2);
+        if (c.g == 0) part[0] = lsum;
+      } else {
       Base::colnorm2(c, w, r2);
       float o = 0.f;
 #pragma unroll
@@ -330,6 +362,7 @@ struct TrainKernel : SolveKernel<MODE, KB, MB, GK, GM, JC_, EXACT, NW, true, fal
         }
       }
       if (c.g == 0) part[0] = A.a * o + rs;
+      }
 
       // ---- reverse: layer l = T-1 .. 0, recomputing its input from a checkpoint
 #pragma unroll 1

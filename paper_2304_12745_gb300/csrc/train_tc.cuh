@@ -73,6 +73,41 @@ struct TrainTC {
     return *reinterpret_cast<const float4*>(fb + L.q * 16 + 4 * (j ^ (L.q & 2)));
   }
 
+  // Supervised loss of the lane's entries and its gradient, in original units:
+  // W_T = f w (f: the output factor of the units w is held in), labels lb at
+  // [K][M] (row g, antennas 8s + 2q + {0, 1}); g = 2 (W_T - W_gt).  Returns the
+  // instance's ||W_T - W_gt||_F^2 (warp sum).
+  __device__ __forceinline__ static float sup_loss_grad(const Lane& L, const float2* lb, float f,
+                                                        const WT& w, WT& g) {
+    float s2 = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float4 v = *reinterpret_cast<const float4*>(lb + L.g * MB + 8 * s + 2 * L.q);
+      const float d0 = f * w[s][0] - v.x, d1 = f * w[s][1] - v.z;
+      const float d2 = f * w[s][2] - v.y, d3 = f * w[s][3] - v.w;
+      s2 += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+      g[s][0] = 2.f * d0;
+      g[s][1] = 2.f * d1;
+      g[s][2] = 2.f * d2;
+      g[s][3] = 2.f * d3;
+    }
+#pragma unroll
+    for (int msk = 1; msk < 32; msk <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, msk);
+    return s2;
+  }
+  // ||W_gt||_F^2 of one instance's labels (warp sum).
+  __device__ __forceinline__ static float sup_loss_zero(const Lane& L, const float2* lb) {
+    float s2 = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float4 v = *reinterpret_cast<const float4*>(lb + L.g * MB + 8 * s + 2 * L.q);
+      s2 += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+    }
+#pragma unroll
+    for (int msk = 1; msk < 32; msk <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, msk);
+    return s2;
+  }
+
   // g <- d loss / d v through the group shrink with threshold tau at input v;
   // returns d loss / d tau
   __device__ __forceinline__ static float shrink_back(const Lane& L, float* nb, float* fb, float* fb2,
@@ -205,7 +240,7 @@ struct TrainTC {
     const int64_t n_inst = A.s.B;
     const int64_t stride = (int64_t)gridDim.x * NW;
     auto issue_copy = [&](int64_t it) {
-      if (c.g != 0 || it >= n_inst) return;
+      if (c.g != 0 || it >= n_inst || (A.s.opts & OPT_STALL_COPY)) return;
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(c.bar, KB * MB * 8);
       bulk_g2s(c.Hs, A.s.H + it * (int64_t)(KB * MB), KB * MB * 8, c.bar);
@@ -218,13 +253,13 @@ struct TrainTC {
       float* const part = A.part + inst * PW;
       __syncwarp();
       if (c.g < KB) c.tks[c.g] = A.s.t[inst * A.s.t_stride + c.g];
-      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s)) ? 1 : 0;
       __syncwarp();
       if (c.misc[0] == 0) {
         if (c.g == 0) {
           atomicAdd(A.s.err, 1ull);
           if (A.s.flags) A.s.flags[inst] = PRECODE_F_TIMEOUT;
-          c.misc[1] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+          c.misc[1] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s)) ? 1 : 0;
         }
         __syncwarp();
         if (c.misc[1] == 0) return;
@@ -233,15 +268,19 @@ struct TrainTC {
         issue_copy(inst + stride);
         continue;
       }
-      if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);
+      if (c.g != 0) mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s));
       phase ^= 1u;
 
       float invL;
       const int fl = S::setup(c, L, A.s, xf, hlo, w, invL, xr);
       __syncwarp();
-      if (fl & PRECODE_F_SINGULAR) {
+      if (fl & PRECODE_F_SINGULAR) {  // W_T = 0: ||S||_F^2, or ||W_gt||_F^2 with labels
         float s2 = 0.f;
-        for (int k = 0; k < KB; ++k) s2 += c.tks[k] * c.tks[k];
+        if (A.wgt) {
+          s2 = sup_loss_zero(L, A.wgt + inst * (int64_t)(KB * MB));
+        } else {
+          for (int k = 0; k < KB; ++k) s2 += c.tks[k] * c.tks[k];
+        }
         for (int j = c.g; j < PW; j += 32) part[j] = (j == 0) ? s2 : 0.f;
         if (c.g == 0 && A.s.flags) A.s.flags[inst] = fl;
         __syncwarp();
@@ -274,7 +313,10 @@ struct TrainTC {
 
       // ---- loss and its gradient at W_T
       float o, rs, e[4];
-      {
+      if (A.wgt) {  // supervised: ||W_T - W_gt||_F^2, g = 2 (W_T - W_gt)
+        const float ls = sup_loss_grad(L, A.wgt + inst * (int64_t)(KB * MB), 1.f, w, g);
+        if (c.g == 0) part[0] = ls;
+      } else {
         const float2 r2 = S::colsum(L, nb, w);
         o = sqrtf(r2.x) + sqrtf(r2.y);
 #pragma unroll
@@ -304,8 +346,8 @@ struct TrainTC {
           update_raw(L, xr, e, g);  // g += 2 E_T H^*
         else
           S::update(L, xf, e, g);
+        if (c.g == 0) part[0] = A.a * o + rs;
       }
-      if (c.g == 0) part[0] = A.a * o + rs;
 
       // ---- reverse: layer l = T-1 .. 0, recomputing its input from a checkpoint
 #pragma unroll 1

@@ -10,7 +10,8 @@
 //   shrink      g' <- (1 - tau'/r') g' + (tau'/r'^3) Re(v'^H g') v'  (scale-free)
 //               d tau' = -sum_active Re(v'^H g') / r'  =  s dL/dmu
 // The loss and its gradient at W_T are formed in original units in FP32 (the
-// gradient's 2 E_T H^* with split-TF32 MMAs on the unscaled conj(H)).  W_l is
+// gradient's 2 E_T H^* with split-TF32 MMAs on the unscaled conj(H); with labels,
+// the supervised 2 (W_T - W_gt)).  W_l is
 // kept (scaled) at every c-th layer in global memory and the reverse pass
 // recomputes the layers in between.
 #pragma once
@@ -94,7 +95,7 @@ struct TrainTCH {
     const int64_t n_inst = A.s.B;
     const int64_t stride = (int64_t)gridDim.x * NW;
     auto issue_copy = [&](int64_t it) {
-      if (c.g != 0 || it >= n_inst) return;
+      if (c.g != 0 || it >= n_inst || (A.s.opts & OPT_STALL_COPY)) return;
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(c.bar, KB * MB * 8);
       bulk_g2s(c.Hs, A.s.H + it * (int64_t)(KB * MB), KB * MB * 8, c.bar);
@@ -107,13 +108,13 @@ struct TrainTCH {
       float* const part = A.part + inst * PW;
       __syncwarp();
       if (c.g < KB) c.tks[c.g] = A.s.t[inst * A.s.t_stride + c.g];
-      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (c.g == 0) c.misc[0] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s)) ? 1 : 0;
       __syncwarp();
       if (c.misc[0] == 0) {
         if (c.g == 0) {
           atomicAdd(A.s.err, 1ull);
           if (A.s.flags) A.s.flags[inst] = PRECODE_F_TIMEOUT;
-          c.misc[1] = mbar_wait_bounded(c.bar, phase, kCopyWaitNs) ? 1 : 0;
+          c.misc[1] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s)) ? 1 : 0;
         }
         __syncwarp();
         if (c.misc[1] == 0) return;
@@ -122,16 +123,20 @@ struct TrainTCH {
         issue_copy(inst + stride);
         continue;
       }
-      if (c.g != 0) mbar_wait_bounded(c.bar, phase, kCopyWaitNs);
+      if (c.g != 0) mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s));
       phase ^= 1u;
 
       float beta;
       const int fl = SH::setup(c, L, A.s, xf, w, beta, xr);
       __syncwarp();
-      if (fl & PRECODE_F_SINGULAR) {  // t' = b d t: back to ||t||^2
+      if (fl & PRECODE_F_SINGULAR) {  // t' = b d t: back to ||t||^2 (||W_gt||^2 with labels)
         float s2 = 0.f;
-        for (int k = 0; k < KB; ++k) s2 += (c.tks[k] * c.dsc[k]) * (c.tks[k] * c.dsc[k]);
-        s2 /= beta * beta;
+        if (A.wgt) {
+          s2 = TT::sup_loss_zero(L, A.wgt + inst * (int64_t)(KB * MB));
+        } else {
+          for (int k = 0; k < KB; ++k) s2 += (c.tks[k] * c.dsc[k]) * (c.tks[k] * c.dsc[k]);
+          s2 /= beta * beta;
+        }
         for (int j = c.g; j < PW; j += 32) part[j] = (j == 0) ? s2 : 0.f;
         if (c.g == 0 && A.s.flags) A.s.flags[inst] = fl;
         __syncwarp();
@@ -165,7 +170,10 @@ struct TrainTCH {
       // ---- loss and its gradient at W_T, in original units
       const float ib = 1.f / beta;
       float o, rs, e[4];
-      {
+      if (A.wgt) {  // supervised: ||W_T - W_gt||_F^2, g = 2 (W_T - W_gt), W_T = w / b
+        const float ls = TT::sup_loss_grad(L, A.wgt + inst * (int64_t)(KB * MB), ib, w, g);
+        if (c.g == 0) part[0] = ls;
+      } else {
         const float2 r2 = S::colsum(L, nb, w);
         o = sqrtf(r2.x) + sqrtf(r2.y);
 #pragma unroll
@@ -202,8 +210,8 @@ struct TrainTCH {
 #pragma unroll
         for (int k = 0; k < 4; ++k) e[k] *= -2.f;
         TT::update_raw(L, xr, e, g);  // g += 2 E_T H^*
+        if (c.g == 0) part[0] = A.a * o + rs;
       }
-      if (c.g == 0) part[0] = A.a * o + rs;
       // g' = s g with max |g'| in [8, 16)
       float gm = 0.f;
 #pragma unroll

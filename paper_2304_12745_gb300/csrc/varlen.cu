@@ -71,8 +71,8 @@ struct VarlenCall {
 precode_status_t ensure_workspace(precode_plan_t p) {
   if (p->d_index) return PRECODE_OK;
   const size_t nb = p->buckets.size();
-  if (cudaMalloc(&p->d_index, sizeof(int32_t) * nb * (size_t)p->max_instances) != cudaSuccess ||
-      cudaMalloc(&p->d_count, sizeof(int32_t) * nb) != cudaSuccess) {
+  if (dev_alloc(&p->d_index, sizeof(int32_t) * nb * (size_t)p->max_instances) != cudaSuccess ||
+      dev_alloc(&p->d_count, sizeof(int32_t) * nb) != cudaSuccess) {
     cudaFree(p->d_index);
     p->d_index = nullptr;
     return fail(PRECODE_ENOMEM, "precode_solve_varlen: bucket workspace");
@@ -119,7 +119,8 @@ void fill_args(precode_plan_t p, VarlenCall& call, const precode_inst_t* tbl, in
     A.M = p->buckets[i].M;
     A.T = p->T;
     A.cond_thr = p->cond_thr;
-    A.opts = (p->flags & PRECODE_PLAN_STEP_NORMALISED) ? OPT_STEP_NORMALISED : 0u;
+    A.opts = p->kernel_opts();
+    A.wait_ns = p->wait_ns;
     A.tbl = call.tbl;
     A.index = p->d_index + (size_t)i * p->max_instances;
     A.count = p->d_count + i;

@@ -112,9 +112,10 @@ extern "C" precode_status_t precode_solve_varlen_static(
     return fail(PRECODE_EINVAL, "precode_solve_varlen_static: unknown layer mode");
   if (d->T < 1 || d->T > PRECODE_MAX_T)
     return fail(PRECODE_EINVAL, "precode_solve_varlen_static: T out of range");
-  if (d->flags & (PRECODE_PLAN_AUTOTUNE | PRECODE_PLAN_GRAPHS))
+  if (d->flags & (PRECODE_PLAN_AUTOTUNE | PRECODE_PLAN_GRAPHS | PRECODE_PLAN_TENSOR_CORES))
     return fail(PRECODE_EINVAL,
-                "precode_solve_varlen_static: autotuning and graphs need a plan (precode_plan)");
+                "precode_solve_varlen_static: autotuning, graphs and tensor-core buckets need a "
+                "plan (precode_plan)");
   if ((d->flags & PRECODE_PLAN_STEP_NORMALISED) && d->mode != PRECODE_LAYER_PGD)
     return fail(PRECODE_EINVAL, "precode_solve_varlen_static: step normalisation is PGD-only");
   if (B < 0 || B > kMaxInst)
@@ -206,7 +207,7 @@ extern "C" precode_status_t precode_solve_varlen_static(
     A.K = bt.K[i];
     A.M = bt.M[i];
     A.T = d->T;
-    A.cond_thr = d->cond_threshold > 0 ? (float)d->cond_threshold : 1e3f;
+    A.cond_thr = d->cond_threshold > 0 ? (float)d->cond_threshold : kDefaultCondThreshold;
     A.opts = (d->flags & PRECODE_PLAN_STEP_NORMALISED) ? OPT_STEP_NORMALISED : 0u;
     A.tbl = reinterpret_cast<const InstDesc*>(tbl);
     A.index = scratch + (int64_t)i * kMaxInst;

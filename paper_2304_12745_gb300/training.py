@@ -12,7 +12,8 @@ parameter projections after every step:
 
 The unsupervised cost is a ||W_T||_{2,1} + ||H W_T^T - S||_F^2 averaged over the
 batch (a = lambda in the paper's cost; the PA-consumption weight for the
-projected layer).
+projected layer).  The supervised cost (labels given) is the MSE
+||W_T - W_gt||_F^2 to ground-truth precoders, averaged over the batch.
 """
 from __future__ import annotations
 
@@ -26,16 +27,22 @@ from .precoder import Plan, _stream_handle
 
 class PrecodeLoss(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, step, lam, plan, H, t, a, group=None):
+    def forward(ctx, step, lam, plan, H, t, a, group=None, labels=None):
         B, K, M = H.shape
         dev = H.device
         loss = torch.empty(1, device=dev)
         dstep = torch.empty_like(step)
         dlam = torch.empty_like(step) if lam is not None else None
         t_stride = 0 if t.dim() == 1 else K
-        capi.precode_train_step(plan.handle, M, K, B, H, t, t_stride, step.detach().contiguous(),
-                                None if lam is None else lam.detach().contiguous(), a, loss,
-                                dstep, dlam, None, _stream_handle(None))
+        lm = None if lam is None else lam.detach().contiguous()
+        if labels is None:
+            capi.precode_train_step(plan.handle, M, K, B, H, t, t_stride, step.detach().contiguous(),
+                                    lm, a, loss, dstep, dlam, None, _stream_handle(None))
+        else:
+            assert labels.shape == H.shape and labels.dtype == torch.complex64 and labels.is_cuda
+            capi.precode_train_step_supervised(plan.handle, M, K, B, H, t, t_stride,
+                                               labels.contiguous(), step.detach().contiguous(), lm,
+                                               loss, dstep, dlam, None, _stream_handle(None))
         if group is not None:  # data-parallel ranks: global batch mean (2T + 2 numbers)
             from .sharding import allreduce_mean
             loss, dstep, dlam = allreduce_mean(loss, dstep, dlam, B, group)
@@ -46,7 +53,7 @@ class PrecodeLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         dstep, dlam = ctx.saved_tensors
-        return g * dstep, (g * dlam if ctx.has_lam else None), None, None, None, None, None
+        return g * dstep, (g * dlam if ctx.has_lam else None), None, None, None, None, None, None
 
 
 def mp_bound(K: int, M: int) -> float:
@@ -106,30 +113,33 @@ class UnfoldedTrainer:
             else:
                 self.step.clamp_(min=0.0)
 
-    def loss(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
-        return PrecodeLoss.apply(self.step, self.lam, self.plan, H, t, self.a, self.group)
+    def loss(self, H: torch.Tensor, t: torch.Tensor, labels=None) -> torch.Tensor:
+        return PrecodeLoss.apply(self.step, self.lam, self.plan, H, t, self.a, self.group, labels)
 
-    def train_step(self, H: torch.Tensor, t: torch.Tensor, sync: bool = True):
+    def train_step(self, H: torch.Tensor, t: torch.Tensor, sync: bool = True, labels=None):
         """One Adam step on batch (H, t).  Returns the batch loss as a float, or
         with sync=False as a device tensor (no host synchronisation, so steps
-        queue back to back on the stream)."""
+        queue back to back on the stream).  `labels` (complex64 [B, K, M] on the
+        device): ground-truth precoders for the supervised cost instead of the
+        unsupervised one."""
         if self.graphs:
-            loss = self._graphed_step(H, t)
+            loss = self._graphed_step(H, t, labels)
         else:
-            loss = self._eager_step(H, t)
+            loss = self._eager_step(H, t, labels)
         self.steps_done += 1
         return float(loss) if sync else loss
 
-    def _eager_step(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+    def _eager_step(self, H: torch.Tensor, t: torch.Tensor, labels=None) -> torch.Tensor:
         self.opt.zero_grad(set_to_none=True)
-        loss = self.loss(H, t)
+        loss = self.loss(H, t, labels)
         loss.backward()
         self.opt.step()
         self.project()
         return loss.detach()
 
-    def _graphed_step(self, H: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
-        key = (H.data_ptr(), tuple(H.shape), t.data_ptr(), tuple(t.shape))
+    def _graphed_step(self, H: torch.Tensor, t: torch.Tensor, labels=None) -> torch.Tensor:
+        key = (H.data_ptr(), tuple(H.shape), t.data_ptr(), tuple(t.shape),
+               None if labels is None else labels.data_ptr())
         entry = self._graphs.get(key)
         if entry is not None:
             graph, loss = entry
@@ -141,14 +151,14 @@ class UnfoldedTrainer:
         # MAX_GRAPHS batches keep a graph (the oldest is dropped): a caller that
         # brings a new tensor every step gets eager steps plus a capture each time,
         # so graphs pay off only for batches that stay resident.
-        loss = self._eager_step(H, t)
+        loss = self._eager_step(H, t, labels)
         if len(self._graphs) >= self.MAX_GRAPHS:
             self._graphs.pop(next(iter(self._graphs)))
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         self.opt.zero_grad(set_to_none=True)
         with torch.cuda.graph(graph):
-            static_loss = self.loss(H, t)
+            static_loss = self.loss(H, t, labels)
             static_loss.backward()
             self.opt.step()
             self.project()

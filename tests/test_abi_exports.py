@@ -129,6 +129,7 @@ int main(void) {
     if (precode_serve_destroy(NULL) != PRECODE_EINVAL) return 24;
     if (precode_plan_errors(NULL, &u) != PRECODE_EINVAL) return 25;
     if (precode_plan_describe(NULL, 64, 8, buf, sizeof buf) != PRECODE_EINVAL) return 26;
+    if (precode_plan_set_debug(NULL, 1000, 1) != PRECODE_EINVAL) return 27;
   }
   {
     pthread_t a, b;

@@ -133,11 +133,11 @@ def test_proj_generic_buckets(pc, orc, K, M):
     mu = np.full(6, 0.05, np.float32)
     gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu)
     ref = oracle_ref(orc, 1, H, t, mu)
-    assert_parity(gpu, ref, w_tol=(3e-4 if M == K else W_TOL), obj_tol=(3e-5 if M == K else OBJ_TOL))
+    assert_parity(gpu, ref)
     if M == K:
         for b in range(B):
             Wstar = np.linalg.solve(H[b].astype(np.complex128), np.diag(t[b]).astype(np.complex128)).T
-            assert np.linalg.norm(gpu[0][b] - Wstar) / np.linalg.norm(Wstar) < 3e-4
+            assert np.linalg.norm(gpu[0][b] - Wstar) / np.linalg.norm(Wstar) < W_TOL
 
 
 def test_proj_singular_and_nonfinite_flags(pc, orc):
@@ -160,7 +160,8 @@ def test_proj_singular_and_nonfinite_flags(pc, orc):
 
 def test_proj_ill_conditioned_uses_fp64(pc, orc):
     """Two almost collinear users push the equilibrated pivot ratio over the
-    threshold: the FP64 path runs and parity still holds."""
+    threshold: the FP64 path runs (Gram factorised in FP64, the layers in an
+    orthonormal basis of the channel's row space) and the FP32 bar still holds."""
     capi, precoder = pc
     rs = np.random.default_rng(5)
     H = ch.rayleigh(16, 4, 32, seed=22)
@@ -172,8 +173,7 @@ def test_proj_ill_conditioned_uses_fp64(pc, orc):
     assert np.all(gpu[3][0::2] == capi.F_FP64_CHOL)
     assert np.all(gpu[3][1::2] == 0)
     ref = oracle_ref(orc, 1, H, t, mu)
-    # the conditioning amplifies FP32 rounding of the layers themselves
-    assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
+    assert_parity(gpu, ref)
 
 
 # ---------------------------------------------------------------- paper layer
@@ -497,8 +497,7 @@ def test_fp16_split_flags_and_fp64(pc, orc, tmp_path):
     gpu, ref = (W[ok], obj[ok], res[ok], fl[ok]), oracle_ref(orc, 1, H[ok], t[ok], mu)
     sel = np.isin(ok, well)
     assert_parity(tuple(x[sel] for x in gpu), tuple(x[sel] for x in ref))
-    # the conditioning amplifies the rounding of the layers themselves
-    assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
+    assert_parity(gpu, ref)
 
 
 def test_fp16_split_full_size_sampled(pc, orc, tmp_path):
@@ -599,12 +598,7 @@ def test_fp16_multiwarp_flags_and_fp64(pc, orc, tmp_path, eps):
     sel = np.isin(ok, well)
     assert_parity(tuple(x[sel] for x in gpu), tuple(x[sel] for x in ref))
     assert np.all(np.isfinite(W[ok])) and np.all(np.isfinite(obj[ok]))
-    if eps >= 1e-3:
-        # the conditioning amplifies the rounding of the layers themselves
-        assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
-    # (at eps = 1e-4 the Gram condition is ~1e8: no layer map carried at FP32
-    # precision is accurate there; what is checked is that those instances are
-    # flagged and their outputs stay finite)
+    assert_parity(gpu, ref)
 
 
 @pytest.mark.parametrize("build", ["default", "tf32"])
@@ -625,8 +619,7 @@ def test_tensor_core_ill_conditioned_uses_fp64(pc, orc, tmp_path, build):
     assert np.all(gpu[3][1::2] == 0)
     ref = oracle_ref(orc, 1, H, t, mu)
     assert_parity(tuple(x[1::2] for x in gpu), tuple(x[1::2] for x in ref))
-    # the conditioning amplifies FP32 rounding of the layers themselves
-    assert_parity(gpu, ref, w_tol=2e-3, obj_tol=2e-4)
+    assert_parity(gpu, ref)
 
 
 def tcw_tf32_build(tmp_path, capi, M, K, exact=True):
@@ -692,9 +685,9 @@ def test_tensor_core_padded_users(pc, orc, tmp_path, K, M, build):
     ok = gpu[3] == 0
     assert ok.sum() > B // 2
     assert_parity(tuple(x[ok] for x in gpu), tuple(x[ok] for x in ref))
-    if np.any(~ok):  # FP64-path instances: conditioning amplifies the layers' FP32 rounding
+    if np.any(~ok):  # FP64-path instances (orthonormal basis): the same bar
         assert np.all(gpu[3][~ok] == capi.F_FP64_CHOL)
-        assert_parity(tuple(x[~ok] for x in gpu), tuple(x[~ok] for x in ref), w_tol=2e-3, obj_tol=2e-4)
+        assert_parity(tuple(x[~ok] for x in gpu), tuple(x[~ok] for x in ref))
 
 
 @pytest.mark.parametrize("build", ["default", "tf32"])
@@ -720,9 +713,7 @@ def test_tensor_core_large_flags_and_fp64(pc, orc, tmp_path, build):
     ok = [b for b in range(24) if b not in (3, 5) and b not in fb]
     assert np.all(fl[ok] == 0)
     assert_parity(tuple(x[ok] for x in gpu), oracle_ref(orc, 1, H[ok], t[ok], mu))
-    # the conditioning amplifies FP32 rounding of the layers themselves
-    assert_parity(tuple(x[fb] for x in gpu), oracle_ref(orc, 1, H[fb], t[fb], mu),
-                  w_tol=2e-3, obj_tol=2e-4)
+    assert_parity(tuple(x[fb] for x in gpu), oracle_ref(orc, 1, H[fb], t[fb], mu))
 
 
 def test_tensor_core_kernels_independent_of_earlier_kernels(pc, tmp_path):
@@ -768,3 +759,85 @@ def test_tensor_core_full_size_sampled(pc, orc, tmp_path):
     idx = np.sort(np.random.default_rng(1).choice(wl.B, 256, replace=False))
     assert_parity((W[idx], obj[idx], res[idx], fl[idx]), oracle_ref(orc, 1, H[idx], t[idx], mu))
     assert np.all(res < 1e-4 * math.sqrt(wl.K)) and (fl != 0).mean() < 0.01
+
+
+# ---------------------------------------------------------------- conditioning sweep
+
+def cond_hat(H):
+    """Pivot ratio max d / min d of the LDL^H factorisation of the equilibrated
+    Gram matrix D H H^H D, D = diag(H H^H)^{-1/2} (FP64 numpy): the condition
+    estimate the kernels compare with the threshold of the FP64 path."""
+    out = []
+    for Hb in H.astype(np.complex128):
+        G = Hb @ Hb.conj().T
+        d = 1 / np.sqrt(np.real(np.diag(G)))
+        p = np.real(np.diag(np.linalg.cholesky(d[:, None] * G * d[None, :]))) ** 2
+        out.append(p.max() / p.min())
+    return np.array(out)
+
+
+def near_collinear(B, K, M, eps, seed):
+    """CN(0,1) channels where, per instance, one user's row is another user's
+    row plus eps times CN(0,1) noise (equilibrated Gram condition ~ 1 / eps^2)."""
+    rs = np.random.default_rng(seed + 7)
+    H = ch.rayleigh(B, K, M, seed=seed).copy()
+    for b in range(B):
+        i, j = rs.choice(K, 2, replace=False)
+        H[b, j] = H[b, i] + (eps * (rs.standard_normal(M) + 1j * rs.standard_normal(M))).astype(np.complex64)
+    return H
+
+
+COND_SWEEP = [  # (build label, K, M): every kernel family of the projected layer
+    ("ffma", 4, 32), ("ffma", 11, 100), ("default", 8, 64), ("tf32", 8, 64),
+    ("default", 16, 128), ("default", 32, 256), ("tf32", 32, 256), ("default", 27, 256)]
+
+
+@pytest.mark.parametrize("build,K,M", COND_SWEEP)
+def test_fp64_path_conditioning_sweep(pc, orc, tmp_path, build, K, M):
+    """Rician ULA channels (estimates ~2 to ~8: the FP32 setup) and near-collinear
+    user pairs eps apart, eps from 1e-1 to 1e-5 (equilibrated Gram condition
+    estimates from ~50 to ~5e9: the FP64 path, whose layers run in an orthonormal
+    basis of the channel's row space), default threshold (16), T = 20: every
+    instance meets the 1e-4 / 1e-5 bar; FP64_CHOL is set exactly on the instances
+    whose estimate is clearly above the threshold."""
+    capi, precoder = pc
+    per = 6 if M >= 128 else 12
+    H = np.concatenate([ch.rician_ula(per, K, M, seed=190 + K)] +
+                       [near_collinear(per, K, M, eps, seed=200 + K + i)
+                        for i, eps in enumerate((1e-1, 1e-2, 1e-3, 1e-4, 1e-5))])
+    t = ch.targets(len(H), K)
+    mu = np.full(20, 0.03, np.float32)
+    if build == "ffma":
+        kw = {}
+    elif build == "tf32":
+        kw = build_kw(tmp_path, capi, "tf32", M, K)
+    else:
+        kw = dict(tensor_cores=True)
+    gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **kw)
+    kap = cond_hat(H)
+    fl = gpu[3]
+    assert np.all(fl[kap > 32] == capi.F_FP64_CHOL) and np.all(fl[kap < 8] == 0), (kap, fl)
+    assert (fl == 0).sum() >= per // 2 and (fl != 0).sum() >= 4 * per
+    assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
+    assert np.all(np.isfinite(gpu[0]))
+
+
+# ---------------------------------------------------------------- classical PGD, 5,000 layers
+
+@pytest.mark.parametrize("tc", [False, True])
+def test_pgd_5000_layers_paper_setting(pc, orc, tc):
+    """The classical PGD of Sec. VI-C through the paper-layer kernels: 5,000
+    layers with the constant step eta = 1/L~ and lambda = 1/15, K = 8, M = 64,
+    CN(0,1) channels, gamma = 10 dB.  After 5,000 layers W and the objective still
+    meet the 1e-4 / 1e-5 bar against the FP64 oracle (the tensor-core build adds
+    each update to W with a rounded FP32 add, so the MMA accumulation's rounding
+    does not accumulate into a drift)."""
+    capi, precoder = pc
+    B, K, M, T = 32, 8, 64, 5000
+    H = ch.rayleigh(B, K, M, seed=500)
+    t = ch.targets(B, K, gamma_db=10.0)
+    eta = np.full(T, ch.paper_eta(K, M), np.float32)
+    lam = np.full(T, 1 / 15, np.float32)
+    gpu = run_gpu(precoder, capi.LAYER_PGD, H, t, eta, lam, tensor_cores=tc)
+    ref = oracle_ref(orc, 0, H, t, eta, lam)
+    assert_parity(gpu, ref)

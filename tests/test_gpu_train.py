@@ -229,3 +229,117 @@ def test_graphed_training_matches_eager(mode):
     le = eager.train_step(batches[0], t)
     assert graphed.train_step(batches[0], t) == pytest.approx(le, rel=1e-6, abs=0)
     assert torch.allclose(graphed.step, eager.step, rtol=1e-5, atol=0)
+
+
+def _train_step_one(plan, Hb, tb, step, lam, a, labels=None):
+    """One instance (B = 1) through precode_train_step, or through
+    precode_train_step_supervised with labels: (loss, dstep, dlam)."""
+    from paper_2304_12745_gb300 import capi
+    K, M = Hb.shape
+    Hd = torch.from_numpy(Hb[None].astype(np.complex64)).cuda()
+    td = torch.from_numpy(np.ascontiguousarray(tb, np.float32)).cuda()
+    sd = torch.tensor(step, dtype=torch.float32, device="cuda")
+    ld = torch.tensor(lam, dtype=torch.float32, device="cuda") if lam is not None else None
+    loss = torch.empty(1, device="cuda")
+    ds = torch.empty(len(step), device="cuda")
+    dl = torch.empty(len(step), device="cuda") if lam is not None else None
+    stream = torch.cuda.current_stream().cuda_stream
+    if labels is None:
+        capi.precode_train_step(plan.handle, M, K, 1, Hd, td, 0, sd, ld, a, loss, ds, dl, None, stream)
+    else:
+        Wd = torch.from_numpy(labels[None].astype(np.complex64)).cuda()
+        capi.precode_train_step_supervised(plan.handle, M, K, 1, Hd, td, 0, Wd, sd, ld, loss, ds, dl,
+                                           None, stream)
+    torch.cuda.synchronize()
+    return (float(loss.item()), ds.cpu().numpy().astype(np.float64),
+            None if dl is None else dl.cpu().numpy().astype(np.float64))
+
+
+PER_INSTANCE = [  # (layer, K, M, T, tensor cores, loss)
+    ("proj", 8, 64, 10, True, "unsupervised"), ("proj", 8, 64, 10, True, "supervised"),
+    ("proj", 8, 64, 10, False, "supervised"), ("proj", 4, 32, 6, False, "unsupervised"),
+    ("pgd", 8, 64, 20, True, "unsupervised"), ("pgd", 8, 64, 20, True, "supervised"),
+    ("pgd", 4, 32, 20, False, "supervised")]
+
+
+@pytest.mark.parametrize("layer,K,M,T,tc,kind", PER_INSTANCE)
+def test_gradients_per_instance(orc, layer, K, M, T, tc, kind):
+    """Loss and parameter gradients instance by instance (B = 1 calls), so that an
+    error on a minority of instances cannot average out: the projected layer on
+    8 dB log-normal user gains, the paper layer in the paper's setting (CN(0,1),
+    gamma = 10 dB, I = 20 layers, eta in the clamp interval, lambda = 1/15).  The
+    supervised cost (Sec. V) uses as labels the constrained optimum from the
+    oracle's ADMM (O3), as the paper uses convex-solver solutions.  Per instance:
+    the unsupervised loss within 1e-5 relative, the supervised one within what the
+    W bar (1e-4) allows for a squared distance, each gradient within 2e-3 of the
+    oracle's (relative to the instance's largest component)."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+    rs = np.random.default_rng(60 + K + T)
+    B0 = 24
+    if layer == "proj":
+        H = ch.lognormal(B0, K, M, seed=61 + K).astype(np.complex128)
+        t = np.ones((B0, K))
+        mu = ch.uniform_steps(T, 0.02, 0.08, seed=62).astype(np.float64)
+        keep = _far_from_kinks_proj(orc, H, t, mu, 2e-5)
+        mode, step, lam, a = capi.LAYER_PROJ, mu, None, 1.0
+    else:
+        H = ch.rayleigh(B0, K, M, seed=63 + K).astype(np.complex128)
+        t = np.full((B0, K), math.sqrt(10.0))
+        eta0 = ch.paper_eta(K, M)
+        step = (eta0 * rs.uniform(0.5, 1.0, T)).astype(np.float32).astype(np.float64)
+        lam = np.full(T, np.float32(1 / 15), np.float64)
+        keep = _far_from_kinks_pgd(orc, H, t, step, lam, 2e-5)
+        mode, a = capi.LAYER_PGD, 1 / 15
+    idx = np.nonzero(keep)[0][:12]
+    assert len(idx) >= 8
+    plan = Plan(mode, T, [(M, K)], 1, tensor_cores=tc)
+    if kind == "supervised":  # labels: the constrained optimum (ADMM), as the paper's CVXPY ones
+        Wgt, _, st = orc.batch_admm(H[idx], t[idx], tol=1e-10, nthreads=8)
+        assert np.all(st == orc.OK)
+        Wgt = Wgt.astype(np.complex64)
+    for n, b in enumerate(idx):
+        labels = None
+        if kind == "supervised":
+            labels = Wgt[n]  # complex64, as the GPU sees them
+            ref = (orc.ufproj_grad_supervised(H[b], t[b], step, labels) if layer == "proj"
+                   else orc.ufpgd_grad_supervised(H[b], t[b], step, lam, labels))
+            W_o = (orc.ufproj_forward(H[b], t[b], step)[0] if layer == "proj"
+                   else orc.ufpgd_forward(H[b], t[b], step, lam))
+            # |loss error| <= 2 ||W - W_gt|| ||dW|| + ||dW||^2 with ||dW|| <= 1e-4 ||W|| (the W bar)
+            dw = 1e-4 * np.linalg.norm(W_o)
+            ltol = 2 * math.sqrt(ref[0]) * dw + dw * dw
+        else:
+            ref = (orc.ufproj_grad(H[b], t[b], step, a) if layer == "proj"
+                   else orc.ufpgd_grad(H[b], t[b], step, lam, a))
+            ltol = 1e-5 * ref[0]
+        loss, g, gl = _train_step_one(plan, H[b], t[b], step, lam, a, labels)
+        assert abs(loss - ref[0]) <= ltol, (b, loss, ref[0], ltol)
+        assert np.allclose(g, ref[1], rtol=2e-3, atol=2e-3 * np.abs(ref[1]).max()), (b, g, ref[1])
+        if layer == "pgd":
+            assert np.allclose(gl, ref[2], rtol=2e-3, atol=2e-3 * np.abs(ref[2]).max()), (b, gl, ref[2])
+    plan.close()
+
+
+def test_supervised_training_lowers_the_mse(orc):
+    """Adam on the supervised cost (Sec. V) through the trainer: the projected
+    layer's steps learned towards labels that are the layer's own output at other
+    steps; the MSE falls to a fifth of its start (the steps themselves are not
+    identifiable: several step vectors give nearly the same output)."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.training import UnfoldedTrainer
+    K, M, T, B = 8, 64, 6, 256
+    mu_true = np.linspace(0.09, 0.03, T).astype(np.float32)
+    H = ch.rayleigh(B, K, M, seed=70)
+    t = np.ones((B, K))
+    Wl = orc.batch_forward(1, H.astype(np.complex128), t, mu_true.astype(np.float64), nthreads=8)[0]
+    tr = UnfoldedTrainer(capi.LAYER_PROJ, T, K, M, B, a=1.0, lr=3e-3, init_step=[0.05] * T)
+    Hd = torch.from_numpy(H).cuda()
+    td = torch.ones(K, device="cuda")
+    labels = torch.from_numpy(Wl.astype(np.complex64)).cuda()
+    first = tr.train_step(Hd, td, labels=labels)
+    for _ in range(150):
+        last = tr.train_step(Hd, td, labels=labels)
+    assert last < 0.2 * first, (first, last)
+    assert np.all(tr.step.detach().cpu().numpy() >= 0)  # the projection mu >= 0 held
+    tr.plan.close()

@@ -102,9 +102,10 @@ def test_uneven_tensor_core_buckets_with_padded_users(orc):
         Wg = np.stack([W[h_off[b]:h_off[b] + k * m].reshape(k, m) for b in idx])
         err = np.linalg.norm((Wg - Wo).reshape(len(idx), -1), axis=1) / np.linalg.norm(
             Wo.reshape(len(idx), -1), axis=1)
-        tol = 2e-3 if np.any(fl[idx]) else 1e-4
-        assert err.max() <= tol, (m, k, err.max())
-        assert np.max(np.abs(obj[idx] - oo) / oo) <= (2e-4 if np.any(fl[idx]) else 1e-5), (m, k)
+        # every instance, FP64-path ones included (they run in an orthonormal basis
+        # of the channel's row space), at the same bar
+        assert err.max() <= 1e-4, (m, k, err.max(), fl[idx][err.argmax()])
+        assert np.max(np.abs(obj[idx] - oo) / oo) <= 1e-5, (m, k)
         if m != 100:
             pu = Plan(capi.LAYER_PROJ, T, [(m, k)], len(idx), tensor_cores=True)
             Wu, ou, _, _ = pu.solve(torch.from_numpy(Hb).cuda(), torch.ones(k, device="cuda"), md)
