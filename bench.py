@@ -328,22 +328,42 @@ def bench_train(torch, capi):
             "loss_last": last, "mu_learned": [float(x) for x in mu], "kernel": kernel}, mu
 
 
-def bench_paper_setting(torch, capi):
-    """The paper's own setting (Sec. VI): K = 8, M = 64, i.i.d. CN(0,1) channels,
-    gamma = 10 dB per user (t = sqrt(10), sigma_nu = 1).
-    speed:   the classical PGD of Sec. VI (5,000 iterations, constant eta = 1/L~,
-             lambda = 1/15) through the same paper-layer kernel, next to the 20-layer
-             unfolded network, 8,192 channels per call;
-    quality: PCG = ||W_ZF||_{2,1} / ||W||_{2,1} and the constraint residual
-             ||H W^T - S||_F / ||S||_F after each of the 20 layers, on 4,096 test
-             channels, for PGD (untrained), the unfolded paper layer trained here
-             (eta_t, lambda_t) and the unfolded projected layer trained here (mu_t):
-             Adam, lr 1e-3, 200 steps of 8,192 training channels, loss
-             ||W||_{2,1} + ||H W^T - S||_F^2."""
+def sum_rate_per_channel(torch, H, W, sigma: float = 1.0):
+    """R_sum = sum_k log2(1 + SINR_k) per channel (Sec. VI-B), SINR_k =
+    |[H W^T]_kk|^2 / (sum_{j != k} |[H W^T]_kj|^2 + sigma^2); evaluation of the
+    solver's outputs, not part of the solve."""
+    E = torch.bmm(H, W.transpose(1, 2))  # [B][K][K], row k: user k's received gains
+    p = E.abs() ** 2
+    sig = torch.diagonal(p, dim1=1, dim2=2)
+    intf = p.sum(dim=2) - sig
+    return torch.log2(1 + sig / (intf + sigma * sigma)).sum(dim=1)
+
+
+def bench_paper_setting(torch, capi, max_epochs: int = 200, patience: int = 5):
+    """The paper's own setting and recipe (Sec. VI): K = 8, M = 64, i.i.d. CN(0,1)
+    channels, gamma = 10 dB per user (t = sqrt(10), sigma_nu = 1), lambda = 1/15,
+    I = 20 layers, W^(0) = H^* for the paper layer.
+    speed:   the classical PGD (5,000 iterations, constant eta = 1/L~, lambda = 1/15)
+             through the same paper-layer kernel, next to the 20-layer unfolded
+             network, 8,192 channels per call;
+    quality: Sec. VI-A's training recipe: 10^5 training channels, Adam with batch 64
+             and learning rate 1e-3, epochs of 1,562 steps over a fresh permutation,
+             at most 200 epochs, early stopping when the loss on 5,000 validation
+             channels has not improved for `patience` epochs (the best parameters are
+             kept); then per-layer PCG, sum rate and constraint residual on 5,000
+             test channels (Sec. VI-B) for PGD, the unfolded paper layer trained
+             unsupervised (cost lambda ||W||_{2,1} + ||H W^T - S||_F^2) and supervised
+             (MSE to labels), and the unfolded projected layer trained unsupervised.
+             Labels: the constrained optimum approximated on the GPU by 4,000
+             projected layers with shrink mu_t = 0.1 / sqrt(t) (within ~0.1 % of the
+             ADMM optimum's objective), in place of the paper's CVXPY solutions.
+             Target: the FP64 oracle's ADMM optimum of the same test channels
+             (tests/golden/quality_reference.json), the paper's 1.1160."""
     from paper_2304_12745_gb300.precoder import Plan
     from paper_2304_12745_gb300.training import UnfoldedTrainer
     K, M, T = 8, 64, 20
     amp = math.sqrt(10.0)
+    lam_pgd = 1.0 / 15
     eta = ch.paper_eta(K, M)
     dev = "cuda"
     tK = torch.full((K,), amp, device=dev)
@@ -366,55 +386,129 @@ def bench_paper_setting(torch, capi):
     for name, TT in (("pgd_5000", 5000), ("unfolded_20", T)):
         pl = Plan(capi.LAYER_PGD, TT, [(M, K)], Bs, tensor_cores=True)
         st = torch.full((TT,), eta, device=dev)
-        lm = torch.full((TT,), 1.0 / 15, device=dev)
+        lm = torch.full((TT,), lam_pgd, device=dev)
         ms = timed(lambda: pl.solve(Hs, tK, st, lm), 2 if TT > 100 else 20)
         speed[name] = {"ms_per_call": ms, "precoders_per_s": Bs / (ms / 1e3),
                        "kernel": capi.precode_plan_describe(pl.handle, M, K)}
         pl.close()
     speed["ratio"] = speed["pgd_5000"]["ms_per_call"] / speed["unfolded_20"]["ms_per_call"]
+    del Hs
 
-    # training
-    trained = {}
-    for name, mode in (("unfolded_paper_layer", capi.LAYER_PGD), ("unfolded_projected_layer",
-                                                                   capi.LAYER_PROJ)):
-        tr = UnfoldedTrainer(mode, T, K, M, 8192, a=1.0, lr=1e-3)
-        batches = [tr.make_batch(i, seed=5) for i in range(8)]
-        for i in range(200):
-            tr.train_step(batches[i % 8], tK, sync=False)
-        trained[name] = (mode, tr.step.detach().clone(),
-                         None if tr.lam is None else tr.lam.detach().clone())
-        tr.plan.close()
-    trained["pgd"] = (capi.LAYER_PGD, torch.full((T,), eta, device=dev),
-                      torch.full((T,), 1.0 / 15, device=dev))
-
-    # quality per layer on test channels
-    Bt = 4096
-    Ht = torch.from_numpy(ch.rayleigh(Bt, K, M, seed=41)).cuda()
-    pz = Plan(capi.LAYER_PROJ, 1, [(M, K)], Bt, tensor_cores=True)
-    _, obj_zf, _, _ = pz.solve(Ht, tK, torch.zeros(1, device=dev))
+    # data (Sec. VI-A) and labels
+    Htr = torch.from_numpy(ch.paper_set("train")).cuda()
+    Hva = torch.from_numpy(ch.paper_set("validation")).cuda()
+    Hte = torch.from_numpy(ch.paper_set("test")).cuda()
+    T_long = 4000
+    mu_long = (0.1 / torch.sqrt(torch.arange(1, T_long + 1, device=dev, dtype=torch.float32))).contiguous()
+    pl_long = Plan(capi.LAYER_PROJ, T_long, [(M, K)], len(Htr), tensor_cores=True)
+    t0 = time.perf_counter()
+    lab_tr = pl_long.solve(Htr, tK, mu_long, want_resid=False)[0]
+    lab_va = pl_long.solve(Hva, tK, mu_long, want_resid=False)[0]
+    _, obj_long_te, _, _ = pl_long.solve(Hte, tK, mu_long, want_resid=False)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    pl_long.close()
+    pz = Plan(capi.LAYER_PROJ, 1, [(M, K)], len(Hte), tensor_cores=True)
+    _, obj_zf, _, _ = pz.solve(Hte, tK, torch.zeros(1, device=dev))
     pz.close()
+
+    def val_loss(mode, st, lm, kind, plan):
+        W, obj, res, _ = plan.solve(Hva, tK, st.detach().contiguous(),
+                                    None if lm is None else lm.detach().contiguous())
+        if kind == "supervised":
+            return float(((W - lab_va).abs() ** 2).sum(dim=(1, 2)).mean())
+        return float((lam_pgd * obj + res * res).mean())
+
+    def train(mode, kind):
+        bs = 64
+        tr = UnfoldedTrainer(mode, T, K, M, bs, a=lam_pgd, lr=1e-3, graphs=True)
+        vplan = Plan(mode, T, [(M, K)], len(Hva), tensor_cores=True)
+        Hbuf = torch.empty(bs, K, M, dtype=torch.complex64, device=dev)
+        Lbuf = torch.empty_like(Hbuf) if kind == "supervised" else None
+        gen = torch.Generator().manual_seed(7)
+        steps_per_epoch = len(Htr) // bs
+        best = (val_loss(mode, tr.step, tr.lam, kind, vplan), tr.step.detach().clone(),
+                None if tr.lam is None else tr.lam.detach().clone(), 0)
+        history, bad, epoch = [best[0]], 0, 0
+        t0 = time.perf_counter()
+        for epoch in range(1, max_epochs + 1):
+            perm = torch.randperm(len(Htr), generator=gen).to(dev)
+            for i in range(steps_per_epoch):
+                idx = perm[i * bs:(i + 1) * bs]
+                torch.index_select(Htr, 0, idx, out=Hbuf)
+                if Lbuf is not None:
+                    torch.index_select(lab_tr, 0, idx, out=Lbuf)
+                tr.train_step(Hbuf, tK, sync=False, labels=Lbuf)
+            vl = val_loss(mode, tr.step, tr.lam, kind, vplan)
+            history.append(vl)
+            if vl < best[0] * (1 - 1e-6):
+                best, bad = (vl, tr.step.detach().clone(),
+                             None if tr.lam is None else tr.lam.detach().clone(), epoch), 0
+            else:
+                bad += 1
+                if bad >= patience:
+                    break
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        vplan.close()
+        tr.plan.close()
+        return {"mode": mode, "steps": best[1], "lams": best[2], "epochs": epoch,
+                "best_epoch": best[3], "adam_steps": epoch * steps_per_epoch, "train_s": secs,
+                "val_loss_per_epoch": history}
+
+    runs = {"ufpgd_unsupervised": train(capi.LAYER_PGD, "unsupervised"),
+            "ufpgd_supervised": train(capi.LAYER_PGD, "supervised"),
+            "ufpgd_projected": train(capi.LAYER_PROJ, "unsupervised")}
+    runs["pgd"] = {"mode": capi.LAYER_PGD, "steps": torch.full((T,), eta, device=dev),
+                   "lams": torch.full((T,), lam_pgd, device=dev)}
+
     s_norm = amp * math.sqrt(K)
-    quality = {}
-    for name, (mode, st, lm) in trained.items():
-        pcg, res = [], []
+    methods = {}
+    for name, r in runs.items():
+        pcg, rsum, res = [], [], []
         for TT in range(1, T + 1):
-            pl = Plan(mode, TT, [(M, K)], Bt, tensor_cores=True)
-            _, obj, rsd, _ = pl.solve(Ht, tK, st[:TT].contiguous(),
-                                      None if lm is None else lm[:TT].contiguous())
+            pl = Plan(r["mode"], TT, [(M, K)], len(Hte), tensor_cores=True)
+            W, obj, rsd, _ = pl.solve(Hte, tK, r["steps"][:TT].contiguous(),
+                                      None if r["lams"] is None else r["lams"][:TT].contiguous())
             pcg.append(float((obj_zf / obj).mean()))
+            rsum.append(float(sum_rate_per_channel(torch, Hte, W).mean()))
             res.append(float(rsd.mean()) / s_norm)
             pl.close()
-        quality[name] = {"pcg_per_layer": pcg, "rel_residual_per_layer": res,
-                         "steps": [float(x) for x in st.cpu()],
-                         "lambdas": None if lm is None else [float(x) for x in lm.cpu()]}
-    return {"workload": "paper setting: K=8, M=64, CN(0,1), gamma=10 dB; PGD 5000 it. vs 20 "
-                        "unfolded layers; per-layer PCG on 4,096 test channels",
-            "speed": speed, "quality": quality,
-            "paper_printed": {"pcg_unfolded_20": 1.0915, "pcg_cvx_optimum": 1.1160,
-                              "pcg_pgd_20": "about 1"}}
+        m = {"pcg_per_layer": pcg, "sum_rate_per_layer": rsum, "rel_residual_per_layer": res,
+             "steps": [float(x) for x in r["steps"].cpu()],
+             "lambdas": None if r["lams"] is None else [float(x) for x in r["lams"].cpu()]}
+        for k in ("epochs", "best_epoch", "adam_steps", "train_s", "val_loss_per_epoch"):
+            if k in r:
+                m[k] = r[k]
+        methods[name] = m
+    try:
+        ref = json.load(open(os.path.join(ROOT, "tests", "golden", "quality_reference.json")))
+    except Exception:
+        ref = {}
+    return {"workload": "paper setting: K=8, M=64, CN(0,1), gamma=10 dB, I=20; PGD 5000 it. vs "
+                        "20 unfolded layers; Sec. VI-A training recipe; per-layer metrics on "
+                        "5,000 test channels",
+            "speed": speed,
+            "quality": {
+                "recipe": "10^5 training / 5,000 validation / 5,000 test channels (seeded "
+                          "CN(0,1)); Adam, batch 64, lr 1e-3, epochs of 1,562 steps, early "
+                          f"stopping after {patience} epochs without validation improvement "
+                          f"(at most {max_epochs}); lambda = 1/15 in PGD and in the "
+                          "unsupervised cost; supervised labels from 4,000 projected layers "
+                          "with mu_t = 0.1/sqrt(t) on the GPU",
+                "pcg_20": {k: v["pcg_per_layer"][-1] for k, v in methods.items()},
+                "sum_rate_20": {k: v["sum_rate_per_layer"][-1] for k, v in methods.items()},
+                "target": {"pcg_admm_optimum_test_set": ref.get("pcg_mean"),
+                           "sum_rate_admm_optimum_test_set": ref.get("sum_rate_mean"),
+                           "source": "tests/golden/quality_reference.json (FP64 oracle ADMM)",
+                           "pcg_gpu_long_run_labels": float((obj_zf / obj_long_te).mean()),
+                           "label_generation_s": label_s},
+                "methods": methods,
+                "paper_printed": {"pcg_ufpgd_unsupervised_20": 1.0915, "pcg_cvx_optimum": 1.1160,
+                                  "pcg_pgd_20": "about 1", "sum_rate_target": 27.68}}}
 
 
-def bench_serve(capi, mu, duration_s: float = 2.0):
+def bench_serve(capi, mu, duration_s: float = 2.0, n_runs: int = 3):
     """Serving workload: Poisson arrivals at 2,000 jobs/s, M in {64,128,256},
     K in {4..32}, N_sc in {64,...,1024}, Rician, T = 10 with the learned steps."""
     from paper_2304_12745_gb300.serving import Server, poisson_load
@@ -434,14 +528,24 @@ def bench_serve(capi, mu, duration_s: float = 2.0):
     for j in warm:
         j.wait()
     poisson_load(s, 500.0, 0.2, seed=11)
-    s.reset_stats()
-    st = poisson_load(s, 2000.0, duration_s, seed=12)
+    runs = []
+    for r in range(n_runs):  # independent Poisson runs back to back (seeds 12, 13, ...)
+        s.reset_stats()
+        st = poisson_load(s, 2000.0, duration_s, seed=12 + r)
+        runs.append({"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                     "max_ms": st["max_us"] / 1e3, "precoders_per_s": st["precoders_per_s"],
+                     "jobs": st["jobs"], "achieved_jobs_per_s": st["achieved_rate_per_s"],
+                     "launches": st["launches"]})
     s.close()
-    return {"workload": "serve: Poisson 2,000 jobs/s for %.1f s; M in {64,128,256}, K in {4..32}, "
-                        "N_sc in {64,128,256,512,1024}; Rician; T=10, learned mu" % duration_s,
-            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
-            "precoders_per_s": st["precoders_per_s"], "jobs": st["jobs"],
-            "achieved_jobs_per_s": st["achieved_rate_per_s"], "launches": st["launches"]}
+    med = lambda k: float(np.median([r[k] for r in runs]))  # noqa: E731
+    return {"workload": "serve: Poisson 2,000 jobs/s, %d runs of %.1f s; M in {64,128,256}, "
+                        "K in {4..32}, N_sc in {64,128,256,512,1024}; Rician; T=10, learned mu"
+                        % (n_runs, duration_s),
+            "p50_ms": med("p50_ms"), "p99_ms": med("p99_ms"), "max_ms": max(r["max_ms"] for r in runs),
+            "p99_ms_per_run": [r["p99_ms"] for r in runs],
+            "precoders_per_s": med("precoders_per_s"), "jobs": sum(r["jobs"] for r in runs),
+            "achieved_jobs_per_s": med("achieved_jobs_per_s"), "runs": runs,
+            "note": "p50 / p99 / precoders per s: median over the runs; max: over all runs"}
 
 
 def run_bucket(args):
@@ -537,6 +641,10 @@ def _parser() -> argparse.ArgumentParser:
                     help="profiling aid: solve one uniform bucket of Rician channels (autotuned "
                          "plan), the last solve inside an NVTX range 'prof', print one line, exit")
     ap.add_argument("--bucket-instances", type=int, default=4096)
+    ap.add_argument("--paper", action="store_true",
+                    help="run only the paper-setting sub-benchmark (speed of PGD-5000 vs 20 "
+                         "unfolded layers, and the Sec. VI-A training recipe with per-layer "
+                         "PCG / sum rate on the test set), print its line, exit")
     ap.add_argument("--train", action="store_true",
                     help="run only the training sub-benchmark (the 200 Adam steps, then the "
                          "train-step launch alone with one launch inside an NVTX range 'prof'), "
@@ -556,6 +664,11 @@ def main():
         from paper_2304_12745_gb300 import capi
         line, _ = bench_train(torch, capi)
         print(json.dumps(line))
+        return
+    if args.paper:
+        import torch
+        from paper_2304_12745_gb300 import capi
+        print(json.dumps(bench_paper_setting(torch, capi)))
         return
 
     import torch

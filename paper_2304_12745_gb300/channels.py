@@ -111,6 +111,21 @@ WORKLOADS = {
                       "batches of 8,192 x C^{8x64} i.i.d. CN(0,1), T=10"),
 }
 
+# The paper's training / validation / test sets (Sec. VI-A): i.i.d. CN(0,1) channels
+# C^{8x64}, 10^5 for training, 5,000 for validation, 5,000 for testing; per-user
+# target SINR 10 dB with sigma_nu = 1 (t = sqrt(10)).  name -> (B, seed)
+PAPER_SETS = {"train": (100_000, 300), "validation": (5_000, 301), "test": (5_000, 302)}
+
+
+def paper_set(name: str, chunk: int = 10_000) -> np.ndarray:
+    """One of the paper-setting channel sets, complex64 [B][8][64], drawn in chunks
+    of `chunk` instances (chunk i uses seed * 1000 + i)."""
+    B, seed = PAPER_SETS[name]
+    parts = [rayleigh(min(chunk, B - lo), 8, 64, seed=seed * 1000 + i)
+             for i, lo in enumerate(range(0, B, chunk))]
+    return np.concatenate(parts)
+
+
 UNEVEN_SHAPES = ((32, 4), (64, 8), (128, 16), (256, 32))  # (M, K) buckets of the uneven workload
 
 
