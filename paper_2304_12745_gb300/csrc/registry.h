@@ -24,6 +24,7 @@ struct Variant {
   bool tc;       // contractions on the tensor cores (warp MMA, split TF32); a non-exact
                  // tensor-core build pads users (K <= KB) but needs M == MB
   bool f16 = false;  // the layers' contractions as split-FP16 MMAs (scaled instances)
+  bool tg = false;   // tcgen05 build: operands in shared memory, accumulators in tensor memory
 };
 
 // The instance shapes (M, K) a variant solves.
@@ -55,6 +56,7 @@ void register_solve_proj(std::vector<Variant>& v);
 void register_solve_tc(std::vector<Variant>& v);
 void register_solve_tch(std::vector<Variant>& v);
 void register_solve_tcwh(std::vector<Variant>& v);
+void register_solve_tg(std::vector<Variant>& v);
 const void* tch_host_kernel(int nw, int minb);  // host-buffer twin of a split-FP16 K=8 build
 void register_solve_tcw_64(std::vector<Variant>& v);
 void register_solve_tcw_128(std::vector<Variant>& v);

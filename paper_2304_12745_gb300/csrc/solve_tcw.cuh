@@ -369,11 +369,12 @@ struct SolveTCW {
   // ------------------------------------------------------------------ setup
   // In-place equilibrated Gauss-Jordan inverse of E = G^T (natural, in Es) over
   // the CTA; pivot row / column staged in rowp / colp.  On success Es = G^{-T}.
+  template <int NTX = NT>
   __device__ static bool gj_fp32(const Lane& L, float2* Es, float* dsc, float2* rowp, float2* colp,
                                  float cond_thr) {
     if (L.tid < KB) dsc[L.tid] = rsqrtf(Es[L.tid * KB + L.tid].x);
     __syncthreads();
-    for (int idx = L.tid; idx < KB * KB; idx += NT) {
+    for (int idx = L.tid; idx < KB * KB; idx += NTX) {
       const float sc = dsc[idx / KB] * dsc[idx % KB];
       const float2 v = Es[idx];
       Es[idx] = make_float2(v.x * sc, v.y * sc);
@@ -393,7 +394,7 @@ struct SolveTCW {
       dmin = fminf(dmin, d);
       dmax = fmaxf(dmax, d);
       const float inv = __frcp_rn(d);
-      for (int idx = L.tid; idx < KB * KB; idx += NT) {
+      for (int idx = L.tid; idx < KB * KB; idx += NTX) {
         const int i = idx / KB, j = idx % KB;
         float2 v;
         if (i == p && j == p) {
@@ -417,7 +418,7 @@ struct SolveTCW {
     __syncthreads();
     const bool ok = !fail && !(dmax > cond_thr * dmin);
     if (ok) {
-      for (int idx = L.tid; idx < KB * KB; idx += NT) {
+      for (int idx = L.tid; idx < KB * KB; idx += NTX) {
         const float sc = dsc[idx / KB] * dsc[idx % KB];
         const float2 v = Es[idx];
         Es[idx] = make_float2(v.x * sc, v.y * sc);
@@ -507,13 +508,14 @@ struct SolveTCW {
   // conditioning, while G^{-T} rounded to FP32 perturbs the projector by
   // O(u cond G), which the layers amplify once u cond G nears 1.  Writes U over
   // the channel rows (in place, one thread per antenna column), S~^T into Es
-  // (natural [KB][KB]) and the identity's B fragments into gf.  Padded users
+  // (natural [KB][KB]) and, unless gf is null, the identity's B fragments into gf.  Padded users
   // (K <= k < KB) have zero channel rows and targets and get a unit pivot, so
   // their rows of U and of S~ stay zero.  Returns the instance flags.
+  template <int NTX = NT>
   __device__ static int basis_fp64(const Lane& L, int K, float2* Hs, float2* Es, float4* gf,
                                    double2* A, double* piv, double* ipv, double* orig,
                                    const float* tks) {
-    for (int idx = L.tid; idx < KB * KB; idx += NT) {
+    for (int idx = L.tid; idx < KB * KB; idx += NTX) {
       const int i = idx / KB, j = idx % KB;
       if (j > i) continue;
       double sr = 0.0, si = 0.0;  // sum_m H_im conj(H_jm)
@@ -540,7 +542,7 @@ struct SolveTCW {
       }
       const double inv = 1.0 / d;
       const int R = KB - 1 - p;
-      for (int idx = L.tid; idx < R * R; idx += NT) {
+      for (int idx = L.tid; idx < R * R; idx += NTX) {
         const int i = p + 1 + idx / R, l = p + 1 + idx % R;
         if (l > i) continue;
         const double2 aip = A[i * KB + p], alp = A[l * KB + p];
@@ -565,7 +567,7 @@ struct SolveTCW {
     __syncthreads();
     // U by forward substitution L Y = H, column by column in FP64, then D^{-1/2}
 #pragma unroll 1
-    for (int m = L.tid; m < MB; m += NT) {
+    for (int m = L.tid; m < MB; m += NTX) {
       double yr[KB], yi[KB];
 #pragma unroll 1
       for (int i = 0; i < KB; ++i) {
@@ -589,7 +591,7 @@ struct SolveTCW {
     }
     // S~^T[k][i] = S~[i][k]: forward substitution of t_k e_k
 #pragma unroll 1
-    for (int k = L.tid; k < KB; k += NT) {
+    for (int k = L.tid; k < KB; k += NTX) {
       double yr[KB], yi[KB];
 #pragma unroll 1
       for (int i = 0; i < KB; ++i) {
@@ -612,7 +614,7 @@ struct SolveTCW {
       }
     }
     __syncthreads();  // the FP64 scratch is read out: the identity's fragments go over it
-    for (int idx = L.tid; idx < KW * KW * 32; idx += NT) {
+    for (int idx = L.tid; gf && idx < KW * KW * 32; idx += NTX) {
       const int kt = idx / (KW * 32), cp = (idx / 32) % KW, ln = idx % 32;
       const int gg = ln >> 2, qq = ln & 3;
       gf[idx] = make_float4(8 * kt + 2 * qq == 8 * cp + gg ? 1.f : 0.f,

@@ -1,0 +1,15 @@
+// Instantiation of the fifth-generation tensor-core projected-layer kernel:
+// any K <= 32 users at exactly 256 antennas (users padded to 32).
+#include "registry.h"
+#include "solve_tg.cuh"
+
+namespace precode {
+
+void register_solve_tg(std::vector<Variant>& v) {
+  Variant x{kModeProj, 32, 256, 4, 8, 8, TgCfg::NT / 32, 1, false, true, false,
+            (const void*)&solve_tg_kernel<1>, TgCfg::SMEM_BYTES, TgCfg::NT, 1, true, true};
+  x.tg = true;
+  v.push_back(x);
+}
+
+}  // namespace precode
