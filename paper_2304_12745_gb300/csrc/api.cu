@@ -105,12 +105,15 @@ int variant_occupancy(const Variant& v, int device) {
   return c[idx];
 }
 
-// Default choice: with tensor cores, the exact tensor-core build of (mode, K, M),
+// Default choice: with tensor cores, the tcgen05 build where it holds (K, M) with
+// fewer than 8 padded users, else the exact tensor-core build of (mode, K, M),
 // else the smallest user-padded one with M antennas; then the first exact FP32
 // variant, else the smallest generic bucket that holds (K, M).
 const Variant* pick_variant(int mode, int M, int K, bool tensor_cores) {
   const Variant* best = nullptr;
   if (tensor_cores) {
+    for (const auto& v : variants())
+      if (v.tg && v.mode == mode && variant_fits(v, M, K) && v.KB < K + 8) return &v;
     for (const auto& v : variants())
       if (v.tc && v.exact && v.mode == mode && variant_fits(v, M, K)) return &v;
     for (const auto& v : variants())

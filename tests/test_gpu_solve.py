@@ -259,7 +259,7 @@ def test_fp16_builds_small_batches_and_shared_targets(pc, orc, M, K):
     for T in (1, 4):
         mu = ch.uniform_steps(T, 0.01, 0.1, seed=61)
         plan = precoder.Plan(capi.LAYER_PROJ, T, [(M, K)], 3, tensor_cores=True)
-        assert capi.precode_plan_describe(plan.handle, M, K).startswith(("solve_tch", "solve_tcwh"))
+        assert capi.precode_plan_describe(plan.handle, M, K).startswith(("solve_tch", "solve_tcwh", "solve_tg"))
         md, td = torch.from_numpy(mu).cuda(), torch.from_numpy(t_shared).cuda()
         plan.solve(torch.empty((0, K, M), dtype=torch.complex64, device="cuda"), td, md)  # no-op
         W3, o3, r3, f3 = plan.solve(torch.from_numpy(H).cuda(), td, md)
@@ -740,10 +740,10 @@ def tcw_tf32_build(tmp_path, capi, M, K, exact=True):
 @pytest.mark.parametrize("K,M,B", [(16, 128, 2600), (32, 256, 700)])
 @pytest.mark.parametrize("mode", ["proj", "proj_tf32", "pgd"])
 def test_tensor_core_large_buckets(pc, orc, tmp_path, K, M, B, mode):
-    """Multi-warp tensor-core builds (one CTA of K/8 warps per instance; split FP16
-    by default for the projected layer, split TF32 pinned, split TF32 for the paper
-    layer) against the oracle, over more instances than one persistent round, so
-    CTAs take a ragged number of instances."""
+    """Multi-warp tensor-core builds (one CTA per instance; for the projected layer
+    split FP16 by default, tcgen05 at 32 x 256, split TF32 pinned; split TF32 for
+    the paper layer) against the oracle, over more instances than one persistent
+    round, so CTAs take a ragged number of instances."""
     capi, precoder = pc
     kw = tcw_tf32_build(tmp_path, capi, M, K) if mode == "proj_tf32" else dict(tensor_cores=True)
     if mode.startswith("proj"):
@@ -759,7 +759,8 @@ def test_tensor_core_large_buckets(pc, orc, tmp_path, K, M, B, mode):
     plan = precoder.Plan(m, len(step), [(M, K)], B, **kw)
     name = capi.precode_plan_describe(plan.handle, M, K)
     plan.close()
-    assert name.startswith("solve_tcwh_kernel" if mode == "proj" else "solve_tcw_kernel"), name
+    expect = {"proj": "solve_tg_kernel" if M == 256 else "solve_tcwh_kernel"}.get(mode, "solve_tcw_kernel")
+    assert name.startswith(expect), name
     gpu = run_gpu(precoder, m, H, t, step, lam, **kw)
     ref = oracle_ref(orc, 0 if mode == "pgd" else 1, H, t, step, lam)
     assert_parity(gpu, ref)
@@ -781,8 +782,12 @@ def test_tensor_core_padded_users(pc, orc, tmp_path, K, M, build):
     plan = precoder.Plan(capi.LAYER_PROJ, 10, [(M, K)], B, **kw)
     name = capi.precode_plan_describe(plan.handle, M, K)
     plan.close()
-    # K <= 8 has only split-TF32 padded builds (one warp); 9..32 default to split FP16
-    assert name.startswith("solve_tcwh_kernel" if build == "default" and K > 8 else "solve_tcw_kernel"), name
+    # K <= 8 has only split-TF32 padded builds (one warp); 9..32 default to split FP16,
+    # 25..32 at 256 antennas to the tcgen05 build
+    expect = "solve_tcw_kernel"
+    if build == "default" and K > 8:
+        expect = "solve_tg_kernel" if (M == 256 and K > 24) else "solve_tcwh_kernel"
+    assert name.startswith(expect), name
     gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **kw)
     ref = oracle_ref(orc, 1, H, t, mu)
     ok = gpu[3] == 0
