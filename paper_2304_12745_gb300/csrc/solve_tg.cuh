@@ -65,7 +65,9 @@ struct TgCfg {
   static constexpr int ECS = KB + 1;                    // E row stride (float2)
   static constexpr int OFF_EC = OFF_ED + 128 * EDS * 4;  // E [32][33] float2
   static constexpr int OFF_ES = OFF_EC + KB * ECS * 8;   // G'^{-T} or S~^T [32][32] float2
-  static constexpr int OFF_NP = OFF_ES + 8192;           // column-norm partials [4 row groups][256]
+  static constexpr int FSS = 72;                         // F staging row stride (floats)
+  static constexpr int OFF_FS = OFF_ES + 8192;           // F staging [8 warps][4 rows][FSS]
+  static constexpr int OFF_NP = OFF_FS + 8 * 4 * FSS * 4;  // column-norm partials [4 row groups][256]
   static constexpr int OFF_FAC = OFF_NP + 4096;          // shrink factors [256]
   static constexpr int OFF_S64 = OFF_FAC + 1024;         // FP64 pivots: double2[32] x 2, double[32]
   // t[32] dsc[32] misc[8] wred[8] fsc[32] dd[32] dgs[32] rowpub[2][32] colpub[2][32] (float2)
@@ -79,7 +81,7 @@ struct TgCfg {
   static_assert(KB * RSF * 8 <= HS_BYTES && OFF_AWL + 32768 <= HS_BYTES, "channel and A_W share an area");
   static_assert(128 * EDS * 4 >= KB * KB * 16, "the FP64 matrix of the setup fits the staging");
   static_assert(OFF_HR % 1024 == 0 && OFF_AF % 128 == 0 && OFF_ED % 16 == 0 && OFF_ES % 16 == 0 &&
-                    OFF_SC % 16 == 0 && OFF_BAR % 8 == 0,
+                    OFF_FS % 16 == 0 && OFF_SC % 16 == 0 && OFF_BAR % 8 == 0,
                 "alignment");
   static_assert(SMEM_BYTES <= 227 * 1024, "one CTA per SM");
 };
@@ -254,10 +256,6 @@ struct SolveTG {
     return ss;
   }
 
-  __device__ __forceinline__ static void st_h(unsigned char* sm, int off, int r, int c, __half v) {
-    *reinterpret_cast<__half*>(sm + off + tc5::tile_off(r, c, 64)) = v;
-  }
-
   // F from the thread's E entries (F = E G'^{-T}, or in the basis F = E diag(dd)),
   // each row's power-of-two range scale (into fsc: the factor D_W's rows k and
   // k + 32 take back), and the thread's entries of A_F hi / lo.  The warp's rows
@@ -265,7 +263,7 @@ struct SolveTG {
   // consecutive words.
   __device__ __forceinline__ static void make_af(const Lane& L, const float (&er)[4], const float (&ei)[4],
                                                  bool basis, const float* dd, const float2* G, float2* Ec,
-                                                 float* fsc, unsigned char* sm) {
+                                                 float* fsc, float* Fs, unsigned char* sm) {
     const int k0 = 4 * L.w, j = L.lane;
     float fr[4], fi[4];
     if (basis) {
@@ -301,6 +299,11 @@ struct SolveTG {
     for (int msk = 1; msk < 32; msk <<= 1)
 #pragma unroll
       for (int i = 0; i < 4; ++i) m[i] = fmaxf(m[i], __shfl_xor_sync(FULL, m[i], msk));
+    // scaled F rows [Re F | Im F] into the warp's FP32 staging (word stores), then
+    // lane (row r = lane % 4, chunk c = lane / 4 of 8 columns) splits 8 columns and
+    // writes them into rows k (chunk c) and k + 32 (chunk c +- 4, Re negated) of the
+    // A_F tiles with 16-byte stores (an access phase spans four rows)
+    float* const fw = Fs + L.w * 4 * C::FSS;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int k = k0 + i;
@@ -313,18 +316,28 @@ struct SolveTG {
         xs = ldexpf(1.f, ex - 14);
       }
       if (j == 0) fsc[k] = xs;
-      const float a = fs * fr[i], b = fs * fi[i];
-      const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
-      const __half al = __float2half_rn(a - __half2float(ah)), bl = __float2half_rn(b - __half2float(bh));
-      st_h(sm, C::OFF_AF, k, j, ah);
-      st_h(sm, C::OFF_AFL, k, j, al);
-      st_h(sm, C::OFF_AF, k, j + 32, bh);
-      st_h(sm, C::OFF_AFL, k, j + 32, bl);
-      st_h(sm, C::OFF_AF, k + 32, j, bh);
-      st_h(sm, C::OFF_AFL, k + 32, j, bl);
-      st_h(sm, C::OFF_AF, k + 32, j + 32, __hneg(ah));
-      st_h(sm, C::OFF_AFL, k + 32, j + 32, __hneg(al));
+      fw[i * C::FSS + j] = fs * fr[i];
+      fw[i * C::FSS + 32 + j] = fs * fi[i];
     }
+    __syncwarp();
+    {
+      const int r = L.lane & 3, c = L.lane >> 2, k = k0 + r;
+      const float4 x0 = *reinterpret_cast<const float4*>(fw + r * C::FSS + 8 * c);
+      const float4 x1 = *reinterpret_cast<const float4*>(fw + r * C::FSS + 8 * c + 4);
+      const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      uint4 h, lo;
+      split8(x, h, lo);
+      *reinterpret_cast<uint4*>(sm + C::OFF_AF + tc5::tile_off(k, 8 * c, 64)) = h;
+      *reinterpret_cast<uint4*>(sm + C::OFF_AFL + tc5::tile_off(k, 8 * c, 64)) = lo;
+      // row k + 32 = [Im F | -Re F]: chunk c of [Re | Im] lands at c + 4 (negated) or c - 4
+      const int c2 = c < 4 ? c + 4 : c - 4;
+      const uint32_t neg = c < 4 ? 0x80008000u : 0u;
+      const uint4 hn = make_uint4(h.x ^ neg, h.y ^ neg, h.z ^ neg, h.w ^ neg);
+      const uint4 ln = make_uint4(lo.x ^ neg, lo.y ^ neg, lo.z ^ neg, lo.w ^ neg);
+      *reinterpret_cast<uint4*>(sm + C::OFF_AF + tc5::tile_off(k + 32, 8 * c2, 64)) = hn;
+      *reinterpret_cast<uint4*>(sm + C::OFF_AFL + tc5::tile_off(k + 32, 8 * c2, 64)) = ln;
+    }
+    __syncwarp();
   }
 
   // w = a w - xs D_W for the thread's 64 entries (a = 1, or 0 for W^(0))
@@ -386,11 +399,17 @@ struct SolveTG {
   // G'^T[i][j_c] on entry and G'^{-T}[i][j_c] on a true return.  Pivot p's row and
   // column are published by their owners into one of two buffers (alternating),
   // one barrier a pivot.  The per-entry arithmetic is that of the multi-warp
-  // kernels' shared-memory version.
+  // kernels' shared-memory version (a - (c / d) b for the rest of the matrix).
   __device__ static bool gj_regs(const Lane& L, float2 (&a)[4], float* dsc, float2* rowpub,
                                  float2* colpub, float cond_thr) {
     const int i = L.tid >> 3, j0 = L.tid & 7;
-    if (j0 == (i & 7)) dsc[i] = rsqrtf(a[i >> 3].x);
+    if (j0 == (i & 7)) {  // the diagonal entry (static register indices only)
+      float dv = a[0].x;
+#pragma unroll
+      for (int c = 1; c < 4; ++c)
+        if (c == (i >> 3)) dv = a[c].x;
+      dsc[i] = rsqrtf(dv);
+    }
     __syncthreads();
     const float di = dsc[i];
     float dj[4];
@@ -418,29 +437,23 @@ struct SolveTG {
       }
       __syncthreads();
       const float d = rp[p].x;
+      const float2 ci = cp[i];
+      float2 rb[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rb[c] = rp[j0 + 8 * c];
       fail |= !(d > 0.f) || !(d < FLT_MAX);
       dmin = fminf(dmin, d);
       dmax = fmaxf(dmax, d);
       const float inv = __frcp_rn(d);
-      const float2 ci = cp[i];
+      const float tr = ci.x * inv, ti = ci.y * inv;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < 4; ++c) {  // all four cases formed, one selected (no divergence)
         const int j = j0 + 8 * c;
-        float2 v;
-        if (i == p && j == p) {
-          v = make_float2(inv, 0.f);
-        } else if (i == p) {
-          v = make_float2(a[c].x * inv, a[c].y * inv);
-        } else if (j == p) {
-          v = make_float2(-ci.x * inv, -ci.y * inv);
-        } else {
-          const float2 b = rp[j];
-          const float tr = ci.x * inv, ti = ci.y * inv;
-          v = a[c];
-          v.x -= tr * b.x - ti * b.y;
-          v.y -= tr * b.y + ti * b.x;
-        }
-        a[c] = v;
+        const float2 b = rb[c], v = a[c];
+        const float2 g = make_float2(v.x - (tr * b.x - ti * b.y), v.y - (tr * b.y + ti * b.x));
+        const float2 rowv = make_float2(v.x * inv, v.y * inv);
+        const float2 colv = make_float2(-ci.x * inv, -ci.y * inv);
+        a[c] = (i == p) ? ((j == p) ? make_float2(inv, 0.f) : rowv) : ((j == p) ? colv : g);
       }
     }
     const bool ok = !fail && !(dmax > cond_thr * dmin);
@@ -503,6 +516,7 @@ struct SolveTG {
     double2* const A64 = reinterpret_cast<double2*>(sm + C::OFF_ED);
     float2* const Ec = reinterpret_cast<float2*>(sm + C::OFF_EC);
     float2* const Es = reinterpret_cast<float2*>(sm + C::OFF_ES);
+    float* const Fs = reinterpret_cast<float*>(sm + C::OFF_FS);
     float* const np = reinterpret_cast<float*>(sm + C::OFF_NP);
     float* const fac = reinterpret_cast<float*>(sm + C::OFF_FAC);
     double2* const r64 = reinterpret_cast<double2*>(sm + C::OFF_S64);
@@ -679,7 +693,7 @@ struct SolveTG {
               ei[i] = 0.f;
             }
           }
-          make_af(L, er, ei, basis, dd, Es, Ec, fsc, sm);
+          make_af(L, er, ei, basis, dd, Es, Ec, fsc, Fs, sm);
         }
         publish_smem();
         if (L.tid == 0) {
@@ -746,7 +760,7 @@ struct SolveTG {
           {
             float er[4], ei[4];
             form_e(L, Sg, tks, Es, dinv, basis, er, ei);
-            make_af(L, er, ei, basis, dd, Es, Ec, fsc, sm);
+            make_af(L, er, ei, basis, dd, Es, Ec, fsc, Fs, sm);
           }
           publish_smem();
           if (L.tid == 0) {
