@@ -44,6 +44,7 @@ struct TrainVariant {
   int groups;
   bool tc;  // tensor-core (split TF32) build
   bool f16 = false;  // the layers' contractions as split-FP16 MMAs (scaled instances)
+  int cp_onchip = 0;  // up to this many checkpoints per instance stay in tensor memory
 };
 
 void register_solve_pgd(std::vector<Variant>& v);

@@ -117,7 +117,10 @@ static precode_status_t train_step_impl(precode_plan_t p, int32_t M, int32_t K, 
   const int T = p->T;
   const int cpe = (int)std::ceil(std::sqrt((double)T));
   const int ncp = (T + cpe - 1) / cpe;
-  const size_t cp_need = (size_t)p->max_instances * ncp * v->KB * v->MB * sizeof(float2);
+  // checkpoints in tensor memory where the kernel holds them, else a global workspace
+  const bool cp_onchip = ncp <= v->cp_onchip;
+  const size_t cp_need =
+      cp_onchip ? 0 : (size_t)p->max_instances * ncp * v->KB * v->MB * sizeof(float2);
   const size_t part_need = (size_t)p->max_instances * (1 + 2 * T) * sizeof(float);
   if (cp_need > p->cp_bytes) {
     cudaFree(p->d_cp);
@@ -154,7 +157,7 @@ static precode_status_t train_step_impl(precode_plan_t p, int32_t M, int32_t K, 
   A.s.err = p->d_err;
   A.a = a;
   A.wgt = static_cast<const float2*>(wgt);
-  A.cp = p->d_cp;
+  A.cp = cp_onchip ? nullptr : p->d_cp;
   A.cp_every = cpe;
   A.ncp = ncp;
   A.part = p->d_part;

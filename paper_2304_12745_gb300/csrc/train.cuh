@@ -28,7 +28,8 @@ struct TrainArgs {
   SolveArgs s;      // H, t, t_stride, step, lam, B, K, M, T, cond_thr, opts, err, flags
   float a;          // weight of ||W_T||_{2,1} in the unsupervised loss
   const float2* wgt;  // supervised loss: labels W_gt [B][K][M] (W's layout), else nullptr
-  float2* cp;       // checkpoints [B][ncp][KB*MB] (bucket-sized slots)
+  float2* cp;       // checkpoints [B][ncp][KB*MB] (bucket-sized slots); nullptr: in
+                    // tensor memory (kernels that keep ncp of them on chip)
   int cp_every;     // checkpoint interval c
   int ncp;          // checkpoints per instance = ceil(T / c)
   float* part;      // per-instance [B][1 + 2T]: loss, d step[T], d lam[T]

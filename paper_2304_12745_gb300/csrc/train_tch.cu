@@ -9,8 +9,10 @@ namespace precode {
 // 8,192-instance training step it is 5 % faster (more warps for a short persistent
 // loop); on 65,536 resident instances 4 % slower.
 void register_train_tch(std::vector<TrainVariant>& v) {
-  v.push_back(TrainVariant{kModeProj, 8, 64, true, (const void*)&train_tch_kernel<4, 3>,
-                           TrainTCH<4>::SMEM_BYTES, 4 * 32, 4, true, true});
+  TrainVariant x{kModeProj, 8, 64, true, (const void*)&train_tch_kernel<4, 3>,
+                 TrainTCH<4>::SMEM_BYTES, 4 * 32, 4, true, true};
+  x.cp_onchip = TrainTCH<4>::CP_ONCHIP;
+  v.push_back(x);
 }
 
 }  // namespace precode

@@ -12,11 +12,15 @@
 // The loss and its gradient at W_T are formed in original units in FP32 (the
 // gradient's 2 E_T H^* with split-TF32 MMAs on the unscaled conj(H); with labels,
 // the supervised 2 (W_T - W_gt)).  W_l is
-// kept (scaled) at every c-th layer in global memory and the reverse pass
-// recomputes the layers in between.
+// kept (scaled) at every c-th layer and the reverse pass recomputes the layers in
+// between.  Up to CP_ONCHIP checkpoints stay in tensor memory: a warp's W
+// fragments are 32 registers a lane, one 32x32b store of 32 columns into the
+// warp's lane quarter (the block holds 32 CP_ONCHIP columns, three blocks fit an
+// SM's 512); more go to a global workspace.
 #pragma once
 
 #include "solve_tch.cuh"
+#include "tcgen05.cuh"
 #include "train_tc.cuh"
 
 namespace precode {
@@ -35,7 +39,12 @@ struct TrainTCH {
   static constexpr int OFF_FB2 = SH::GROUP_STRIDE;
   static constexpr int OFF_XR = OFF_FB2 + 256;
   static constexpr int GROUP_STRIDE = OFF_XR + 8 * 32 * 16;
-  static constexpr int SMEM_BYTES = NW * GROUP_STRIDE;
+  static constexpr int OFF_TSLOT = NW * GROUP_STRIDE;  // the block's TMEM address
+  static constexpr int SMEM_BYTES = OFF_TSLOT + 16;
+  static constexpr int CP_ONCHIP = 4;
+  static constexpr uint32_t CP_COLS = 32 * CP_ONCHIP;
+  static_assert(NW <= 4, "one TMEM lane quarter per warp");
+  static_assert(GROUP_STRIDE % 16 == 0, "alignment");
 
   // one forward layer l in scaled units: W'_l -> W'_{l+1}
   __device__ __forceinline__ static void fwd_layer(const Lane& L, const Ctx& c, const TrainArgs& A,
@@ -87,7 +96,14 @@ struct TrainTCH {
     float4* const xr = reinterpret_cast<float4*>(gs + OFF_XR);
     if (c.g == 0) mbar_init(c.bar, 1);
     fence_mbar_init();
+    const bool onchip = A.cp == nullptr;  // checkpoints in tensor memory
+    uint32_t* const tslot = reinterpret_cast<uint32_t*>(smem + OFF_TSLOT);
+    if (onchip && c.gid == 0) tc5::alloc(smem_addr(tslot), CP_COLS);
+    tc5::fence_before_sync();
     __syncthreads();
+    tc5::fence_after_sync();
+    const uint32_t tbase = onchip ? *tslot : 0u;
+    const uint32_t tcp = tbase + ((uint32_t)(32 * c.gid) << 16);  // this warp's lane quarter
 
     const int T = A.s.T;
     const int PW = 1 + 2 * T;
@@ -117,7 +133,7 @@ struct TrainTCH {
           c.misc[1] = mbar_wait_bounded(c.bar, phase, copy_wait_ns(A.s)) ? 1 : 0;
         }
         __syncwarp();
-        if (c.misc[1] == 0) return;
+        if (c.misc[1] == 0) break;  // the copy never landed: stop (TMEM is freed below)
         for (int j = c.g; j < PW; j += 32) part[j] = 0.f;
         phase ^= 1u;
         issue_copy(inst + stride);
@@ -143,13 +159,34 @@ struct TrainTCH {
         issue_copy(inst + stride);
         continue;
       }
-      float4* const cp = reinterpret_cast<float4*>(A.cp + inst * (int64_t)A.ncp * (KB * MB));
+      float4* const cp = onchip ? nullptr
+                                : reinterpret_cast<float4*>(A.cp + inst * (int64_t)A.ncp * (KB * MB));
       auto store_cp = [&](int k) {
+        if (onchip) {
+          float v[32];
+#pragma unroll
+          for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[4 * s + i] = w[s][i];
+          tc5::st32x32b_x32(tcp + 32 * k, v);
+          tc5::wait_st();
+          return;
+        }
 #pragma unroll
         for (int s = 0; s < 8; ++s)
           cp[(k * 8 + s) * 32 + L.lane] = make_float4(w[s][0], w[s][1], w[s][2], w[s][3]);
       };
       auto load_cp = [&](int k) {
+        if (onchip) {
+          float v[32];
+          tc5::ld32x32b_x32(tcp + 32 * k, v);
+          tc5::wait_ld();
+#pragma unroll
+          for (int s = 0; s < 8; ++s)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[s][i] = v[4 * s + i];
+          return;
+        }
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
           const float4 v = cp[(k * 8 + s) * 32 + L.lane];
@@ -245,6 +282,9 @@ struct TrainTCH {
       __syncwarp();  // the channel buffer is free
       issue_copy(inst + stride);
     }
+    tc5::fence_before_sync();
+    __syncthreads();
+    if (onchip && c.gid == 0) tc5::dealloc(tbase, CP_COLS);
   }
 };
 

@@ -257,6 +257,9 @@ def _train_step_one(plan, Hb, tb, step, lam, a, labels=None):
 
 PER_INSTANCE = [  # (layer, K, M, T, tensor cores, loss)
     ("proj", 8, 64, 10, True, "unsupervised"), ("proj", 8, 64, 10, True, "supervised"),
+    # the split-FP16 kernel's checkpoints: 4 in tensor memory at T = 20, a global
+    # workspace at T = 30 (5 checkpoints)
+    ("proj", 8, 64, 20, True, "unsupervised"), ("proj", 8, 64, 30, True, "unsupervised"),
     ("proj", 8, 64, 10, False, "supervised"), ("proj", 4, 32, 6, False, "unsupervised"),
     ("pgd", 8, 64, 20, True, "unsupervised"), ("pgd", 8, 64, 20, True, "supervised"),
     ("pgd", 4, 32, 20, False, "supervised")]
