@@ -15,8 +15,10 @@
 // kept (scaled) at every c-th layer and the reverse pass recomputes the layers in
 // between.  Up to CP_ONCHIP checkpoints stay in tensor memory: a warp's W
 // fragments are 32 registers a lane, one 32x32b store of 32 columns into the
-// warp's lane quarter (the block holds 32 CP_ONCHIP columns, three blocks fit an
-// SM's 512); more go to a global workspace.
+// warp's lane quarter (warp w: quarter w % 4, column group w / 4 of 32 CP_ONCHIP
+// columns); more go to a global workspace.  A kernel that allocates tensor memory
+// is resident once per SM, so the build runs one block of 12 warps per SM (the
+// warps of three 4-warp blocks).
 #pragma once
 
 #include "solve_tch.cuh"
@@ -42,8 +44,9 @@ struct TrainTCH {
   static constexpr int OFF_TSLOT = NW * GROUP_STRIDE;  // the block's TMEM address
   static constexpr int SMEM_BYTES = OFF_TSLOT + 16;
   static constexpr int CP_ONCHIP = 4;
-  static constexpr uint32_t CP_COLS = 32 * CP_ONCHIP;
-  static_assert(NW <= 4, "one TMEM lane quarter per warp");
+  static constexpr uint32_t CP_GROUP = 32 * CP_ONCHIP;  // columns of one warp's checkpoints
+  static constexpr uint32_t CP_COLS = NW <= 4 ? CP_GROUP : NW <= 8 ? 2 * CP_GROUP : 4 * CP_GROUP;
+  static_assert(NW <= 16 && (NW <= 4 || NW % 4 == 0), "warps share lane quarters by column group");
   static_assert(GROUP_STRIDE % 16 == 0, "alignment");
 
   // one forward layer l in scaled units: W'_l -> W'_{l+1}
@@ -103,7 +106,8 @@ struct TrainTCH {
     __syncthreads();
     tc5::fence_after_sync();
     const uint32_t tbase = onchip ? *tslot : 0u;
-    const uint32_t tcp = tbase + ((uint32_t)(32 * c.gid) << 16);  // this warp's lane quarter
+    // this warp's lane quarter and column group
+    const uint32_t tcp = tbase + ((uint32_t)(32 * (c.gid & 3)) << 16) + CP_GROUP * (uint32_t)(c.gid >> 2);
 
     const int T = A.s.T;
     const int PW = 1 + 2 * T;
