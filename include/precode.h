@@ -311,6 +311,7 @@ typedef struct {
   int64_t instances_done;
   int64_t bytes_in_use, bytes_budget;
   int32_t slots_busy, queued;
+  int64_t factor_instances; /* instances launched with their channel's resident Gram factors */
 } precode_serve_stats_t;
 
 /* Create the server (arena, one plan + stream per slot, dispatcher and
@@ -328,7 +329,15 @@ precode_status_t precode_serve_wait(precode_server_t s, uint64_t ticket, int64_t
 precode_status_t precode_serve_stats(precode_server_t s, precode_serve_stats_t* st);
 precode_status_t precode_serve_reset_stats(precode_server_t s);
 /* Copy n_sc channels [n_sc][K][M] (HOST) to the device once; jobs that name the
- * handle skip the host->device copy of H. */
+ * handle skip the host->device copy of H.  Where the kernel that serves (M, K) keeps
+ * Gram factors (the projected layer's split-FP16 K = 8 / M = 64, multi-warp
+ * split-FP16 and tcgen05 builds), the channel also keeps each subcarrier's
+ * G'^{-T} = (D H H^H D)^{-T} (the Gram inverse of P_A above, with the kernel's
+ * per-user power-of-two scales D), computed here once by that kernel, and jobs on it
+ * skip the Gram matrix and its inversion: results bitwise the same as a copied
+ * channel.  Subcarriers whose Gram matrix takes the FP64 path are set up in full by
+ * every job.  ENOMEM: no arena room for H (room for H but not for the factors keeps
+ * the channel without them). */
 precode_status_t precode_serve_channel_create(precode_server_t s, int32_t M, int32_t K,
                                               int32_t n_sc, const void* H, uint64_t* handle);
 /* Waits until no unfinished job uses the channel, then frees it. */

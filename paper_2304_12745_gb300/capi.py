@@ -68,7 +68,8 @@ class ServeStats(ctypes.Structure):
                 ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double),
                 ("precoders_per_s", ctypes.c_double), ("instances_done", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_int64), ("bytes_budget", ctypes.c_int64),
-                ("slots_busy", ctypes.c_int32), ("queued", ctypes.c_int32)]
+                ("slots_busy", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("factor_instances", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p

@@ -228,6 +228,37 @@ namespace precode {
 precode_status_t autotune_plan(precode_plan_t p, const char* cache_path);
 }  // namespace precode
 
+precode_status_t precode::plan_export_factors(precode_plan_t p, int32_t M, int32_t K, int64_t n,
+                                              const void* H, float2* fac, void* W, const float* t,
+                                              cudaStream_t stream, int* stride) {
+  *stride = 0;
+  if (!p || n < 1 || !H || !fac || !W || !t || p->mode != PRECODE_LAYER_PROJ || !shape_ok(p->mode, M, K))
+    return PRECODE_OK;
+  const Variant* v = p->variant_for(M, K);
+  if (!v || !v->fac) return PRECODE_OK;
+  std::lock_guard<std::mutex> lk(p->mu);
+  DeviceGuard g(p->device);
+  SolveArgs A{};
+  A.H = static_cast<const float2*>(H);
+  A.t = t;
+  A.t_stride = 0;
+  A.step = t;  // not read: no layers
+  A.lam = t;
+  A.W = static_cast<float2*>(W);
+  A.B = n;
+  A.K = K;
+  A.M = M;
+  A.T = 0;
+  A.cond_thr = p->cond_thr;
+  A.opts = p->kernel_opts() | OPT_FAC_EXPORT;
+  A.wait_ns = p->wait_ns;
+  A.err = p->d_err;
+  A.fac = fac;
+  const precode_status_t st = launch_variant(*v, p->device, p->num_sms, A, n, stream);
+  if (st == PRECODE_OK) *stride = fac_stride(v->KB);
+  return st;
+}
+
 extern "C" {
 
 const char* precode_status_str(precode_status_t s) {

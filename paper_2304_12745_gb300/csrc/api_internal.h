@@ -62,6 +62,22 @@ struct Bucket {
   const Variant* v;
 };
 
+// precode_solve_varlen with resident Gram factors: fidx[b] >= 0 is the float2
+// offset in fac of instance b's factor slot (nullptr fac / fidx: none).
+precode_status_t solve_varlen_fac(precode_plan_t p, int64_t B, const precode_inst_t* tbl,
+                                  const void* H, const float* t, const float* step,
+                                  const float* lam, void* W, float* obj, float* resid,
+                                  int32_t* flags, float2* fac, const int64_t* fidx,
+                                  precode_stream_t stream);
+
+// Resident Gram factors of n instances of shape (M, K) (device H [n][K][M], scratch
+// W of the same size, t: K device floats), computed by the kernel the plan runs for
+// that shape and written to fac, slot i at i * (*stride) float2.  *stride = 0 when
+// that kernel does not keep factors (nothing is launched then).
+precode_status_t plan_export_factors(precode_plan_t p, int32_t M, int32_t K, int64_t n,
+                                     const void* H, float2* fac, void* W, const float* t,
+                                     cudaStream_t stream, int* stride);
+
 }  // namespace precode
 
 struct precode_plan_s {

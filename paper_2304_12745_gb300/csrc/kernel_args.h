@@ -29,7 +29,14 @@ constexpr float kDefaultCondThreshold = 16.f;
 enum : uint32_t {
   OPT_STEP_NORMALISED = 1u,  // PGD: eta_l / (max_k sum_j |G_kj|)
   OPT_STALL_COPY = 2u,       // test aid: issue no channel copy, so every copy wait runs out
+  OPT_FAC_EXPORT = 4u,       // write each instance's Gram factor into its slot of fac
 };
+
+// Resident Gram factor of one instance, in float2 units: the kernel's own
+// G'^{-T} = (D H H^H D)^{-T} [KB][KB] (D its per-user power-of-two scales) and
+// one entry whose x is 1 when that inverse is the FP32 path's (0: the instance
+// takes the FP64 path and is set up in full every time).
+__host__ __device__ constexpr int fac_stride(int KB) { return KB * KB + 2; }
 
 struct SolveArgs {
   const float2* H;   // channel base
@@ -50,6 +57,9 @@ struct SolveArgs {
   const int32_t* count;   // this bucket's instance count (device)
   unsigned long long* err;  // device counter of wait timeouts
   uint64_t wait_ns;         // limit of one channel-copy wait (0: the default, 1 s)
+  float2* fac;              // resident Gram factors (kernels with Variant::fac), or nullptr
+  const int64_t* fidx;      // per instance: its factor slot's offset in fac (float2), -1 none;
+                            // with OPT_FAC_EXPORT the slot of instance i is fac + i fac_stride(KB)
 };
 
 }  // namespace precode

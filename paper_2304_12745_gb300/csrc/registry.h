@@ -25,6 +25,7 @@ struct Variant {
                  // tensor-core build pads users (K <= KB) but needs M == MB
   bool f16 = false;  // the layers' contractions as split-FP16 MMAs (scaled instances)
   bool tg = false;   // tcgen05 build: operands in shared memory, accumulators in tensor memory
+  bool fac = false;  // exports / imports resident Gram factors (SolveArgs::fac)
 };
 
 // The instance shapes (M, K) a variant solves.

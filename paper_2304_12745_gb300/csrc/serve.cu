@@ -93,6 +93,8 @@ class Arena {
 struct Channel {
   int M, K, n_sc;
   size_t off, bytes;
+  size_t fac_off = 0, fac_bytes = 0;  // resident Gram factors (fac_stride 0: none)
+  int fac_stride = 0;                 // float2 per subcarrier's slot
 };
 
 struct Job {
@@ -102,6 +104,8 @@ struct Job {
   size_t h_off = 0, h_bytes = 0, w_off = 0, w_bytes = 0, t_off = 0, t_bytes = 0;
   bool resident = false;
   size_t res_h_off = 0;
+  size_t fac_off = 0;  // its channel's factor slots (fac_stride 0: none)
+  int fac_stride = 0;
   double submit_us = 0, start_us = 0, done_us = 0;
   precode_status_t status = PRECODE_PENDING;
   int64_t first = 0;  // index of its first instance inside its launch
@@ -111,6 +115,8 @@ struct Slot {
   cudaStream_t stream = nullptr;
   precode_plan_t plan = nullptr;
   precode_inst_t* h_tbl = nullptr;  // pinned
+  int64_t* h_fidx = nullptr;        // pinned: per instance its factor slot, -1 none
+  int64_t* d_fidx = nullptr;
   // per-instance outputs of the launch, staged in pinned memory: a copy into a
   // caller's pageable buffer would hold the dispatcher until the launch ends
   float* h_obj = nullptr;
@@ -154,7 +160,7 @@ struct precode_server_s {
   std::thread dispatcher;
   // statistics
   uint64_t submitted = 0, completed = 0, rejected = 0, launches = 0;
-  int64_t instances_done = 0;
+  int64_t instances_done = 0, factor_instances = 0;
   double first_submit_us = 0, last_done_us = 0;
   std::vector<double> latencies;  // per completed job (us)
   std::string error;              // first asynchronous CUDA error
@@ -216,7 +222,7 @@ void dispatch_loop(precode_server_t s) {
     char* base = static_cast<char*>(s->arena_base);
     cudaStream_t st = slot->stream;
     cudaError_t e = cudaSuccess;
-    int64_t b = 0;
+    int64_t b = 0, n_fac = 0;
     for (auto& j : batch) {
       j->start_us = t_start;
       const size_t hoff = j->resident ? j->res_h_off : j->h_off;
@@ -233,16 +239,22 @@ void dispatch_loop(precode_server_t s) {
         d.t_off = (int64_t)(j->t_off / 4) + (j->d.t_shared ? 0 : i * kk);
         d.M = (int32_t)mm;
         d.K = (int32_t)kk;
+        slot->h_fidx[b] = j->fac_stride ? (int64_t)(j->fac_off / 8) + i * j->fac_stride : -1;
+        n_fac += j->fac_stride ? 1 : 0;
       }
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(slot->d_tbl, slot->h_tbl, sizeof(precode_inst_t) * n,
                           cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_fac)
+      e = cudaMemcpyAsync(slot->d_fidx, slot->h_fidx, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st);
     precode_status_t ps = PRECODE_OK;
-    if (e == cudaSuccess)
-      ps = precode_solve_varlen(slot->plan, n, static_cast<const precode_inst_t*>(slot->d_tbl),
-                                base, reinterpret_cast<const float*>(base), s->d_step, s->d_lam,
-                                base, slot->d_obj, slot->d_resid, slot->d_flags, st);
+    if (e == cudaSuccess)  // resident channels' instances import their Gram factors
+      ps = solve_varlen_fac(slot->plan, n, static_cast<const precode_inst_t*>(slot->d_tbl), base,
+                            reinterpret_cast<const float*>(base), s->d_step, s->d_lam, base,
+                            slot->d_obj, slot->d_resid, slot->d_flags,
+                            n_fac ? reinterpret_cast<float2*>(base) : nullptr,
+                            n_fac ? slot->d_fidx : nullptr, st);
     for (auto& j : batch) {
       if (e != cudaSuccess || ps != PRECODE_OK) break;
       e = cudaMemcpyAsync(j->d.W_out, base + j->w_off, j->w_bytes, cudaMemcpyDeviceToHost, st);
@@ -261,6 +273,7 @@ void dispatch_loop(precode_server_t s) {
       for (auto& j : batch) j->status = (e != cudaSuccess) ? PRECODE_ECUDA : ps;
     }
     ++s->launches;
+    s->factor_instances += n_fac;
     slot->go = true;
     slot->cv.notify_one();
   }
@@ -330,6 +343,8 @@ void server_free(precode_server_t s) {
     if (sl->stream) cudaStreamDestroy(sl->stream);
     if (sl->done) cudaEventDestroy(sl->done);
     cudaFreeHost(sl->h_tbl);
+    cudaFreeHost(sl->h_fidx);
+    cudaFree(sl->d_fidx);
     cudaFreeHost(sl->h_obj);
     cudaFreeHost(sl->h_resid);
     cudaFreeHost(sl->h_flags);
@@ -401,6 +416,8 @@ precode_status_t precode_serve_create(const precode_serve_desc_t* d, precode_ser
     st = ensure_workspace(sl->plan);
     if (st != PRECODE_OK) return st;
     if (pinned_alloc(&sl->h_tbl, sizeof(precode_inst_t) * cap) != cudaSuccess ||
+        pinned_alloc(&sl->h_fidx, sizeof(int64_t) * cap) != cudaSuccess ||
+        dev_alloc(&sl->d_fidx, sizeof(int64_t) * cap) != cudaSuccess ||
         pinned_alloc(&sl->h_obj, 4 * cap) != cudaSuccess ||
         pinned_alloc(&sl->h_resid, 4 * cap) != cudaSuccess ||
         pinned_alloc(&sl->h_flags, 4 * cap) != cudaSuccess ||
@@ -429,15 +446,72 @@ precode_status_t precode_serve_channel_create(precode_server_t s, int32_t M, int
       return fail(PRECODE_ENOMEM, "precode_serve_channel_create: arena full");
   }
   DeviceGuard g(s->device);
-  const cudaError_t e =
-      cudaMemcpy(static_cast<char*>(s->arena_base) + off, H, bytes, cudaMemcpyHostToDevice);
-  std::lock_guard<std::mutex> lk(s->mu);
+  char* const base = static_cast<char*>(s->arena_base);
+  cudaError_t e = cudaMemcpy(base + off, H, bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(s->mu);
     s->arena.release(off, bytes);
     return cuda_fail(e, "precode_serve_channel_create: copy");
   }
+  Channel ch{M, K, n_sc, off, bytes};
+  // The Gram factors of every subcarrier, kept beside H, when the kernel that
+  // serves (M, K) imports them: computed here by that kernel, once, so that the
+  // jobs on the channel skip the Gram matrix and its inversion.  Without memory
+  // for them (or scratch) the channel is kept without factors.
+  const Variant* v = s->slots[0]->plan->variant_for(M, K);
+  if (v && v->fac && s->desc.mode == PRECODE_LAYER_PROJ) {
+    const size_t fac_bytes = (size_t)n_sc * fac_stride(v->KB) * sizeof(float2);
+    size_t fac_off = 0, w_off = 0, t_off = 0;
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->arena.alloc(fac_bytes, &fac_off)) {
+        if (s->arena.alloc(bytes, &w_off)) {
+          if (s->arena.alloc(4 * (size_t)K, &t_off)) {
+            have = true;
+          } else {
+            s->arena.release(w_off, bytes);
+            s->arena.release(fac_off, fac_bytes);
+          }
+        } else {
+          s->arena.release(fac_off, fac_bytes);
+        }
+      }
+    }
+    if (have) {
+      std::vector<float> ones(K, 1.f);
+      cudaStream_t st = nullptr;
+      int stride = 0;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + t_off, ones.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, st);
+      precode_status_t ps = PRECODE_OK;
+      if (e == cudaSuccess)
+        ps = plan_export_factors(s->slots[0]->plan, M, K, n_sc, base + off,
+                                 reinterpret_cast<float2*>(base + fac_off), base + w_off,
+                                 reinterpret_cast<const float*>(base + t_off), st, &stride);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (st) cudaStreamDestroy(st);
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->arena.release(w_off, bytes);
+      s->arena.release(t_off, 4 * (size_t)K);
+      if (e != cudaSuccess || ps != PRECODE_OK || stride == 0) {
+        s->arena.release(fac_off, fac_bytes);
+        if (e != cudaSuccess || ps != PRECODE_OK) {
+          s->arena.release(off, bytes);
+          return e != cudaSuccess ? cuda_fail(e, "precode_serve_channel_create: factors")
+                                  : fail(ps, "precode_serve_channel_create: factors");
+        }
+      } else {
+        ch.fac_off = fac_off;
+        ch.fac_bytes = fac_bytes;
+        ch.fac_stride = stride;
+      }
+    }
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
   *handle = s->next_channel++;
-  s->channels[*handle] = Channel{M, K, n_sc, off, bytes};
+  s->channels[*handle] = ch;
   return PRECODE_OK;
 }
 
@@ -453,6 +527,7 @@ precode_status_t precode_serve_channel_destroy(precode_server_t s, uint64_t hand
     return true;
   });
   s->arena.release(it->second.off, it->second.bytes);
+  if (it->second.fac_stride) s->arena.release(it->second.fac_off, it->second.fac_bytes);
   s->channels.erase(it);
   return PRECODE_OK;
 }
@@ -479,6 +554,8 @@ precode_status_t precode_serve_submit(precode_server_t s, const precode_job_t* j
       return fail(PRECODE_EINVAL, "precode_serve_submit: job shape differs from its channel");
     j->resident = true;
     j->res_h_off = it->second.off;
+    j->fac_off = it->second.fac_off;
+    j->fac_stride = it->second.fac_stride;
     j->h_bytes = 0;
   }
   const size_t need = ((j->h_bytes + 255) & ~size_t(255)) + ((j->w_bytes + 255) & ~size_t(255)) +
@@ -551,6 +628,7 @@ precode_status_t precode_serve_stats(precode_server_t s, precode_serve_stats_t* 
   const double span = s->last_done_us - s->first_submit_us;
   st->precoders_per_s = span > 0 ? s->instances_done / (span * 1e-6) : 0.0;
   st->instances_done = s->instances_done;
+  st->factor_instances = s->factor_instances;
   st->bytes_in_use = (int64_t)s->arena.used();
   st->bytes_budget = (int64_t)s->arena.size();
   int busy = 0;

@@ -7,9 +7,13 @@ namespace precode {
 
 void register_solve_tch(std::vector<Variant>& v) {
 #define X(NW, MINB)                                                                     \
-  v.push_back(Variant{kModeProj, 8, 64, 4, 8, 8, NW, MINB, true, true, false,           \
-                      (const void*)&solve_tch_kernel<NW, MINB>, SolveTCH<NW>::SMEM_BYTES, \
-                      NW * 32, NW, true, true});
+  {                                                                                     \
+    Variant x{kModeProj, 8, 64, 4, 8, 8, NW, MINB, true, true, false,                   \
+              (const void*)&solve_tch_kernel<NW, MINB>, SolveTCH<NW>::SMEM_BYTES,       \
+              NW * 32, NW, true, true};                                                 \
+    x.fac = true;                                                                       \
+    v.push_back(x);                                                                     \
+  }
   X(4, 3)
   X(4, 4)
 #undef X

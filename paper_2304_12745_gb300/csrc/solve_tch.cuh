@@ -247,9 +247,13 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
   // Returns the instance flags.
   // With BASIS, FP64-path instances run in an orthonormal basis of the channel's
   // row space (S~^T at OFF_ST, `basis` set); else their Q is formed in FP64.
+  // fin: the instance's resident factor slot (its G'^{-T} replaces the Gram matrix
+  // and its inversion when the slot holds the FP32 path's); fout: the slot that
+  // receives them.
   template <bool BASIS = false>
   __device__ static int setup(Ctx& c, const Lane& L, const SolveArgs& A, uint4* xf, WT& w,
-                              float& beta, float4* xraw = nullptr, bool* basis_out = nullptr) {
+                              float& beta, float4* xraw = nullptr, bool* basis_out = nullptr,
+                              const float2* fin = nullptr, float2* fout = nullptr) {
     float2* const Hs = c.Hs;
     uint4* const hh = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HH);
     uint4* const hl = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(Hs) + OFF_HL);
@@ -297,9 +301,24 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
     __syncwarp();
 
     // ---- Gram G'^T (split FP16, as a layer's residual with W = conj(H')), inverse, Q
-    residual_h(L, hh, hl, w, e);
     float gi[4];
-    const bool fast = S::gram_inverse(L, e, A.cond_thr, gi);
+    bool fast;
+    if (fin && fin[KB * KB].x == 1.f) {  // resident: G'^{-T}[g][2q + h] of this channel
+      const float2 f0 = fin[L.g * KB + 2 * L.q], f1 = fin[L.g * KB + 2 * L.q + 1];
+      gi[0] = f0.x;
+      gi[1] = f1.x;
+      gi[2] = f0.y;
+      gi[3] = f1.y;
+      fast = true;
+    } else {
+      residual_h(L, hh, hl, w, e);
+      fast = S::gram_inverse(L, e, A.cond_thr, gi);
+    }
+    if (fout) {
+      fout[L.g * KB + 2 * L.q] = make_float2(gi[0], gi[2]);
+      fout[L.g * KB + 2 * L.q + 1] = make_float2(gi[1], gi[3]);
+      if (L.lane == 0) fout[KB * KB] = make_float2(fast ? 1.f : 0.f, 0.f);
+    }
     float qt[8][4];
     bool singular = false, basis = false;
     if (fast) {
@@ -633,7 +652,15 @@ struct SolveTCH : SolveTC<MODE, NW, false> {
       int fl = 0;
       bool basis = false;  // FP64 path: the layers run in an orthonormal basis
       if constexpr (MODE == kModeProj) {
-        fl = setup<true>(c, L, A, xf, w, beta, nullptr, &basis);
+        const float2* fin = nullptr;
+        float2* fout = nullptr;
+        if (A.fac) {
+          if (A.opts & OPT_FAC_EXPORT)
+            fout = A.fac + inst * (int64_t)fac_stride(KB);
+          else if (A.fidx && A.fidx[inst] >= 0)
+            fin = A.fac + A.fidx[inst];
+        }
+        fl = setup<true>(c, L, A, xf, w, beta, nullptr, &basis, fin, fout);
         f_out = f_res = 1.f / beta;
       } else {
         setup_pgd(c, L, A, xf, w, invLp, ba, f_out, f_res);

@@ -8,9 +8,13 @@ namespace precode {
 
 void register_solve_tcwh(std::vector<Variant>& v) {
 #define X(KW, MB, MINB, EXACT)                                                             \
-  v.push_back(Variant{kModeProj, 8 * KW, MB, KW, 8, 8, KW, MINB, EXACT, true, false,        \
-                      (const void*)&solve_tcwh_kernel<KW, MB, MINB>,                        \
-                      TcwhCfg<KW, MB>::SMEM_BYTES, KW * 32, 1, true, true});
+  {                                                                                        \
+    Variant x{kModeProj, 8 * KW, MB, KW, 8, 8, KW, MINB, EXACT, true, false,               \
+              (const void*)&solve_tcwh_kernel<KW, MB, MINB>, TcwhCfg<KW, MB>::SMEM_BYTES,  \
+              KW * 32, 1, true, true};                                                     \
+    x.fac = true;                                                                          \
+    v.push_back(x);                                                                        \
+  }
   X(4, 256, 2, true)
   X(4, 256, 2, false)
   X(3, 256, 2, false)

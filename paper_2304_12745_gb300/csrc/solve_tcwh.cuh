@@ -418,22 +418,42 @@ struct SolveTCWH : SolveTCW<kModeProj, KW, MB_> {
       }
       __syncthreads();
 
-      // ---- setup on the scaled channel (split TF32, as the TF32 kernel)
+      // ---- setup on the scaled channel (split TF32, as the TF32 kernel); a resident
+      // factor slot holding the FP32 path's G'^{-T} replaces the Gram matrix and its
+      // inversion
       int fl = 0;
+      const float2* fin = nullptr;
+      float2* fout = nullptr;
+      if (A.fac) {
+        if (A.opts & OPT_FAC_EXPORT)
+          fout = A.fac + inst * (int64_t)fac_stride(KB);
+        else if (A.fidx && A.fidx[inst] >= 0)
+          fin = A.fac + A.fidx[inst];
+      }
+      const bool imported = fin && fin[KB * KB].x == 1.f;
+      if (imported) {
+        for (int idx = L.tid; idx < KB * KB; idx += NT) Es[idx] = fin[idx];
+      } else {
 #pragma unroll 1
-      for (int ct = 0; ct < KW; ++ct) {  // G'^T rows 8w .. 8w + 7
-        float e[4];
-        S::template e_tile<true>(L, Hs, w, ct, e);
-        float2* row = Es + (8 * L.w + L.g) * KB + 8 * ct + 2 * L.q;
-        *reinterpret_cast<float4*>(row) = make_float4(e[0], e[2], e[1], e[3]);
+        for (int ct = 0; ct < KW; ++ct) {  // G'^T rows 8w .. 8w + 7
+          float e[4];
+          S::template e_tile<true>(L, Hs, w, ct, e);
+          float2* row = Es + (8 * L.w + L.g) * KB + 8 * ct + 2 * L.q;
+          *reinterpret_cast<float4*>(row) = make_float4(e[0], e[2], e[1], e[3]);
+        }
       }
       __syncthreads();
-      if (K < KB) {  // padded users: unit Gram diagonal
+      if (K < KB && !imported) {  // padded users: unit Gram diagonal
         if (L.tid >= K && L.tid < KB) Es[L.tid * KB + L.tid] = make_float2(1.f, 0.f);
         __syncthreads();
       }
       bool singular = false, basis = false;
-      if (!S::gj_fp32(L, Es, dsc, rowp, colp, A.cond_thr)) {
+      const bool fast = imported || S::gj_fp32(L, Es, dsc, rowp, colp, A.cond_thr);
+      if (fout) {
+        for (int idx = L.tid; idx < KB * KB; idx += NT) fout[idx] = Es[idx];
+        if (L.tid == 0) fout[KB * KB] = make_float2(fast ? 1.f : 0.f, 0.f);
+      }
+      if (!fast) {
         // FP64 path: the layers run split TF32 in an orthonormal basis of the
         // (scaled) channel's row space, S~^T in Es (S::basis_fp64)
         fl = S::basis_fp64(L, K, Hs, Es, gf, A64, reinterpret_cast<double*>(r64),

@@ -9,6 +9,7 @@ void register_solve_tg(std::vector<Variant>& v) {
   Variant x{kModeProj, 32, 256, 4, 8, 8, TgCfg::NT / 32, 1, false, true, false,
             (const void*)&solve_tg_kernel<1>, TgCfg::SMEM_BYTES, TgCfg::NT, 1, true, true};
   x.tg = true;
+  x.fac = true;
   v.push_back(x);
 }
 

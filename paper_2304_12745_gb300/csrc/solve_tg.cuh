@@ -623,30 +623,54 @@ struct SolveTG {
       __syncthreads();
       build_hr(L, Hs, dgs, sm);
 
-      // ---- Gram matrix G' = H' H'^H as a residual with A = B = H_R
+      // ---- Gram matrix G' = H' H'^H as a residual with A = B = H_R (or the
+      // resident factor slot's G'^{-T}, when it holds the FP32 path's)
       int fl = 0;
       bool ok = true;
-      publish_smem();
-      if (L.tid == 0) {
-        issue_residual(tm, s_hr, s_hr);
-        tc5::commit(smem_addr(mbar));
+      const float2* fin = nullptr;
+      float2* fout = nullptr;
+      if (A.fac) {
+        if (A.opts & OPT_FAC_EXPORT)
+          fout = A.fac + inst * (int64_t)fac_stride(KB);
+        else if (A.fidx && A.fidx[inst] >= 0)
+          fin = A.fac + A.fidx[inst];
       }
-      ok = mma_wait(mbar, mphase, lim);
-      stage_e(L, tm_q, Sg);
+      const bool imported = fin && fin[KB * KB].x == 1.f;
+      if (!imported) {
+        publish_smem();
+        if (L.tid == 0) {
+          issue_residual(tm, s_hr, s_hr);
+          tc5::commit(smem_addr(mbar));
+        }
+        ok = mma_wait(mbar, mphase, lim);
+        stage_e(L, tm_q, Sg);
+      }
       ok = __syncthreads_and(ok) != 0;
       bool singular = false, basis = false;
       {
         // thread (i, j_c) takes G'^T[i][j_c] = conj(G'[i][j_c]); padded users get a unit pivot
         const int i = L.tid >> 3, j0 = L.tid & 7;
         float2 a[4];
+        bool fast = imported;
+        if (imported) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int j = j0 + 8 * c;
-          const float gr = dp(Sg, i, j) + dp(Sg, i + 32, j + 32);
-          const float gi = dp(Sg, i + 32, j) - dp(Sg, i, j + 32);
-          a[c] = (i >= K && i == j) ? make_float2(1.f, 0.f) : make_float2(gr, -gi);
+          for (int c = 0; c < 4; ++c) a[c] = fin[i * KB + j0 + 8 * c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int j = j0 + 8 * c;
+            const float gr = dp(Sg, i, j) + dp(Sg, i + 32, j + 32);
+            const float gi = dp(Sg, i + 32, j) - dp(Sg, i, j + 32);
+            a[c] = (i >= K && i == j) ? make_float2(1.f, 0.f) : make_float2(gr, -gi);
+          }
+          fast = ok && gj_regs(L, a, dsc, rowpub, colpub, A.cond_thr);
         }
-        if (ok && gj_regs(L, a, dsc, rowpub, colpub, A.cond_thr)) {
+        if (fout && ok) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) fout[i * KB + j0 + 8 * c] = a[c];
+          if (L.tid == 0) fout[KB * KB] = make_float2(fast ? 1.f : 0.f, 0.f);
+        }
+        if (fast) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) Es[i * KB + j0 + 8 * c] = a[c];
         } else if (ok) {

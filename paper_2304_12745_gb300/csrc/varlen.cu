@@ -86,7 +86,8 @@ int bucketize_grid(precode_plan_t p) { return 2 * p->num_sms; }
 
 void fill_args(precode_plan_t p, VarlenCall& call, const precode_inst_t* tbl, int64_t B,
                const void* H, const float* t, const float* step, const float* lam, void* W,
-               float* obj, float* resid, int32_t* flags) {
+               float* obj, float* resid, int32_t* flags, float2* fac = nullptr,
+               const int64_t* fidx = nullptr) {
   const int nb = (int)p->buckets.size();
   call.bt.n = nb;
   call.bt.mode = p->mode;
@@ -122,6 +123,8 @@ void fill_args(precode_plan_t p, VarlenCall& call, const precode_inst_t* tbl, in
     A.opts = p->kernel_opts();
     A.wait_ns = p->wait_ns;
     A.tbl = call.tbl;
+    A.fac = p->buckets[i].v->fac ? fac : nullptr;
+    A.fidx = p->buckets[i].v->fac ? fidx : nullptr;
     A.index = p->d_index + (size_t)i * p->max_instances;
     A.count = p->d_count + i;
     A.err = p->d_err;
@@ -216,6 +219,18 @@ extern "C" precode_status_t precode_solve_varlen(precode_plan_t p, int64_t B,
                                                  const float* lam, void* W, float* obj,
                                                  float* resid, int32_t* flags,
                                                  precode_stream_t stream) {
+  return precode::solve_varlen_fac(p, B, tbl, H, t, step, lam, W, obj, resid, flags, nullptr,
+                                   nullptr, stream);
+}
+
+// The uneven-batch solve with optional resident Gram factors: fidx[b] >= 0 names
+// instance b's factor slot in fac (float2 offset), for the buckets whose kernel
+// imports them.
+precode_status_t precode::solve_varlen_fac(precode_plan_t p, int64_t B, const precode_inst_t* tbl,
+                                           const void* H, const float* t, const float* step,
+                                           const float* lam, void* W, float* obj, float* resid,
+                                           int32_t* flags, float2* fac, const int64_t* fidx,
+                                           precode_stream_t stream) {
   if (!p) return fail(PRECODE_EINVAL, "precode_solve_varlen: NULL plan");
   if (B < 0 || B > p->max_instances)
     return fail(PRECODE_EINVAL, "precode_solve_varlen: B outside [0, max_instances]");
@@ -232,7 +247,7 @@ extern "C" precode_status_t precode_solve_varlen(precode_plan_t p, int64_t B,
   precode_status_t st = ensure_workspace(p);
   if (st != PRECODE_OK) return st;
   VarlenCall call;
-  fill_args(p, call, tbl, B, H, t, step, lam, W, obj, resid, flags);
+  fill_args(p, call, tbl, B, H, t, step, lam, W, obj, resid, flags, fac, fidx);
   cudaStream_t s = (cudaStream_t)stream;
   if (p->flags & PRECODE_PLAN_GRAPHS) {
     if (!p->graph_exec) {

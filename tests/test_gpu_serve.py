@@ -27,6 +27,7 @@ def server(request):
     else:  # as bench.py's serving workload builds it
         s = Server(capi.LAYER_PROJ, mu, shapes=BENCH_SHAPES, n_slots=6, max_batch_instances=65536,
                    device_mem_budget=4 << 30, flags=capi.PLAN_TENSOR_CORES)
+    s.kind = request.param
     yield s, mu
     s.close()
 
@@ -97,6 +98,40 @@ def test_resident_channel_matches_copied_channel(server):
     a.wait()
     b.wait()
     assert np.array_equal(a.W, b.W)
+    s.release_channel(cid)
+
+
+@pytest.mark.parametrize("M,K", [(64, 8), (128, 16), (256, 32), (256, 20)])
+def test_resident_factors_bitwise_and_parity(orc, server, M, K):
+    """A resident channel on the tensor-core buckets keeps each subcarrier's Gram
+    inverse (split-FP16 K = 8, multi-warp split-FP16 and tcgen05 kernels): jobs on it
+    give bitwise the copied channel's results, match the oracle, and are counted as
+    launched with factors.  Every fourth subcarrier has a near-collinear user pair
+    (FP64 path: no factor, set up in full by every job)."""
+    from paper_2304_12745_gb300 import capi
+    s, mu = server
+    if s.kind != "tensor_core_buckets":  # the FFMA buckets keep no factors
+        pytest.skip("the tensor-core bucket server only")
+    n = 96
+    H = ch.rician_ula(n, K, M, seed=300 + K)
+    rs = np.random.default_rng(301)
+    for b in range(0, n, 4):
+        H[b, 1] = H[b, 0] + (1e-4 * (rs.standard_normal(M) + 1j * rs.standard_normal(M))).astype(np.complex64)
+    t = np.ones(K, np.float32)
+    cid = s.channel(H)
+    f0 = s.stats()["factor_instances"]
+    a = s.submit(H, t)
+    b = s.submit(None, t, channel=cid, M=M, K=K, n_sc=n)
+    a.wait()
+    b.wait()
+    assert s.stats()["factor_instances"] - f0 == n
+    assert np.array_equal(a.W, b.W) and np.array_equal(a.obj, b.obj) and np.array_equal(a.flags, b.flags)
+    assert np.all(b.flags[0::4] == capi.F_FP64_CHOL) and np.all((b.flags == 0) | (b.flags == capi.F_FP64_CHOL))
+    Wo, oo, _, so = orc.batch_forward(1, H.astype(np.complex128), np.ones((n, K)),
+                                      mu.astype(np.float64), nthreads=8)
+    err = np.linalg.norm((b.W - Wo).reshape(n, -1), axis=1) / np.linalg.norm(Wo.reshape(n, -1), axis=1)
+    assert err.max() <= 1e-4, err.max()
+    assert np.max(np.abs(b.obj - oo) / oo) <= 1e-5
     s.release_channel(cid)
 
 
