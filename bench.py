@@ -88,9 +88,19 @@ def mma_per_instance_f16(T: int) -> tuple:
     return 48 * T + 24 + 24 + 48, 0
 
 
+_PEAK = {"sms": 152, "mhz": 2070.0, "source": "152 SMs (GB300) x 128 FP32 lanes x 2 flop x 2,070 MHz"}
+
+
+def set_fp32_peak(sms: int, mhz: float, source: str):
+    """The FP32 FMA peak every roofline fraction of the run uses: the device's SM
+    count (queried) x 128 FP32 lanes x 2 flop x the SM clock (the median sampled
+    under load during the timed region, else the maximum clock)."""
+    _PEAK.update(sms=int(sms), mhz=float(mhz), source=source)
+
+
 def fp32_peak_tflops() -> float:
-    """152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz (maximum SM clock)."""
-    return 152 * 128 * 2 * 2.070e9 / 1e12
+    """SM count x 128 FP32 lanes x 2 flop x SM clock (see set_fp32_peak)."""
+    return _PEAK["sms"] * 128 * 2 * _PEAK["mhz"] * 1e6 / 1e12
 
 
 def measured_peaks():
@@ -157,6 +167,46 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": float(np.median([r[0] for r in load])), "sm_max_mhz": max(r[1] for r in rows),
                 "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+def host_link_peak(torch, nbytes: int = 268 << 20, reps: int = 5) -> dict:
+    """Copy-engine bandwidth between page-locked host memory and the device, the
+    ceiling of the end-to-end leg: host->device alone, device->host alone, and both
+    directions at once on two streams (best of `reps`, CUDA events)."""
+    src_h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dst_h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    src_d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dst_d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(h2d: bool, d2h: bool) -> float:
+        best = float("inf")
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s1.wait_event(e0)
+            s2.wait_event(e0)
+            if h2d:
+                with torch.cuda.stream(s1):
+                    dst_d.copy_(src_h, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    dst_h.copy_(src_d, non_blocking=True)
+            torch.cuda.current_stream().wait_stream(s1)
+            torch.cuda.current_stream().wait_stream(s2)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return (int(h2d) + int(d2h)) * nbytes / best / 1e9
+
+    out = {"h2d_gbs": run(True, False), "d2h_gbs": run(False, True), "both_gbs": run(True, True),
+           "bytes_per_direction": nbytes,
+           "how": "torch copies between page-locked host and device buffers, one stream per "
+                  "direction, best of %d, CUDA events" % reps}
+    del src_h, dst_h, src_d, dst_d
+    return out
 
 
 def dist_env():
@@ -548,6 +598,51 @@ def bench_serve(capi, mu, duration_s: float = 2.0, n_runs: int = 3):
             "note": "p50 / p99 / precoders per s: median over the runs; max: over all runs"}
 
 
+def bench_resident(capi, mu, reps: int = 20) -> dict:
+    """Jobs on resident channels (H and each subcarrier's Gram factors kept on the
+    device) against the same jobs with H copied in: median latency of a job alone on
+    the server (submit -> results in host memory), 1,024 subcarriers."""
+    from paper_2304_12745_gb300.serving import JobHandle, Server, pinned, touch_by_device
+    shapes = [(m, k) for m in (64, 128, 256) for k in (8, 16, 24, 32)]
+    s = Server(capi.LAYER_PROJ, mu, shapes=shapes, n_slots=2, max_batch_instances=65536,
+               device_mem_budget=8 << 30, flags=capi.PLAN_TENSOR_CORES)
+    out = {}
+    for M, K in ((64, 8), (256, 32)):
+        n = 1024
+        H = ch.rician_ula(n, K, M, seed=77 + K)
+        cid = s.channel(H)
+        # page-locked job buffers, touched by the device once (as poisson_load's)
+        Hp = pinned(H.size, np.complex64).reshape(H.shape)
+        Hp[:] = H
+        Wp = pinned(H.size, np.complex64).reshape(H.shape)
+        ones = pinned(K, np.float32)
+        ones[:] = 1.0
+        touch_by_device(Hp, Wp, ones)
+        lat = {"copied": [], "resident": []}
+        for r in range(reps + 2):
+            for kind in ("copied", "resident"):
+                arrays = {"H": Hp, "t": ones, "W": Wp, "obj": np.empty(n, np.float32),
+                          "resid": None, "flags": np.empty(n, np.int32)}
+                job = capi.Job(M, K, n, capi.ptr(Hp) if kind == "copied" else None, capi.ptr(ones), 1,
+                               capi.ptr(Wp), capi.ptr(arrays["obj"]), None, capi.ptr(arrays["flags"]),
+                               0 if kind == "copied" else cid)
+                res = JobHandle(s, capi.precode_serve_submit(s.handle, job), arrays).wait()
+                if r >= 2:
+                    lat[kind].append(res.latency_us / 1e3)
+        out[f"{M}x{K}x{n}"] = {"copied_ms": float(np.median(lat["copied"])),
+                               "resident_ms": float(np.median(lat["resident"])),
+                               "h_bytes": int(H.nbytes)}
+        s.release_channel(cid)
+    st = s.stats()
+    s.close()
+    out["factor_instances"] = int(st["factor_instances"])
+    out["note"] = ("resident: H and its Gram factors stay on the device, so a job skips the "
+                   "host->device copy of H and the kernels skip the Gram matrix and its "
+                   "inversion; page-locked host buffers; median of %d jobs alone on the "
+                   "server" % reps)
+    return out
+
+
 def run_bucket(args):
     """One bucket alone (profiling aid): B Rician channels C^{K x M} (seed 5), T = 10
     projected layers, autotuned plan; two solves, then one inside an NVTX range."""
@@ -733,6 +828,12 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * B / (ms_per_step / 1e3)
     clocks = clk.summary()
+    props = torch.cuda.get_device_properties(local)
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    run_mhz = (clocks or {}).get("sm_mhz") or max_mhz
+    set_fp32_peak(props.multi_processor_count, run_mhz,
+                  f"{props.multi_processor_count} SMs (queried) x 128 FP32 lanes x 2 flop x "
+                  f"{run_mhz:.0f} MHz (median SM clock sampled under load; maximum {max_mhz:.0f})")
     flags_np = fl.cpu().numpy()
     obj_np = obj.cpu().numpy()
     res_np = res.cpu().numpy()
@@ -746,7 +847,7 @@ def main():
     peaks = measured_peaks()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
-            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.070 GHz",
+            "peak_source": "derived: " + _PEAK["source"],
             "kernel_ms": kern_ms,
             "flop_per_instance": fpi,
             "hbm": {"achieved_gbs": hbm_bytes / (kern_ms / 1e3) / 1e9,
@@ -818,9 +919,15 @@ def main():
         tt = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
+    h2d_b, d2h_b = int(H.nbytes + t.nbytes + 4 * T), int(H.nbytes + 3 * 4 * B)
+    link = host_link_peak(torch)
     line["e2e"] = {"value": world * B / e2e_s, "unit": UNIT,
-                   "h2d_bytes_per_step": int(H.nbytes + t.nbytes + 4 * T),
-                   "d2h_bytes_per_step": int(H.nbytes + 3 * 4 * B),
+                   "h2d_bytes_per_step": h2d_b,
+                   "d2h_bytes_per_step": d2h_b,
+                   "host_link": link,
+                   "host_link_frac": (h2d_b + d2h_b) / e2e_s / 1e9 / link["both_gbs"],
+                   "host_link_frac_source": "bytes moved per step / step time, against the "
+                                            "measured both-directions copy bandwidth",
                    "api": "precode_solve_host (pinned host buffers: the zero-copy kernel reads H and "
                           "writes W over the host link; pageable buffers would take the staged "
                           "copy pipeline)"}
@@ -847,6 +954,7 @@ def main():
         line["train"], mu_learned = bench_train(torch, capi)
         torch.cuda.empty_cache()
         line["serving"] = bench_serve(capi, mu_learned)
+        line["serving"]["resident"] = bench_resident(capi, mu_learned)
         torch.cuda.empty_cache()
         line["paper_setting"] = bench_paper_setting(torch, capi)
     if rank == 0:

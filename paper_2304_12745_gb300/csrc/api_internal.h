@@ -63,12 +63,17 @@ struct Bucket {
 };
 
 // precode_solve_varlen with resident Gram factors: fidx[b] >= 0 is the float2
-// offset in fac of instance b's factor slot (nullptr fac / fidx: none).
+// offset in fac of instance b's factor slot (nullptr fac / fidx: none).  bucket_n
+// (host, one count per plan bucket as bucket_of assigns them, or nullptr): empty
+// buckets launch nothing and the others no more blocks than they need (ignored
+// with PRECODE_PLAN_GRAPHS).
 precode_status_t solve_varlen_fac(precode_plan_t p, int64_t B, const precode_inst_t* tbl,
                                   const void* H, const float* t, const float* step,
                                   const float* lam, void* W, float* obj, float* resid,
                                   int32_t* flags, float2* fac, const int64_t* fidx,
-                                  precode_stream_t stream);
+                                  precode_stream_t stream, const int64_t* bucket_n);
+// The plan bucket the device bucketing assigns to a valid (M, K), or -1.
+int bucket_of(precode_plan_t p, int M, int K);
 
 // Resident Gram factors of n instances of shape (M, K) (device H [n][K][M], scratch
 // W of the same size, t: K device floats), computed by the kernel the plan runs for

@@ -223,8 +223,11 @@ void dispatch_loop(precode_server_t s) {
     cudaStream_t st = slot->stream;
     cudaError_t e = cudaSuccess;
     int64_t b = 0, n_fac = 0;
+    std::vector<int64_t> bucket_n(slot->plan->buckets.size(), 0);
     for (auto& j : batch) {
       j->start_us = t_start;
+      const int bk = bucket_of(slot->plan, j->d.M, j->d.K);
+      if (bk >= 0) bucket_n[bk] += j->n;
       const size_t hoff = j->resident ? j->res_h_off : j->h_off;
       if (!j->resident && e == cudaSuccess)
         e = cudaMemcpyAsync(base + hoff, j->d.H, j->h_bytes, cudaMemcpyHostToDevice, st);
@@ -254,7 +257,7 @@ void dispatch_loop(precode_server_t s) {
                             reinterpret_cast<const float*>(base), s->d_step, s->d_lam, base,
                             slot->d_obj, slot->d_resid, slot->d_flags,
                             n_fac ? reinterpret_cast<float2*>(base) : nullptr,
-                            n_fac ? slot->d_fidx : nullptr, st);
+                            n_fac ? slot->d_fidx : nullptr, st, bucket_n.data());
     for (auto& j : batch) {
       if (e != cudaSuccess || ps != PRECODE_OK) break;
       e = cudaMemcpyAsync(j->d.W_out, base + j->w_off, j->w_bytes, cudaMemcpyDeviceToHost, st);

@@ -68,6 +68,28 @@ struct VarlenCall {
 
 }  // namespace
 
+// The bucket bucketize_kernel assigns to a valid (M, K) on this plan, on the host
+// (the same rule: the exact bucket of the shape, else the smallest generic bucket
+// that holds it, a tensor-core build that needs M == MB winning ties); -1 if none.
+int bucket_of(precode_plan_t p, int M, int K) {
+  const int nb = (int)p->buckets.size();
+  for (int i = 0; i < nb; ++i) {
+    const Variant* v = p->buckets[i].v;
+    if (v->exact && p->buckets[i].M == M && p->buckets[i].K == K) return i;
+  }
+  int s = -1, best = 1 << 30;
+  for (int i = 0; i < nb; ++i) {
+    const Variant* v = p->buckets[i].v;
+    const int mfix = (!v->exact && v->tc) ? 1 : 0;
+    if (!v->exact && v->KB >= K && v->MB >= M && (!mfix || v->MB == M) &&
+        2 * v->KB * v->MB - mfix < best) {
+      best = 2 * v->KB * v->MB - mfix;
+      s = i;
+    }
+  }
+  return s;
+}
+
 precode_status_t ensure_workspace(precode_plan_t p) {
   if (p->d_index) return PRECODE_OK;
   const size_t nb = p->buckets.size();
@@ -220,7 +242,7 @@ extern "C" precode_status_t precode_solve_varlen(precode_plan_t p, int64_t B,
                                                  float* resid, int32_t* flags,
                                                  precode_stream_t stream) {
   return precode::solve_varlen_fac(p, B, tbl, H, t, step, lam, W, obj, resid, flags, nullptr,
-                                   nullptr, stream);
+                                   nullptr, stream, nullptr);
 }
 
 // The uneven-batch solve with optional resident Gram factors: fidx[b] >= 0 names
@@ -230,7 +252,7 @@ precode_status_t precode::solve_varlen_fac(precode_plan_t p, int64_t B, const pr
                                            const void* H, const float* t, const float* step,
                                            const float* lam, void* W, float* obj, float* resid,
                                            int32_t* flags, float2* fac, const int64_t* fidx,
-                                           precode_stream_t stream) {
+                                           precode_stream_t stream, const int64_t* bucket_n) {
   if (!p) return fail(PRECODE_EINVAL, "precode_solve_varlen: NULL plan");
   if (B < 0 || B > p->max_instances)
     return fail(PRECODE_EINVAL, "precode_solve_varlen: B outside [0, max_instances]");
@@ -268,7 +290,11 @@ precode_status_t precode::solve_varlen_fac(precode_plan_t p, int64_t B, const pr
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "precode_solve_varlen: bucketize launch");
   for (size_t i = 0; i < p->buckets.size(); ++i) {
-    st = launch_variant(*p->buckets[i].v, p->device, p->num_sms, call.args[i], -1, s);
+    // with the buckets' instance counts known on the host: no launch for an empty
+    // bucket, and no more blocks than its instances need
+    if (bucket_n && bucket_n[i] == 0) continue;
+    st = launch_variant(*p->buckets[i].v, p->device, p->num_sms, call.args[i],
+                        bucket_n ? bucket_n[i] : -1, s);
     if (st != PRECODE_OK) return st;
   }
   return PRECODE_OK;

@@ -35,6 +35,9 @@ def test_mma_counts():
 
 def test_fp32_peak():
     assert bench.fp32_peak_tflops() == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
+    bench.set_fp32_peak(148, 1965.0, "test")
+    assert bench.fp32_peak_tflops() == pytest.approx(148 * 128 * 2 * 1.965e9 / 1e12)
+    bench.set_fp32_peak(152, 2070.0, "default")
 
 
 def _summary(lines):

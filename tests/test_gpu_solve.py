@@ -225,6 +225,9 @@ def test_pgd_step_normalised_on_lognormal(pc, orc, tc):
         Wo[b] = orc.ufpgd_forward(Hb, t[b], step.astype(np.float64) / Lb, lam)
     e = rel_fro(gpu[0], Wo)
     assert e.max() <= W_TOL
+    # the objective ||W||_{2,1} (sum of the antenna columns' norms) of the oracle's W
+    oo = np.sqrt((np.abs(Wo) ** 2).sum(axis=1)).sum(axis=1)
+    assert np.max(np.abs(gpu[1] - oo) / oo) <= OBJ_TOL
 
 
 # ---------------------------------------------------------------- batch mechanics
