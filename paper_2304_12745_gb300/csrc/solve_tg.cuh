@@ -70,9 +70,9 @@ struct TgCfg {
   static constexpr int OFF_NP = OFF_FS + 8 * 4 * FSS * 4;  // column-norm partials [4 row groups][256]
   static constexpr int OFF_FAC = OFF_NP + 4096;          // shrink factors [256]
   static constexpr int OFF_S64 = OFF_FAC + 1024;         // FP64 pivots: double2[32] x 2, double[32]
-  // t[32] dsc[32] misc[8] wred[8] fsc[32] dd[32] dgs[32] rowpub[2][32] colpub[2][32] (float2)
+  // t[32] dsc[32] misc[8] wred[8] fsc[32] dd[32] dgs[32] rowpub[2][2][32] colpub[2][2][32] (float2)
   static constexpr int OFF_SC = OFF_S64 + 1280;
-  static constexpr int SC_BYTES = 1728;
+  static constexpr int SC_BYTES = 2752;
   static constexpr int OFF_DINV = OFF_SC + SC_BYTES;
   static constexpr int OFF_BAR = OFF_DINV + 128;         // copy barrier, MMA barrier, TMEM address
   static constexpr int SMEM_BYTES = OFF_BAR + 32;
@@ -261,12 +261,22 @@ struct SolveTG {
   // k + 32 take back), and the thread's entries of A_F hi / lo.  The warp's rows
   // of E meet in Ec (warp-synchronous): row operands are broadcasts, G'^{-T} rows
   // consecutive words.
+  // With tdiag (the start, E_0 = -diag(t')): F_0[k][j] = -t'_k G'^{-T}[k][j] directly.
   __device__ __forceinline__ static void make_af(const Lane& L, const float (&er)[4], const float (&ei)[4],
                                                  bool basis, const float* dd, const float2* G, float2* Ec,
-                                                 float* fsc, float* Fs, unsigned char* sm) {
+                                                 float* fsc, float* Fs, unsigned char* sm,
+                                                 const float* tdiag = nullptr) {
     const int k0 = 4 * L.w, j = L.lane;
     float fr[4], fi[4];
-    if (basis) {
+    if (tdiag) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 g = G[(k0 + i) * KB + j];
+        const float tk = tdiag[k0 + i];
+        fr[i] = -tk * g.x;
+        fi[i] = -tk * g.y;
+      }
+    } else if (basis) {
       const float d = dd[j];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -393,13 +403,27 @@ struct SolveTG {
     return sqrtf(r);
   }
 
+  // One entry's Gauss-Jordan step at pivot p: v = A[i][j], c = A[i][p], b = A[p][j],
+  // inv = 1 / A[p][p]; the pivot entry, the pivot row, the pivot column or the rest
+  // (a - (c / d) b), selected without divergence.
+  __device__ __forceinline__ static float2 gj_entry(float2 v, float2 c, float2 b, float inv, bool rowp,
+                                                    bool colp) {
+    const float tr = c.x * inv, ti = c.y * inv;
+    const float2 g = make_float2(v.x - (tr * b.x - ti * b.y), v.y - (tr * b.y + ti * b.x));
+    const float2 rowv = make_float2(v.x * inv, v.y * inv);
+    const float2 colv = make_float2(-c.x * inv, -c.y * inv);
+    return rowp ? (colp ? make_float2(inv, 0.f) : rowv) : (colp ? colv : g);
+  }
+
   // Equilibrated Gauss-Jordan inverse (no pivoting; pivot spread max d / min d of
   // the equilibrated matrix is the condition estimate) with the matrix in
   // registers: thread (i = tid / 8, columns j_c = tid % 8 + 8 c) holds a[c] =
-  // G'^T[i][j_c] on entry and G'^{-T}[i][j_c] on a true return.  Pivot p's row and
-  // column are published by their owners into one of two buffers (alternating),
-  // one barrier a pivot.  The per-entry arithmetic is that of the multi-warp
-  // kernels' shared-memory version (a - (c / d) b for the rest of the matrix).
+  // G'^T[i][j_c] on entry and G'^{-T}[i][j_c] on a true return.  Two pivots per
+  // barrier: the rows and columns of pivots p and p + 1 are published by their
+  // owners (two alternating buffers), and each thread replays pivot p on the
+  // entries pivot p + 1 reads (row p + 1 at its columns, its row's column p + 1, the
+  // pivot) before applying p + 1 to its own: the entries of the one-pivot-a-step
+  // elimination, in half the barriers.
   __device__ static bool gj_regs(const Lane& L, float2 (&a)[4], float* dsc, float2* rowpub,
                                  float2* colpub, float cond_thr) {
     const int i = L.tid >> 3, j0 = L.tid & 7;
@@ -422,38 +446,57 @@ struct SolveTG {
     bool fail = false;
     float dmin = FLT_MAX, dmax = 0.f;
 #pragma unroll 1
-    for (int p = 0; p < KB; ++p) {
-      float2* const rp = rowpub + KB * (p & 1);
-      float2* const cp = colpub + KB * (p & 1);
-      if (i == p)
+    for (int p = 0; p < KB; p += 2) {
+      const int q = p + 1;
+      float2* const rp = rowpub + 2 * KB * ((p >> 1) & 1);  // rows p, q: [2][KB]
+      float2* const cp = colpub + 2 * KB * ((p >> 1) & 1);  // columns p, q: [2][KB]
+      if (i == p || i == q)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) rp[j0 + 8 * c] = a[c];
-      if (j0 == (p & 7)) {
+        for (int c = 0; c < 4; ++c) rp[(i - p) * KB + j0 + 8 * c] = a[c];
+      if (j0 == (p & 7) || j0 == (q & 7)) {
+        const int cc = (j0 == (p & 7)) ? (p >> 3) : (q >> 3);
         float2 v = a[0];
 #pragma unroll
         for (int c = 1; c < 4; ++c)
-          if (c == (p >> 3)) v = a[c];
-        cp[i] = v;
+          if (c == cc) v = a[c];
+        cp[(j0 == (p & 7) ? 0 : KB) + i] = v;
       }
       __syncthreads();
-      const float d = rp[p].x;
-      const float2 ci = cp[i];
-      float2 rb[4];
+      const float2* const Rp = rp;
+      const float2* const Rq = rp + KB;
+      // pivot p
+      const float dp = Rp[p].x;
+      fail |= !(dp > 0.f) || !(dp < FLT_MAX);
+      dmin = fminf(dmin, dp);
+      dmax = fmaxf(dmax, dp);
+      const float invp = __frcp_rn(dp);
+      const float2 cip = cp[i], ciq = cp[KB + i];
+      float2 rpb[4], rqb[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) rb[c] = rp[j0 + 8 * c];
-      fail |= !(d > 0.f) || !(d < FLT_MAX);
-      dmin = fminf(dmin, d);
-      dmax = fmaxf(dmax, d);
-      const float inv = __frcp_rn(d);
-      const float tr = ci.x * inv, ti = ci.y * inv;
+      for (int c = 0; c < 4; ++c) {
+        rpb[c] = Rp[j0 + 8 * c];
+        rqb[c] = Rq[j0 + 8 * c];
+      }
+      const float2 aqp = Rq[p], apq = Rp[q], aqq = Rq[q];
+      // what pivot q reads, after pivot p: its pivot, its row at my columns, my row's column q
+      const float dq = gj_entry(aqq, aqp, apq, invp, false, false).x;
+      const float2 ciq1 = gj_entry(ciq, cip, apq, invp, i == p, false);
+      float2 rq1[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {  // all four cases formed, one selected (no divergence)
+      for (int c = 0; c < 4; ++c) {
         const int j = j0 + 8 * c;
-        const float2 b = rb[c], v = a[c];
-        const float2 g = make_float2(v.x - (tr * b.x - ti * b.y), v.y - (tr * b.y + ti * b.x));
-        const float2 rowv = make_float2(v.x * inv, v.y * inv);
-        const float2 colv = make_float2(-ci.x * inv, -ci.y * inv);
-        a[c] = (i == p) ? ((j == p) ? make_float2(inv, 0.f) : rowv) : ((j == p) ? colv : g);
+        rq1[c] = gj_entry(rqb[c], aqp, rpb[c], invp, false, j == p);
+        a[c] = gj_entry(a[c], cip, rpb[c], invp, i == p, j == p);
+      }
+      // pivot q
+      fail |= !(dq > 0.f) || !(dq < FLT_MAX);
+      dmin = fminf(dmin, dq);
+      dmax = fmaxf(dmax, dq);
+      const float invq = __frcp_rn(dq);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = j0 + 8 * c;
+        a[c] = gj_entry(a[c], ciq1, rq1[c], invq, i == q, j == q);
       }
     }
     const bool ok = !fail && !(dmax > cond_thr * dmin);
@@ -530,7 +573,7 @@ struct SolveTG {
     float* const dd = fsc + KB;
     float* const dgs = dd + KB;
     float2* const rowpub = reinterpret_cast<float2*>(dgs + KB);
-    float2* const colpub = rowpub + 2 * KB;
+    float2* const colpub = rowpub + 4 * KB;
     float* const dinv = reinterpret_cast<float*>(sm + C::OFF_DINV);
     uint64_t* const cbar = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
     uint64_t* const mbar = cbar + 1;
@@ -717,7 +760,7 @@ struct SolveTG {
               ei[i] = 0.f;
             }
           }
-          make_af(L, er, ei, basis, dd, Es, Ec, fsc, Fs, sm);
+          make_af(L, er, ei, basis, dd, Es, Ec, fsc, Fs, sm, basis ? nullptr : tks);
         }
         publish_smem();
         if (L.tid == 0) {
