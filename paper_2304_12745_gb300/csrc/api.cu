@@ -73,6 +73,7 @@ const std::vector<Variant>& variants() {
     register_solve_tc(r);
     register_solve_tcwh(r);  // before the TF32 builds: the projected layer's default there
     register_solve_tg(r);
+    register_solve_tgt(r);
     register_solve_tcw_64(r);
     register_solve_tcw_128(r);
     register_solve_tcw_256(r);
@@ -577,7 +578,9 @@ precode_status_t precode_plan_describe(precode_plan_t p, int32_t M, int32_t K, c
   if (!p || !buf || len == 0) return fail(PRECODE_EINVAL, "precode_plan_describe: bad argument");
   const Variant* v = p->variant_for(M, K);
   if (!v) return fail(PRECODE_EINVAL, "precode_plan_describe: shape not covered by the plan");
-  if (v->tg)
+  if (v->tgt)
+    std::snprintf(buf, len, "solve_tgt_kernel<%d>", v->minb);
+  else if (v->tg)
     std::snprintf(buf, len, "solve_tg_kernel<%d>", v->minb);
   else if (v->f16 && v->exact && v->KB == 8 && v->MB == 64 && v->mode == PRECODE_LAYER_PGD)
     std::snprintf(buf, len, "solve_tch_kernel<%d, %d, 0, 0>", v->NW, v->minb);

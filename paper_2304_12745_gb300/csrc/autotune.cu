@@ -42,7 +42,7 @@ __global__ void fill_const(float* p, int64_t n, float v) {
 std::string variant_key(const Variant& v) {
   std::ostringstream o;
   o << v.KB << "x" << v.MB << "/" << v.GK << "x" << v.GM << "/jc" << v.JC << "/w" << v.NW
-    << "/b" << v.minb << (v.split ? "/split" : "") << (v.tc ? "/tc" : "") << (v.f16 ? "/f16" : "") << (v.tg ? "/tg" : "") << (v.db ? "/db" : "") << (v.exact ? "/exact" : "/generic");
+    << "/b" << v.minb << (v.split ? "/split" : "") << (v.tc ? "/tc" : "") << (v.f16 ? "/f16" : "") << (v.tg ? "/tg" : "") << (v.tgt ? "/tgt" : "") << (v.db ? "/db" : "") << (v.exact ? "/exact" : "/generic");
   return o.str();
 }
 

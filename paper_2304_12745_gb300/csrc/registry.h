@@ -26,6 +26,7 @@ struct Variant {
   bool f16 = false;  // the layers' contractions as split-FP16 MMAs (scaled instances)
   bool tg = false;   // tcgen05 build: operands in shared memory, accumulators in tensor memory
   bool fac = false;  // exports / imports resident Gram factors (SolveArgs::fac)
+  bool tgt = false;  // the transposed tcgen05 build (a thread per antenna, Q^T in tensor memory)
 };
 
 // The instance shapes (M, K) a variant solves.
@@ -59,6 +60,7 @@ void register_solve_tc(std::vector<Variant>& v);
 void register_solve_tch(std::vector<Variant>& v);
 void register_solve_tcwh(std::vector<Variant>& v);
 void register_solve_tg(std::vector<Variant>& v);
+void register_solve_tgt(std::vector<Variant>& v);
 const void* tch_host_kernel(int nw, int minb);  // host-buffer twin of a split-FP16 K=8 build
 void register_solve_tcw_64(std::vector<Variant>& v);
 void register_solve_tcw_128(std::vector<Variant>& v);

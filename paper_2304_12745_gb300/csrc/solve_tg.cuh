@@ -302,6 +302,15 @@ struct SolveTG {
       }
       __syncwarp();
     }
+    af_tail(L, fr, fi, fsc, Fs, sm);
+  }
+
+  // The warp's four rows of F (k = 4 w + i, column j = lane), each scaled by its
+  // own power of two into [2^13, 2^14) (fsc[k]: the factor that rows k and k + 32
+  // of the product take back), into the A_F tiles hi / lo
+  __device__ __forceinline__ static void af_tail(const Lane& L, const float (&fr)[4], const float (&fi)[4],
+                                                 float* fsc, float* Fs, unsigned char* sm) {
+    const int k0 = 4 * L.w, j = L.lane;
     float m[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) m[i] = fmaxf(fabsf(fr[i]), fabsf(fi[i]));

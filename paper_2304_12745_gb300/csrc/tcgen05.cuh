@@ -7,7 +7,7 @@
 // bytes), element (r, c) at
 //     (r / 8) * (cols * 16) + (c / 8) * 128 + (r % 8) * 16 + (c % 8) * 2.
 // The same bytes serve as a K-major operand ([M or N][K], K = cols) and as an
-// MN-major B operand ([K][N], N = cols).  In a shared-memory matrix descriptor
+// MN-major operand ([K][M or N], M or N = cols).  In a shared-memory matrix descriptor
 // the leading byte offset is the stride between core matrices along K and the
 // stride byte offset the stride along M / N, for both majors.  With M = 64 the
 // accumulator's row r lives in TMEM lane 32 (r / 16) + r % 16, with M = 128 in
@@ -32,10 +32,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, A K-major,
-// B K-major (b_mn = 0) or MN-major (b_mn = 1), M x N
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int b_mn) {
-  return (1u << 4) | ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) |
+// instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, B K-major
+// (b_mn = 0) or MN-major (b_mn = 1), A likewise (a_mn; an A read from tensor
+// memory is K-major), M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int b_mn, int a_mn = 0) {
+  return (1u << 4) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
@@ -46,6 +47,18 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate ? 1 : 0)
+      : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B: A read from tensor memory (row i in lane i, its K
+// elements two FP16 per 32-bit column, the even one in the low half; a K step of 16
+// is 8 columns), B from a shared-memory descriptor
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                           bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate ? 1 : 0)
       : "memory");
 }
 

@@ -34,25 +34,27 @@ def pc():
     return capi, precoder
 
 
-# (label, M, K, plan options): the FFMA kernel, the one-warp split-FP16 kernel and
-# the multi-warp split-FP16 kernel
+# (label, M, K, plan options): the FFMA kernel, the one-warp split-FP16 kernel, the
+# multi-warp split-FP16 kernel and the two tcgen05 builds (named by their key)
 STALL_CASES = [("ffma", 32, 4, {}), ("tch", 64, 8, dict(tensor_cores=True)),
-               ("tcwh", 256, 32, dict(tensor_cores=True)), ("tg", 256, 32, None)]
+               ("tcwh", 256, 32, dict(tensor_cores=True)), ("tg", 256, 32, "tg"),
+               ("tgt", 256, 32, "tgt")]
 
 
-def tg_build(tmp_path, capi, M, K):
-    """Plan options that pin (M, K) to the tcgen05 build."""
+def tg_build(tmp_path, capi, M, K, suffix):
+    """Plan options that pin (M, K) to a tcgen05 build (the row build, key suffix
+    "tg", or the transposed one, "tg/tgt")."""
     path = tmp_path / "tune_tg.txt"
     path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|{K}|{M}\t"
-                    "32x256/4x8/jc8/w8/b1/split/tc/f16/tg/generic\n")
+                    f"32x256/4x8/jc8/w8/b1/split/tc/f16/{suffix}/generic\n")
     return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
 
 
 @pytest.mark.parametrize("label,M,K,kw", STALL_CASES)
 def test_copy_wait_runs_out_and_is_reported(pc, orc, tmp_path, label, M, K, kw):
     capi, precoder = pc
-    if kw is None:
-        kw = tg_build(tmp_path, capi, M, K)
+    if isinstance(kw, str):
+        kw = tg_build(tmp_path, capi, M, K, "tg" if kw == "tg" else "tg/tgt")
     B, T = 96, 4
     H = ch.rayleigh(B, K, M, seed=80 + K)
     t = ch.targets(B, K)

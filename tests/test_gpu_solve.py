@@ -604,28 +604,37 @@ def test_fp16_multiwarp_flags_and_fp64(pc, orc, tmp_path, eps):
     assert_parity(gpu, ref)
 
 
-# The tcgen05 build (any K <= 32 users at M = 256: operands in shared memory,
-# accumulators in tensor memory), forced through an autotune cache entry.
+# The tcgen05 builds (any K <= 32 users at M = 256: operands in shared memory,
+# accumulators in tensor memory), forced through an autotune cache entry: the row
+# build (a warp per 16 rows of W) and the transposed one (a thread per antenna,
+# Q^T in tensor memory).
 TG_KEY = "32x256/4x8/jc8/w8/b1/split/tc/f16/tg/generic"
+TG_KEYS = {"tg": TG_KEY, "tgt": "32x256/4x8/jc8/w8/b1/split/tc/f16/tg/tgt/generic"}
+TG_NAMES = {"tg": "solve_tg_kernel<1>", "tgt": "solve_tgt_kernel<1>"}
 
 
-def forced_tg(tmp_path, capi, K, M=256):
-    path = tmp_path / "tune_tg.txt"
-    path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|{K}|{M}\t{TG_KEY}\n")
+@pytest.fixture(params=["tg", "tgt"])
+def tgb(request):
+    return request.param
+
+
+def forced_tg(tmp_path, capi, K, M=256, build="tg"):
+    path = tmp_path / f"tune_{build}.txt"
+    path.write_text(f"{torch.cuda.get_device_name(0)}|{capi.LAYER_PROJ}|{K}|{M}\t{TG_KEYS[build]}\n")
     return dict(tensor_cores=True, autotune=True, tune_cache=str(path))
 
 
-def run_tg(capi, precoder, tmp_path, H, t, mu, **extra):
+def run_tg(capi, precoder, tmp_path, H, t, mu, build="tg", **extra):
     B, K, M = H.shape
-    kw = forced_tg(tmp_path, capi, K, M)
+    kw = forced_tg(tmp_path, capi, K, M, build)
     plan = precoder.Plan(capi.LAYER_PROJ, len(mu), [(M, K)], max(B, 1), **kw, **extra)
-    assert capi.precode_plan_describe(plan.handle, M, K) == "solve_tg_kernel<1>"
+    assert capi.precode_plan_describe(plan.handle, M, K) == TG_NAMES[build]
     plan.close()
     return run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **kw, **extra)
 
 
 @pytest.mark.parametrize("K,B", [(32, 400), (28, 300), (25, 170)])
-def test_tcgen05_parity(pc, orc, tmp_path, K, B):
+def test_tcgen05_parity(pc, orc, tmp_path, K, B, tgb):
     """Rician ULA channels (K-factor 0-10 dB), T = 10 uniform steps: the FP32 bar
     per instance against the FP64 oracle, with more instances than one round of
     the persistent CTAs (one per SM) and users padded to 32."""
@@ -633,26 +642,26 @@ def test_tcgen05_parity(pc, orc, tmp_path, K, B):
     H = ch.rician_ula(B, K, 256, seed=60 + K)
     t = ch.targets(B, K)
     mu = ch.uniform_steps(10, 0.01, 0.1, seed=61)
-    gpu = run_tg(capi, precoder, tmp_path, H, t, mu)
+    gpu = run_tg(capi, precoder, tmp_path, H, t, mu, tgb)
     assert np.all(gpu[3] == 0)
     assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
     assert np.all(gpu[2] <= 1e-4 * math.sqrt(K))
 
 
 @pytest.mark.parametrize("T", [1, 40])
-def test_tcgen05_layer_counts(pc, orc, tmp_path, T):
+def test_tcgen05_layer_counts(pc, orc, tmp_path, T, tgb):
     """One layer (the minimum-norm start W^(0) and a single shrink and
     projection) and 40 layers, on log-normal Rayleigh channels."""
     capi, precoder = pc
     H = ch.lognormal(160, 32, 256, seed=62)
     t = ch.targets(160, 32)
     mu = ch.uniform_steps(T, 0.01, 0.1, seed=63)
-    gpu = run_tg(capi, precoder, tmp_path, H, t, mu)
+    gpu = run_tg(capi, precoder, tmp_path, H, t, mu, tgb)
     assert np.all(gpu[3] == 0)
     assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
 
 
-def test_tcgen05_scales_and_gain_spread(pc, orc, tmp_path):
+def test_tcgen05_scales_and_gain_spread(pc, orc, tmp_path, tgb):
     """Channels and targets over 1e-5 .. 1e5 together per instance, and one user
     1e-4 weaker than the rest in every other instance."""
     capi, precoder = pc
@@ -662,13 +671,13 @@ def test_tcgen05_scales_and_gain_spread(pc, orc, tmp_path):
     H[::2, 5] *= np.float32(1e-4)
     t = (ch.targets(160, K) * sc[:, None]).astype(np.float32)
     mu = np.full(8, 0.03, np.float32)
-    gpu = run_tg(capi, precoder, tmp_path, H, t, mu)
+    gpu = run_tg(capi, precoder, tmp_path, H, t, mu, tgb)
     assert np.all(gpu[3] == 0)
     assert_parity(gpu, oracle_ref(orc, 1, H, t, mu))
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-4])
-def test_tcgen05_flags_and_fp64(pc, orc, tmp_path, eps):
+def test_tcgen05_flags_and_fp64(pc, orc, tmp_path, eps, tgb):
     """A singular Gram matrix, a non-finite input and near-collinear user pairs eps
     apart (the FP64 orthonormal-basis path, its layers on the tensor cores), with
     the per-row range scale of F; the FP32 bar on every solved instance."""
@@ -682,7 +691,7 @@ def test_tcgen05_flags_and_fp64(pc, orc, tmp_path, eps):
     H[5, 1, 9] = np.inf  # non-finite
     t = ch.targets(24, K)
     mu = np.full(6, 0.05, np.float32)
-    W, obj, res, fl = run_tg(capi, precoder, tmp_path, H, t, mu, cond_threshold=1e3)
+    W, obj, res, fl = run_tg(capi, precoder, tmp_path, H, t, mu, tgb, cond_threshold=1e3)
     assert fl[3] & capi.F_SINGULAR and not np.any(W[3]) and obj[3] == 0
     assert fl[5] & capi.F_NONFINITE
     assert np.all(fl[8:20:2] == capi.F_FP64_CHOL)
@@ -692,15 +701,15 @@ def test_tcgen05_flags_and_fp64(pc, orc, tmp_path, eps):
     assert_parity((W[ok], obj[ok], res[ok], fl[ok]), oracle_ref(orc, 1, H[ok], t[ok], mu))
 
 
-def test_tcgen05_deterministic(pc, tmp_path):
+def test_tcgen05_deterministic(pc, tmp_path, tgb):
     """Bitwise the same output on a second call and inside a larger batch."""
     capi, precoder = pc
     H = ch.rician_ula(200, 32, 256, seed=68)
     t = ch.targets(200, 32)
     mu = ch.uniform_steps(10, 0.01, 0.1, seed=69)
-    a = run_tg(capi, precoder, tmp_path, H, t, mu)
-    b = run_tg(capi, precoder, tmp_path, H, t, mu)
-    c = run_tg(capi, precoder, tmp_path, H[:37], t[:37], mu)
+    a = run_tg(capi, precoder, tmp_path, H, t, mu, tgb)
+    b = run_tg(capi, precoder, tmp_path, H, t, mu, tgb)
+    c = run_tg(capi, precoder, tmp_path, H[:37], t[:37], mu, tgb)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
     for x, y in zip(a, c):
