@@ -72,8 +72,8 @@ const std::vector<Variant>& variants() {
     register_solve_tch(r);  // before the TF32 build: the projected layer's default at 8 x 64
     register_solve_tc(r);
     register_solve_tcwh(r);  // before the TF32 builds: the projected layer's default there
+    register_solve_tgt(r);  // before the row build: the default tcgen05 build
     register_solve_tg(r);
-    register_solve_tgt(r);
     register_solve_tcw_64(r);
     register_solve_tcw_128(r);
     register_solve_tcw_256(r);

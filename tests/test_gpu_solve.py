@@ -771,7 +771,7 @@ def test_tensor_core_large_buckets(pc, orc, tmp_path, K, M, B, mode):
     plan = precoder.Plan(m, len(step), [(M, K)], B, **kw)
     name = capi.precode_plan_describe(plan.handle, M, K)
     plan.close()
-    expect = {"proj": "solve_tg_kernel" if M == 256 else "solve_tcwh_kernel"}.get(mode, "solve_tcw_kernel")
+    expect = {"proj": "solve_tgt_kernel" if M == 256 else "solve_tcwh_kernel"}.get(mode, "solve_tcw_kernel")
     assert name.startswith(expect), name
     gpu = run_gpu(precoder, m, H, t, step, lam, **kw)
     ref = oracle_ref(orc, 0 if mode == "pgd" else 1, H, t, step, lam)
@@ -795,10 +795,10 @@ def test_tensor_core_padded_users(pc, orc, tmp_path, K, M, build):
     name = capi.precode_plan_describe(plan.handle, M, K)
     plan.close()
     # K <= 8 has only split-TF32 padded builds (one warp); 9..32 default to split FP16,
-    # 25..32 at 256 antennas to the tcgen05 build
+    # 25..32 at 256 antennas to the transposed tcgen05 build
     expect = "solve_tcw_kernel"
     if build == "default" and K > 8:
-        expect = "solve_tg_kernel" if (M == 256 and K > 24) else "solve_tcwh_kernel"
+        expect = "solve_tgt_kernel" if (M == 256 and K > 24) else "solve_tcwh_kernel"
     assert name.startswith(expect), name
     gpu = run_gpu(precoder, capi.LAYER_PROJ, H, t, mu, **kw)
     ref = oracle_ref(orc, 1, H, t, mu)
