@@ -190,24 +190,25 @@ struct SolveTG {
   }
 
   // D_E = [A hi; A lo] [H_R hi; H_R lo]^T (M = N = 128, both K-major), 16 MMAs
+  // (descriptors stepped by their 16-byte address units; unrolled, so that the MMAs
+  // issue back to back)
   __device__ static void issue_residual(uint32_t tm, uint32_t a, uint32_t b) {
     constexpr uint32_t id = tc5::idesc_f16(128, 128, 0);
-#pragma unroll 1
-    for (int ks = 0; ks < 16; ++ks)
-      tc5::mma_f16(tm + C::TM_E, tc5::sdesc(a + ks * 256, 128, 4096), tc5::sdesc(b + ks * 256, 128, 4096),
-                   id, ks != 0);
+    const uint64_t a0 = tc5::sdesc(a, 128, 4096), b0 = tc5::sdesc(b, 128, 4096);
+#pragma unroll
+    for (int ks = 0; ks < 16; ++ks) tc5::mma_f16(tm + C::TM_E, a0 + 16 * ks, b0 + 16 * ks, id, ks != 0);
   }
   // D_W = A_F[64][64] (K-major) H_R[64][256] (MN-major), split FP16: 3 x 4 MMAs
   __device__ static void issue_update(uint32_t tm, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
                                       uint32_t b_lo) {
     constexpr uint32_t id = tc5::idesc_f16(64, 256, 1);
     const uint32_t as[3] = {a_hi, a_lo, a_hi}, bs[3] = {b_lo, b_hi, b_hi};
-#pragma unroll 1
-    for (int ps = 0; ps < 3; ++ps)
-#pragma unroll 1
-      for (int ks = 0; ks < 4; ++ks)
-        tc5::mma_f16(tm + C::TM_W, tc5::sdesc(as[ps] + ks * 256, 128, 1024),
-                     tc5::sdesc(bs[ps] + ks * 8192, 4096, 128), id, (ps | ks) != 0);
+#pragma unroll
+    for (int ps = 0; ps < 3; ++ps) {
+      const uint64_t a0 = tc5::sdesc(as[ps], 128, 1024), b0 = tc5::sdesc(bs[ps], 4096, 128);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) tc5::mma_f16(tm + C::TM_W, a0 + 16 * ks, b0 + 512 * ks, id, (ps | ks) != 0);
+    }
   }
 
   // D_E -> staging: warp w reads TMEM lanes 32 (w % 4) + lane = rows r of [A hi;
@@ -326,13 +327,13 @@ struct SolveTG {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int k = k0 + i;
+      // max |F_k| into [2^13, 2^14): with m in [2^(e-127), 2^(e-126)) for biased
+      // exponent e, fs = 2^(140 - e) (e clamped to 26 below), xs = 1 / fs
       float fs = 1.f, xs = 1.f;
-      if (m[i] > 0.f && m[i] <= FLT_MAX) {  // max |F_k| into [2^13, 2^14)
-        int ex;
-        frexpf(m[i], &ex);
-        ex = max(ex, -100);
-        fs = ldexpf(1.f, 14 - ex);
-        xs = ldexpf(1.f, ex - 14);
+      if (m[i] > 0.f && m[i] <= FLT_MAX) {
+        const int e = max((int)(__float_as_uint(m[i]) >> 23), 26);
+        fs = __uint_as_float((uint32_t)(267 - e) << 23);
+        xs = __uint_as_float((uint32_t)(e - 13) << 23);
       }
       if (j == 0) fsc[k] = xs;
       fw[i * C::FSS + j] = fs * fr[i];
@@ -412,24 +413,29 @@ struct SolveTG {
     return sqrtf(r);
   }
 
-  // One entry's Gauss-Jordan step at pivot p: v = A[i][j], c = A[i][p], b = A[p][j],
-  // inv = 1 / A[p][p]; the pivot entry, the pivot row, the pivot column or the rest
-  // (a - (c / d) b), selected without divergence.
-  __device__ __forceinline__ static float2 gj_entry(float2 v, float2 c, float2 b, float inv, bool rowp,
-                                                    bool colp) {
-    const float tr = c.x * inv, ti = c.y * inv;
-    const float2 g = make_float2(v.x - (tr * b.x - ti * b.y), v.y - (tr * b.y + ti * b.x));
-    const float2 rowv = make_float2(v.x * inv, v.y * inv);
-    const float2 colv = make_float2(-c.x * inv, -c.y * inv);
-    return rowp ? (colp ? make_float2(inv, 0.f) : rowv) : (colp ? colv : g);
+  // a s - f b (complex a, f, b; real s): one entry of an elimination step
+  __device__ __forceinline__ static float2 sfb(float2 a, float s, float2 f, float2 b) {
+    return make_float2(fmaf(f.y, b.y, fmaf(-f.x, b.x, s * a.x)), fmaf(-f.y, b.x, fmaf(-f.x, b.y, s * a.y)));
+  }
+  __device__ __forceinline__ static float2 cscale(float2 c, float r) { return make_float2(c.x * r, c.y * r); }
+  // reciprocal: the hardware approximation (relative error within 2^-23) and one
+  // Newton-Raphson step r + r (1 - x r), which squares that error (the pivots of an
+  // accepted factorisation are normal numbers)
+  __device__ __forceinline__ static float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.f), r);
   }
 
   // Equilibrated Gauss-Jordan inverse (no pivoting; pivot spread max d / min d of
   // the equilibrated matrix is the condition estimate) with the matrix in
   // registers: thread (i = tid / 8, columns j_c = tid % 8 + 8 c) holds a[c] =
-  // G'^T[i][j_c] on entry and G'^{-T}[i][j_c] on a true return.  Two pivots per
-  // barrier: the rows and columns of pivots p and p + 1 are published by their
-  // owners (two alternating buffers), and each thread replays pivot p on the
+  // G'^T[i][j_c] on entry and G'^{-T}[i][j_c] on a true return.  Pivot p takes
+  // every entry to a s_i - f_i A[p][j] (row p: s = 1 / A[p][p], f = 0; any other
+  // row: s = 1, f = A[i][p] / A[p][p]), then sets column p to the inverse's
+  // (1 / A[p][p] at the pivot, -f_i elsewhere): the in-place elimination.  Two
+  // pivots per barrier: the rows and columns of pivots p and p + 1 are published by
+  // their owners (two alternating buffers), and each thread replays pivot p on the
   // entries pivot p + 1 reads (row p + 1 at its columns, its row's column p + 1, the
   // pivot) before applying p + 1 to its own: the entries of the one-pivot-a-step
   // elimination, in half the barriers.
@@ -449,8 +455,7 @@ struct SolveTG {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       dj[c] = dsc[j0 + 8 * c];
-      const float sc = di * dj[c];
-      a[c] = make_float2(a[c].x * sc, a[c].y * sc);
+      a[c] = cscale(a[c], di * dj[c]);
     }
     bool fail = false;
     float dmin = FLT_MAX, dmax = 0.f;
@@ -478,7 +483,7 @@ struct SolveTG {
       fail |= !(dp > 0.f) || !(dp < FLT_MAX);
       dmin = fminf(dmin, dp);
       dmax = fmaxf(dmax, dp);
-      const float invp = __frcp_rn(dp);
+      const float invp = rcp(dp);
       const float2 cip = cp[i], ciq = cp[KB + i];
       float2 rpb[4], rqb[4];
 #pragma unroll
@@ -487,34 +492,39 @@ struct SolveTG {
         rqb[c] = Rq[j0 + 8 * c];
       }
       const float2 aqp = Rq[p], apq = Rp[q], aqq = Rq[q];
-      // what pivot q reads, after pivot p: its pivot, its row at my columns, my row's column q
-      const float dq = gj_entry(aqq, aqp, apq, invp, false, false).x;
-      const float2 ciq1 = gj_entry(ciq, cip, apq, invp, i == p, false);
-      float2 rq1[4];
+      const bool ip = i == p, iq = i == q;
+      const int colp = (j0 == (p & 7)) ? (p >> 3) : -1, colq = (j0 == (q & 7)) ? (q >> 3) : -1;
+      const float sp = ip ? invp : 1.f;
+      const float2 fp = ip ? make_float2(0.f, 0.f) : cscale(cip, invp);
+      // what pivot q reads, after pivot p: its row at my columns, my row's column q, its pivot
+      const float2 fq = cscale(aqp, invp);
+      float2 bq[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int j = j0 + 8 * c;
-        rq1[c] = gj_entry(rqb[c], aqp, rpb[c], invp, false, j == p);
-        a[c] = gj_entry(a[c], cip, rpb[c], invp, i == p, j == p);
+        bq[c] = sfb(rqb[c], 1.f, fq, rpb[c]);
+        if (c == colp) bq[c] = make_float2(-fq.x, -fq.y);
+        a[c] = sfb(a[c], sp, fp, rpb[c]);
+        if (c == colp) a[c] = ip ? make_float2(invp, 0.f) : make_float2(-fp.x, -fp.y);
       }
+      const float2 cq = sfb(ciq, sp, fp, apq);
+      const float dq = fmaf(fq.y, apq.y, fmaf(-fq.x, apq.x, aqq.x));
       // pivot q
       fail |= !(dq > 0.f) || !(dq < FLT_MAX);
       dmin = fminf(dmin, dq);
       dmax = fmaxf(dmax, dq);
-      const float invq = __frcp_rn(dq);
+      const float invq = rcp(dq);
+      const float sq = iq ? invq : 1.f;
+      const float2 fqq = iq ? make_float2(0.f, 0.f) : cscale(cq, invq);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int j = j0 + 8 * c;
-        a[c] = gj_entry(a[c], ciq1, rq1[c], invq, i == q, j == q);
+        a[c] = sfb(a[c], sq, fqq, bq[c]);
+        if (c == colq) a[c] = iq ? make_float2(invq, 0.f) : make_float2(-fqq.x, -fqq.y);
       }
     }
     const bool ok = !fail && !(dmax > cond_thr * dmin);
     if (ok)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float sc = di * dj[c];
-        a[c] = make_float2(a[c].x * sc, a[c].y * sc);
-      }
+      for (int c = 0; c < 4; ++c) a[c] = cscale(a[c], di * dj[c]);
     return ok;
   }
 

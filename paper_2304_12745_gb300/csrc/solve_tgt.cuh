@@ -42,6 +42,7 @@ struct SolveTGT {
   static_assert(64 * ETS * 4 <= C::OFF_EC - C::OFF_ED, "the residual staging fits");
   static_assert(MB * 128 * 2 <= C::HS_BYTES, "the X tiles fit the channel area");
   static_assert(TM_Q + 128 <= C::TMEM_COLS && C::TM_E + 128 <= TM_Q, "tensor-memory columns");
+  static_assert(C::OFF_FAC % 8 == 0, "the update's two mbarriers sit in the (unused) shrink-factor area");
 
   // The thread's column of W_R (or X) into the residual's B tiles, [256 antennas]
   // [128] MN-major: columns 0..63 hi, 64..127 lo (consecutive antennas of an access
@@ -57,40 +58,57 @@ struct SolveTGT {
     }
   }
 
-  // D_E = [H_R hi; H_R lo] [X hi | X lo]^T (M = N = 128), 16 MMAs
-  __device__ static void issue_residual(uint32_t tm, uint32_t s_hr, uint32_t s_x) {
+  // D_E = [H_R hi; H_R lo] [X hi | X lo]^T (M = N = 128) over antennas 128 part ..
+  // 128 part + 127 (the X tiles of one half of the threads), 8 MMAs
+  // (descriptors stepped by their 16-byte address units: a K step is 256 bytes of A,
+  // 4096 of B; unrolled, so that the MMAs issue back to back)
+  template <int PART>
+  __device__ __forceinline__ static void issue_residual(uint32_t tm, uint32_t s_hr, uint32_t s_x) {
     constexpr uint32_t id = tc5::idesc_f16(128, 128, 1);
-#pragma unroll 1
-    for (int ks = 0; ks < 16; ++ks)
-      tc5::mma_f16(tm + C::TM_E, tc5::sdesc(s_hr + ks * 256, 128, 4096), tc5::sdesc(s_x + ks * 4096, 2048, 128),
-                   id, ks != 0);
+    const uint64_t a0 = tc5::sdesc(s_hr + PART * 8 * 256, 128, 4096);
+    const uint64_t b0 = tc5::sdesc(s_x + PART * 8 * 4096, 2048, 128);
+#pragma unroll 4
+    for (int ks = 0; ks < 8; ++ks)
+      tc5::mma_f16(tm + C::TM_E, a0 + 16 * ks, b0 + 256 * ks, id, PART != 0 || ks != 0);
   }
 
   // Q^T for antenna half h: D[m][n] = sum_r H_R[r][128 h + m] A_G[n][r] with B =
   // [A_G hi; A_G lo] (N = 128), A = H_R hi, then H_R lo (MN-major), 16 MMAs
   __device__ static void issue_q(uint32_t tm, uint32_t s_hr, uint32_t s_hrl, uint32_t s_ag) {
     constexpr uint32_t id = tc5::idesc_f16(128, 128, 0, 1);
+    const uint64_t b0 = tc5::sdesc(s_ag, 128, 1024);
 #pragma unroll 1
     for (int h = 0; h < 2; ++h)
 #pragma unroll 1
-      for (int a = 0; a < 2; ++a)
-#pragma unroll 1
+      for (int a = 0; a < 2; ++a) {
+        const uint64_t a0 = tc5::sdesc((a ? s_hrl : s_hr) + 2048 * h, 4096, 128);
+#pragma unroll
         for (int ks = 0; ks < 4; ++ks)
-          tc5::mma_f16(tm + C::TM_W + 128 * h, tc5::sdesc((a ? s_hrl : s_hr) + 2048 * h + ks * 8192, 4096, 128),
-                       tc5::sdesc(s_ag + ks * 256, 128, 1024), id, (a | ks) != 0);
+          tc5::mma_f16(tm + C::TM_W + 128 * h, a0 + 512 * ks, b0 + 16 * ks, id, (a | ks) != 0);
+      }
   }
 
-  // D_W for antenna half h = [Q^T hi or lo] (tensor memory) [B_E hi; B_E lo]^T, 16 MMAs
-  __device__ static void issue_update(uint32_t tm, uint32_t s_be) {
-    constexpr uint32_t id = tc5::idesc_f16(128, 128, 0);
+  // D_W for antenna half h = Q_h^T (tensor memory) times the real form of E^T: A = Q
+  // hi against [B_E hi; B_E lo] (N = 128), then A = Q lo against B_E hi (N = 64),
+  // three of the four split-FP16 products (lo x lo dropped); each half completes on
+  // its own mbarrier, so that its threads start while the other half's MMAs run
+  __device__ static void issue_update(uint32_t tm, uint32_t s_be, uint64_t* bar) {
+    constexpr uint32_t id128 = tc5::idesc_f16(128, 128, 0), id64 = tc5::idesc_f16(128, 64, 0);
+    const uint64_t b0 = tc5::sdesc(s_be, 128, 1024);
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h)
-#pragma unroll 1
-      for (int a = 0; a < 2; ++a)
-#pragma unroll 1
-        for (int ks = 0; ks < 4; ++ks)
-          tc5::mma_f16_ta(tm + C::TM_W + 128 * h, tm + TM_Q + 64 * h + 32 * a + 8 * ks,
-                          tc5::sdesc(s_be + ks * 256, 128, 1024), id, (a | ks) != 0);
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc5::mma_f16_ta(tm + C::TM_W + 128 * h, tm + TM_Q + 64 * h + 8 * ks, b0 + 16 * ks, id128, ks != 0);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks)
+        tc5::mma_f16_ta(tm + C::TM_W + 128 * h, tm + TM_Q + 64 * h + 32 + 8 * ks, b0 + 16 * ks, id64, true);
+      tc5::commit(smem_addr(bar + h));
+    }
+  }
+
+  __device__ __forceinline__ static void half_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(NT / 2) : "memory");
   }
 
   // D_E -> staging: warp w reads TMEM lanes r = 32 (w % 4) + lane (row r of
@@ -143,23 +161,20 @@ struct SolveTGT {
   __device__ __forceinline__ static void make_be(const Lane& L, const float (&er)[4], const float (&ei)[4],
                                                  float gqi, float* fsc, float* Fs, unsigned char* sm) {
     const int k0 = 4 * L.w, j = L.lane;
-    float m[4];
+    float m[4];  // row maxima of |Re|, |Im| (non-negative floats order as their bits)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) m[i] = fmaxf(fabsf(er[i]), fabsf(ei[i]));
-#pragma unroll
-    for (int msk = 1; msk < 32; msk <<= 1)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) m[i] = fmaxf(m[i], __shfl_xor_sync(FULL, m[i], msk));
+    for (int i = 0; i < 4; ++i)
+      m[i] = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(fmaxf(fabsf(er[i]), fabsf(ei[i])))));
     float* const fw = Fs + L.w * 4 * C::FSS;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      // m in [2^(e-127), 2^(e-126)) for biased exponent e: fs = 2^(140 - e) puts the
+      // row into [2^13, 2^14) (e clamped to 26 below), xs = 1 / fs
       float fs = 1.f, xs = 1.f;
       if (m[i] > 0.f && m[i] <= FLT_MAX) {
-        int ex;
-        frexpf(m[i], &ex);
-        ex = max(ex, -100);
-        fs = ldexpf(1.f, 14 - ex);
-        xs = ldexpf(1.f, ex - 14);
+        const int e = max((int)(__float_as_uint(m[i]) >> 23), 26);
+        fs = __uint_as_float((uint32_t)(267 - e) << 23);
+        xs = __uint_as_float((uint32_t)(e - 13) << 23);
       }
       if (j == 0) fsc[k0 + i] = xs * gqi;
       fw[i * C::FSS + j] = fs * er[i];
@@ -231,6 +246,14 @@ struct SolveTGT {
     tc5::wait_st();
   }
 
+  // sum of squares of the thread's column in four independent chains
+  __device__ __forceinline__ static float sumsq(const float (&w)[NC]) {
+    float r[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int n = 0; n < NC; ++n) r[n & 3] = fmaf(w[n], w[n], r[n & 3]);
+    return (r[0] + r[1]) + (r[2] + r[3]);
+  }
+
   __device__ __forceinline__ static float warp_max(float v) {
 #pragma unroll
     for (int msk = 1; msk < 32; msk <<= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, msk));
@@ -267,12 +290,15 @@ struct SolveTGT {
     uint64_t* const cbar = reinterpret_cast<uint64_t*>(sm + C::OFF_BAR);
     uint64_t* const mbar = cbar + 1;
     uint32_t* const tslot = reinterpret_cast<uint32_t*>(cbar + 2);
+    uint64_t* const ubar = reinterpret_cast<uint64_t*>(sm + C::OFF_FAC);  // update halves
     const uint32_t s_x = smem_addr(sm + C::OFF_HS);
     const uint32_t s_hr = smem_addr(sm + C::OFF_HR), s_hrl = smem_addr(sm + C::OFF_HRL);
     const uint32_t s_af = smem_addr(sm + C::OFF_AF);
     if (L.tid == 0) {
       mbar_init(cbar, 1);
       mbar_init(mbar, 1);
+      mbar_init(ubar, 1);
+      mbar_init(ubar + 1, 1);
     }
     fence_mbar_init();
     if (L.w == 0) tc5::alloc(smem_addr(tslot), C::TMEM_COLS);
@@ -283,7 +309,8 @@ struct SolveTGT {
     const uint32_t tm_q = tm + ((uint32_t)(32 * (L.w & 3)) << 16);  // this warp's lane quarter
     const uint64_t lim = copy_wait_ns(A);
 
-    uint32_t cphase = 0, mphase = 0;
+    uint32_t cphase = 0, mphase = 0, uphase = 0;
+    const int half = L.w >> 2;  // antenna half of the thread (its update's mbarrier)
     const int64_t n_inst = A.tbl ? (int64_t)(*A.count) : A.B;
     auto locate = [&](int64_t it, int64_t& inst, int64_t& h_off, int64_t& w_off, int64_t& t_off,
                       int& K) {
@@ -302,14 +329,23 @@ struct SolveTGT {
         t_off = it * A.t_stride;
       }
     };
+    // the next channel: thread 0 sets the byte count, then lane j of warp w copies row
+    // 4 w + j (j < 4), so that no warp issues more than four copies
     auto issue_copy = [&](int64_t it) {
-      if (L.tid != 0 || it >= n_inst || (A.opts & OPT_STALL_COPY)) return;
+      if (it >= n_inst || (A.opts & OPT_STALL_COPY)) return;
       int64_t inst, h_off, w_off, t_off;
       int K;
       locate(it, inst, h_off, w_off, t_off, K);
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(cbar, K * MB * 8);
-      for (int k = 0; k < K; ++k) bulk_g2s(Hs + k * RSF, A.H + h_off + k * MB, MB * 8, cbar);
+      if (L.tid == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(cbar, K * MB * 8);
+      }
+      __syncthreads();
+      const int k = 4 * L.w + L.lane;
+      if (L.lane < 4 && k < K) {
+        fence_proxy_async_smem();
+        bulk_g2s(Hs + k * RSF, A.H + h_off + k * MB, MB * 8, cbar);
+      }
     };
     issue_copy(blockIdx.x);
     float w[NC];
@@ -318,6 +354,13 @@ struct SolveTGT {
       int64_t inst, h_off, w_off, t_off;
       int K;
       locate(it, inst, h_off, w_off, t_off, K);
+      if (L.w == 1 && it + gridDim.x < n_inst && !(A.opts & OPT_STALL_COPY)) {
+        // the channel copied at the end of this instance: into L2 meanwhile
+        int64_t i2, h2, w2, t2;
+        int K2;
+        locate(it + gridDim.x, i2, h2, w2, t2, K2);
+        if (L.lane < K2) prefetch_l2(A.H + h2 + L.lane * MB, MB * 8);
+      }
       if (L.tid < KB) tks[L.tid] = L.tid < K ? A.t[t_off + L.tid] : 0.f;
       if (L.tid == 0) misc[0] = mbar_wait_bounded(cbar, cphase, lim) ? 1 : 0;
       __syncthreads();
@@ -492,11 +535,9 @@ struct SolveTGT {
             make_be(L, er, ei, gqi, fsc, Fs, sm);
           }
           G::publish_smem();
-          if (L.tid == 0) {
-            issue_update(tm, s_af);
-            tc5::commit(smem_addr(mbar));
-          }
-          ok = G::mma_wait(mbar, mphase, lim) && ok;
+          // issued by a thread of the second half: the first half's warps go on meanwhile
+          if (L.tid == NT / 2) issue_update(tm, s_af, ubar);
+          ok = G::mma_wait(ubar + half, uphase, lim) && ok;
           read_w<false>(L, tm_q, fsc, w);
         }
         // global scale b: max(|W^(0)'|, |targets|) into [8, 16)
@@ -525,51 +566,60 @@ struct SolveTGT {
           }
         __syncthreads();
 
-        // ---- layers (scaled units)
+        // ---- layers (scaled units).  Each antenna half waits for its own half of
+        // the update, shrinks and writes its X tiles; the residual's MMAs over the
+        // first half's antennas start while the second half is still at work.
         const int T = A.T;
+        bool pending = false;  // an update of W is in flight
 #pragma unroll 1
         for (int l = 0; l < T; ++l) {
           const float tau = fmaxf(__ldg(A.step + l), 0.f) * beta, tau2 = tau * tau;
-          float r2 = 0.f;
-#pragma unroll
-          for (int n = 0; n < NC; ++n) r2 = fmaf(w[n], w[n], r2);
+          if (pending) {
+            ok = G::mma_wait(ubar + half, uphase, lim) && ok;
+            read_w<false>(L, tm_q, fsc, w);
+          }
+          const float r2 = sumsq(w);
           const float f = r2 > tau2 ? 1.f - tau * rsqrtf(r2) : 0.f;
 #pragma unroll
           for (int n = 0; n < NC; ++n) w[n] *= f;
           build_xt(L, w, sm);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           tc5::fence_before_sync();
+          if (half == 0) {
+            half_sync(1);
+            if (L.tid == 0) {
+              tc5::fence_after_sync();
+              issue_residual<0>(tm, s_hr, s_x);
+            }
+          }
           ok = __syncthreads_and(ok) != 0;
           tc5::fence_after_sync();
-          if (!ok) break;
           if (L.tid == 0) {
-            issue_residual(tm, s_hr, s_x);
+            issue_residual<1>(tm, s_hr, s_x);
             tc5::commit(smem_addr(mbar));
           }
           ok = G::mma_wait(mbar, mphase, lim) && ok;
           stage_e(L, tm_q, Sg);
           ok = __syncthreads_and(ok) != 0;
+          pending = false;
+          if (!ok) break;
           {
             float er[4], ei[4];
             form_e(L, Sg, tks, Es, dinv, basis, er, ei);
             make_be(L, er, ei, gqi, fsc, Fs, sm);
           }
           G::publish_smem();
-          if (L.tid == 0) {
-            issue_update(tm, s_af);
-            tc5::commit(smem_addr(mbar));
-          }
-          ok = G::mma_wait(mbar, mphase, lim) && ok;
+          // issued by a thread of the second half: the first half's warps go on meanwhile
+          if (L.tid == NT / 2) issue_update(tm, s_af, ubar);
+          pending = true;
+        }
+        if (pending) {
+          ok = G::mma_wait(ubar + half, uphase, lim) && ok;
           read_w<false>(L, tm_q, fsc, w);
         }
 
         // ---- objective (sum of the column norms) and residual of W_T
-        {
-          float r2 = 0.f;
-#pragma unroll
-          for (int n = 0; n < NC; ++n) r2 = fmaf(w[n], w[n], r2);
-          o = sqrtf(r2);
-        }
+        o = sqrtf(sumsq(w));
         ok = __syncthreads_and(ok) != 0;
         if (A.resid && ok) {
           if (basis) {  // against the channel itself: H' again, and its tiles
@@ -585,7 +635,8 @@ struct SolveTGT {
           build_xt(L, w, sm);
           G::publish_smem();
           if (L.tid == 0) {
-            issue_residual(tm, s_hr, s_x);
+            issue_residual<0>(tm, s_hr, s_x);
+            issue_residual<1>(tm, s_hr, s_x);
             tc5::commit(smem_addr(mbar));
           }
           ok = G::mma_wait(mbar, mphase, lim) && ok;
