@@ -93,13 +93,13 @@ struct SolveTGT {
   // three of the four split-FP16 products (lo x lo dropped); each half completes on
   // its own mbarrier, so that its threads start while the other half's MMAs run
   __device__ static void issue_update(uint32_t tm, uint32_t s_be, uint64_t* bar) {
-    constexpr uint32_t id128 = tc5::idesc_f16(128, 128, 0), id64 = tc5::idesc_f16(128, 64, 0);
+    constexpr uint32_t id = tc5::idesc_f16(128, 128, 0), id64 = tc5::idesc_f16(128, 64, 0);
     const uint64_t b0 = tc5::sdesc(s_be, 128, 1024);
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks)
-        tc5::mma_f16_ta(tm + C::TM_W + 128 * h, tm + TM_Q + 64 * h + 8 * ks, b0 + 16 * ks, id128, ks != 0);
+        tc5::mma_f16_ta(tm + C::TM_W + 128 * h, tm + TM_Q + 64 * h + 8 * ks, b0 + 16 * ks, id, ks != 0);
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks)
         tc5::mma_f16_ta(tm + C::TM_W + 128 * h, tm + TM_Q + 64 * h + 32 + 8 * ks, b0 + 16 * ks, id64, true);
@@ -383,6 +383,7 @@ struct SolveTGT {
         for (int idx = L.tid; idx < (KB - K) * MB; idx += NT)
           Hs[(K + idx / MB) * RSF + idx % MB] = make_float2(0.f, 0.f);
       }
+      if (L.tid == NT / 2) bulk_wait_read();  // the last W_T staging is read out
       __syncthreads();
 
       // ---- per-user scales d_k (H' = D H, applied while converting), t' = D t
@@ -474,6 +475,7 @@ struct SolveTGT {
       __syncthreads();
 
       float rss = 0.f, o = 0.f, beta = 1.f, gqi = 1.f;
+      bool copied = false;  // the next instance's copy is issued
       if (!singular && ok) {
         // ---- Q^T = H_R^T times the real form of G'^{-T} (basis: of diag(dd))
         {
@@ -641,22 +643,28 @@ struct SolveTGT {
           }
           ok = G::mma_wait(mbar, mphase, lim) && ok;
           stage_e(L, tm_q, Sg);
-          __syncthreads();
+          ok = __syncthreads_and(ok) != 0;
+          if (ok) {  // the X tiles are read: the channel area takes the next copy
+            issue_copy(it + gridDim.x);
+            copied = true;
+          }
           float er[4], ei[4];
           rss = form_e(L, Sg, tks, Es, dinv, false, er, ei);
         }
       }
       // every MMA has completed (or timed out) on every thread: the channel area
-      // takes the next instance's copy
+      // takes the next instance's copy (if not yet issued)
       ok = __syncthreads_and(ok) != 0;
-      if (ok) issue_copy(it + gridDim.x);
-      {
+      if (ok && !copied) issue_copy(it + gridDim.x);
+      {  // W_T (or 0) as [K][256] float2 into the channel-tile area (read by no MMA any
+         // more), written back below by one bulk copy
         const float fo = 1.f / beta;
         const bool zero = singular || !ok;
-        float2* const dst = A.W + w_off + L.tid;
+        float2* const ws = reinterpret_cast<float2*>(sm + C::OFF_HR) + L.tid;
 #pragma unroll
         for (int k = 0; k < KB; ++k)
-          if (k < K) dst[k * MB] = zero ? make_float2(0.f, 0.f) : make_float2(fo * w[k], fo * w[KB + k]);
+          if (k < K) ws[k * MB] = zero ? make_float2(0.f, 0.f) : make_float2(fo * w[k], fo * w[KB + k]);
+        fence_proxy_async_smem();
       }
 #pragma unroll
       for (int msk = 1; msk < 32; msk <<= 1) {
@@ -668,12 +676,21 @@ struct SolveTGT {
         np[L.w] = o;
       }
       __syncthreads();
-      if (L.tid == 0) {
-        float rs = 0.f, ob = 0.f;
-        for (int v = 0; v < NT / 32; ++v) {
-          rs += wred[v];
-          ob += np[v];
+      if (L.tid == NT / 2) {  // W_T out: one contiguous block of K rows
+        bulk_s2g(A.W + w_off, sm + C::OFF_HR, (uint32_t)(K * MB * 8));
+        bulk_commit();
+      }
+      float rs = 0.f, ob = 0.f;  // warp 0: the eight warps' sums
+      if (L.w == 0) {
+        rs = L.lane < NT / 32 ? wred[L.lane] : 0.f;
+        ob = L.lane < NT / 32 ? np[L.lane] : 0.f;
+#pragma unroll
+        for (int msk = 1; msk < NT / 32; msk <<= 1) {
+          rs += __shfl_xor_sync(FULL, rs, msk);
+          ob += __shfl_xor_sync(FULL, ob, msk);
         }
+      }
+      if (L.tid == 0) {
         if (singular) {  // W = 0: objective 0, residual ||S||_F
           ob = 0.f;
           rs = 0.f;
@@ -694,6 +711,7 @@ struct SolveTGT {
       __syncthreads();  // the scalars are read out
       if (!ok) break;   // a tensor-core wait ran out: stop (TMEM is freed below)
     }
+    if (L.tid == NT / 2) bulk_wait();  // the last W_T write-back has completed
     tc5::fence_before_sync();
     __syncthreads();
     if (L.w == 0) tc5::dealloc(tm, C::TMEM_COLS);
