@@ -307,7 +307,7 @@ struct SolveTC : SolveKernel<MODE, 8, 64, 4, 8, 8, true, NW, true, DB> {
       fail |= !(d > 0.f) || !(d < FLT_MAX);
       dmin = fminf(dmin, d);
       dmax = fmaxf(dmax, d);
-      const float inv = __frcp_rn(d);
+      const float inv = rcp_nr(d);
       const float tr = cr * inv, ti = ci * inv;  // A[g][p] / d
       // generic entry: a - (A[g][p] / d) A[p][j]
       float n0r = ar0 - (tr * pr0 - ti * pi0), n0i = ai0 - (tr * pi0 + ti * pr0);

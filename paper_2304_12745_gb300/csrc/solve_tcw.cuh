@@ -393,7 +393,7 @@ struct SolveTCW {
       fail |= !(d > 0.f) || !(d < FLT_MAX);
       dmin = fminf(dmin, d);
       dmax = fmaxf(dmax, d);
-      const float inv = __frcp_rn(d);
+      const float inv = rcp_nr(d);
       for (int idx = L.tid; idx < KB * KB; idx += NTX) {
         const int i = idx / KB, j = idx % KB;
         float2 v;

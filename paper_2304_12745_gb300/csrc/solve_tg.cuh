@@ -418,14 +418,6 @@ struct SolveTG {
     return make_float2(fmaf(f.y, b.y, fmaf(-f.x, b.x, s * a.x)), fmaf(-f.y, b.x, fmaf(-f.x, b.y, s * a.y)));
   }
   __device__ __forceinline__ static float2 cscale(float2 c, float r) { return make_float2(c.x * r, c.y * r); }
-  // reciprocal: the hardware approximation (relative error within 2^-23) and one
-  // Newton-Raphson step r + r (1 - x r), which squares that error (the pivots of an
-  // accepted factorisation are normal numbers)
-  __device__ __forceinline__ static float rcp(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return fmaf(r, fmaf(-x, r, 1.f), r);
-  }
 
   // Equilibrated Gauss-Jordan inverse (no pivoting; pivot spread max d / min d of
   // the equilibrated matrix is the condition estimate) with the matrix in
@@ -483,7 +475,7 @@ struct SolveTG {
       fail |= !(dp > 0.f) || !(dp < FLT_MAX);
       dmin = fminf(dmin, dp);
       dmax = fmaxf(dmax, dp);
-      const float invp = rcp(dp);
+      const float invp = rcp_nr(dp);
       const float2 cip = cp[i], ciq = cp[KB + i];
       float2 rpb[4], rqb[4];
 #pragma unroll
@@ -512,7 +504,7 @@ struct SolveTG {
       fail |= !(dq > 0.f) || !(dq < FLT_MAX);
       dmin = fminf(dmin, dq);
       dmax = fmaxf(dmax, dq);
-      const float invq = rcp(dq);
+      const float invq = rcp_nr(dq);
       const float sq = iq ? invq : 1.f;
       const float2 fqq = iq ? make_float2(0.f, 0.f) : cscale(cq, invq);
 #pragma unroll
