@@ -115,7 +115,14 @@ static precode_status_t train_step_impl(precode_plan_t p, int32_t M, int32_t K, 
   std::lock_guard<std::mutex> lk(p->mu);
   DeviceGuard g(p->device);
   const int T = p->T;
-  const int cpe = (int)std::ceil(std::sqrt((double)T));
+  // checkpoint interval: ceil(sqrt(T)), or the shortest interval whose checkpoints
+  // all fit in the kernel's tensor memory when that is shorter (fewer layers
+  // recomputed in the reverse pass)
+  int cpe = (int)std::ceil(std::sqrt((double)T));
+  if (v->cp_onchip > 0) {
+    const int c_chip = (T + v->cp_onchip - 1) / v->cp_onchip;
+    if (c_chip < cpe) cpe = c_chip;
+  }
   const int ncp = (T + cpe - 1) / cpe;
   // checkpoints in tensor memory where the kernel holds them, else a global workspace
   const bool cp_onchip = ncp <= v->cp_onchip;

@@ -16,7 +16,9 @@
 // between.  Up to CP_ONCHIP checkpoints stay in tensor memory: a warp's W
 // fragments are 32 registers a lane, one 32x32b store of 32 columns into the
 // warp's lane quarter (warp w: quarter w % 4, column group w / 4 of 32 CP_ONCHIP
-// columns); more go to a global workspace.  A kernel that allocates tensor memory
+// columns); more go to a global workspace.  The host takes the shortest interval c
+// whose ceil(T / c) checkpoints fit on chip when that is below ceil(sqrt(T)): at
+// T = 10, c = 2 and 5 recomputed layers instead of 13.  A kernel that allocates tensor memory
 // is resident once per SM, so the build runs one block of 12 warps per SM (the
 // warps of three 4-warp blocks).
 #pragma once
@@ -43,9 +45,12 @@ struct TrainTCH {
   static constexpr int GROUP_STRIDE = OFF_XR + 8 * 32 * 16;
   static constexpr int OFF_TSLOT = NW * GROUP_STRIDE;  // the block's TMEM address
   static constexpr int SMEM_BYTES = OFF_TSLOT + 16;
-  static constexpr int CP_ONCHIP = 4;
+  static constexpr int CP_ONCHIP = 5;
   static constexpr uint32_t CP_GROUP = 32 * CP_ONCHIP;  // columns of one warp's checkpoints
-  static constexpr uint32_t CP_COLS = NW <= 4 ? CP_GROUP : NW <= 8 ? 2 * CP_GROUP : 4 * CP_GROUP;
+  // allocation: the next power of two (at least 32) above the column groups in use
+  static constexpr uint32_t pow2_at_least(uint32_t n) { return n <= 32 ? 32u : 2u * pow2_at_least((n + 1) / 2); }
+  static constexpr uint32_t CP_COLS = pow2_at_least(CP_GROUP * (uint32_t)((NW + 3) / 4));
+  static_assert(CP_COLS <= 512, "the checkpoints fit tensor memory");
   static_assert(NW <= 16 && (NW <= 4 || NW % 4 == 0), "warps share lane quarters by column group");
   static_assert(GROUP_STRIDE % 16 == 0, "alignment");
 
