@@ -354,12 +354,13 @@ struct SolveTGT {
       int64_t inst, h_off, w_off, t_off;
       int K;
       locate(it, inst, h_off, w_off, t_off, K);
-      if (L.w == 1 && it + gridDim.x < n_inst && !(A.opts & OPT_STALL_COPY)) {
-        // the channel copied at the end of this instance: into L2 meanwhile
+      if (L.tid == 32 && it + gridDim.x < n_inst && !(A.opts & OPT_STALL_COPY)) {
+        // the channel copied at the end of this instance (one contiguous block): into
+        // L2 meanwhile
         int64_t i2, h2, w2, t2;
         int K2;
         locate(it + gridDim.x, i2, h2, w2, t2, K2);
-        if (L.lane < K2) prefetch_l2(A.H + h2 + L.lane * MB, MB * 8);
+        prefetch_l2(A.H + h2, (uint32_t)(K2 * MB * 8));
       }
       if (L.tid < KB) tks[L.tid] = L.tid < K ? A.t[t_off + L.tid] : 0.f;
       if (L.tid == 0) misc[0] = mbar_wait_bounded(cbar, cphase, lim) ? 1 : 0;
