@@ -88,6 +88,18 @@ def mma_per_instance_f16(T: int) -> tuple:
     return 48 * T + 24 + 24 + 48, 0
 
 
+def tcgen05_flop_per_instance(T: int, resid: bool) -> tuple:
+    """tcgen05.mma work the transposed tcgen05 kernel (32 users x 256 antennas)
+    issues for one instance: (flop, pipe slots).  Setup: the Gram matrix and Q^T,
+    16 M = N = 128 K = 16 products each; a layer: the residual (16) and the update
+    (8 at N = 128, 8 at N = 64); the final residual (16) when it is asked for.  An
+    N = 64 product holds the tensor pipe as long as an N = 128 one, so it is one
+    slot either way."""
+    full = 32 + 24 * T + (16 if resid else 0)
+    half = 8 * T
+    return full * 2 * 128 * 128 * 16 + half * 2 * 128 * 64 * 16, full + half
+
+
 _PEAK = {"sms": 152, "mhz": 2070.0, "source": "152 SMs (GB300) x 128 FP32 lanes x 2 flop x 2,070 MHz"}
 
 
@@ -299,9 +311,20 @@ def bench_uneven(torch, capi, Plan, inst_table):
         msb = timed(lambda: pb.solve(Hb, tb, mu, out=out))
         fpi = flops_per_instance(K, M, T, 1)
         flops_total += fpi * n
+        kname = capi.precode_plan_describe(pb.handle, M, K)
         per[f"{M}x{K}"] = {"instances": n, "precoders_per_s": n / (msb / 1e3), "ms": msb,
                            "fp32_roofline_frac": fpi * n / (msb / 1e3) / 1e12 / peak,
-                           "kernel": capi.precode_plan_describe(pb.handle, M, K)}
+                           "kernel": kname}
+        if kname.startswith("solve_tgt_kernel"):  # its products run on the tensor pipe
+            fl, slots = tcgen05_flop_per_instance(T, resid=False)
+            bf16 = measured_peaks().get("bf16_tflops", 1900.0)
+            issued = fl * n / (msb / 1e3) / 1e12
+            per[f"{M}x{K}"]["tensor"] = {
+                "issued_tflops": issued, "peak_tflops": bf16, "frac": issued / bf16,
+                "flop_per_instance": fl, "mma_slots_per_instance": slots,
+                "note": "issued tcgen05.mma work (FP16, split hi / lo) against the measured "
+                        "bf16 burst peak (of measured); the FP32 fraction above counts "
+                        "the algorithmic complex flops against the FP32 roofline"}
         pb.close()
     return {"workload": "uneven: 32,768 instances, (M,K) uniform over (32,4),(64,8),(128,16),"
                         "(256,32), Rician ULA per instance, T=10, one CUDA graph per call",
