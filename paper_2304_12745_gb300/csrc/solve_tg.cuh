@@ -312,13 +312,10 @@ struct SolveTG {
   __device__ __forceinline__ static void af_tail(const Lane& L, const float (&fr)[4], const float (&fi)[4],
                                                  float* fsc, float* Fs, unsigned char* sm) {
     const int k0 = 4 * L.w, j = L.lane;
-    float m[4];
+    float m[4];  // row maxima of |Re|, |Im| (non-negative floats order as their bits)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) m[i] = fmaxf(fabsf(fr[i]), fabsf(fi[i]));
-#pragma unroll
-    for (int msk = 1; msk < 32; msk <<= 1)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) m[i] = fmaxf(m[i], __shfl_xor_sync(FULL, m[i], msk));
+    for (int i = 0; i < 4; ++i)
+      m[i] = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(fmaxf(fabsf(fr[i]), fabsf(fi[i])))));
     // scaled F rows [Re F | Im F] into the warp's FP32 staging (word stores), then
     // lane (row r = lane % 4, chunk c = lane / 4 of 8 columns) splits 8 columns and
     // writes them into rows k (chunk c) and k + 32 (chunk c +- 4, Re negated) of the

@@ -254,6 +254,55 @@ struct SolveTGT {
     return (r[0] + r[1]) + (r[2] + r[3]);
   }
 
+  // Per-user scales d_k (row k's largest component into [1/2, 1)), t' = D t, and the
+  // H_R tiles of the scaled channel in one pass over the channel: lane k of warp w
+  // holds row k at antennas 32 w .. 32 w + 31 in registers (consecutive lanes read rows
+  // 16 bytes apart in the padded layout: distinct bank groups), the eight warps' row
+  // maxima meet in pm[8][32]; then it converts as build_hr does
+  __device__ static void scale_tiles(const Lane& L, const float2* Hs, float* tks, float* dinv, float* dgs,
+                                     float* pm, unsigned char* sm) {
+    const int k = L.lane;
+    const float4* const src = reinterpret_cast<const float4*>(Hs + k * RSF + 32 * L.w);
+    float4 v[16];
+    float hm = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      v[i] = src[i];
+      hm = fmaxf(hm, fmaxf(fmaxf(fabsf(v[i].x), fabsf(v[i].y)), fmaxf(fabsf(v[i].z), fabsf(v[i].w))));
+    }
+    pm[L.w * KB + k] = hm;
+    __syncthreads();
+    float rm = pm[k];
+#pragma unroll
+    for (int q = 1; q < NT / 32; ++q) rm = fmaxf(rm, pm[q * KB + k]);
+    const float dg = G::inv_pow2_of(rm);
+    if (L.w == 0) {
+      tks[k] *= dg;
+      dinv[k] = 1.f / dg;
+      dgs[k] = dg;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int m0 = 32 * L.w + 8 * c;
+      float re[8], im[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 x = v[4 * c + i];
+        re[2 * i] = dg * x.x;
+        im[2 * i] = dg * x.y;
+        re[2 * i + 1] = dg * x.z;
+        im[2 * i + 1] = dg * x.w;
+      }
+      uint4 rh, rl, ih, il;
+      G::split8(re, rh, rl);
+      G::split8(im, ih, il);
+      *reinterpret_cast<uint4*>(sm + C::OFF_HR + tc5::tile_off(k, m0, 256)) = rh;
+      *reinterpret_cast<uint4*>(sm + C::OFF_HRL + tc5::tile_off(k, m0, 256)) = rl;
+      *reinterpret_cast<uint4*>(sm + C::OFF_HR + tc5::tile_off(k + 32, m0, 256)) = ih;
+      *reinterpret_cast<uint4*>(sm + C::OFF_HRL + tc5::tile_off(k + 32, m0, 256)) = il;
+    }
+  }
+
   __device__ __forceinline__ static float warp_max(float v) {
 #pragma unroll
     for (int msk = 1; msk < 32; msk <<= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, msk));
@@ -388,17 +437,7 @@ struct SolveTGT {
       __syncthreads();
 
       // ---- per-user scales d_k (H' = D H, applied while converting), t' = D t
-      {
-        const float dg = G::row_scale(L, Hs);
-        if ((L.tid & 7) == 0) {
-          const int k = L.tid >> 3;
-          tks[k] *= dg;
-          dinv[k] = 1.f / dg;
-          dgs[k] = dg;
-        }
-      }
-      __syncthreads();
-      G::build_hr(L, Hs, dgs, sm);
+      scale_tiles(L, Hs, tks, dinv, dgs, np, sm);
 
       // ---- Gram matrix G' = H' H'^H (or the resident factor slot's G'^{-T})
       int fl = 0;
