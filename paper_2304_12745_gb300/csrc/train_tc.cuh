@@ -110,9 +110,11 @@ struct TrainTC {
 
   // g <- d loss / d v through the group shrink with threshold tau at input v;
   // returns d loss / d tau
+  // (r2_in: the column sums of v when the caller already has them)
   __device__ __forceinline__ static float shrink_back(const Lane& L, float* nb, float* fb, float* fb2,
-                                                      const WT& v, WT& g, float tau) {
-    const float2 r2 = S::colsum(L, nb, v);
+                                                      const WT& v, WT& g, float tau,
+                                                      const float2* r2_in = nullptr) {
+    const float2 r2 = r2_in ? *r2_in : S::colsum(L, nb, v);
     __syncwarp();  // every lane has read its norms before nb is reused
     const float2 vg = colsum_vg(L, nb, v, g);
     float dtau = 0.f, c1[2], c2[2];

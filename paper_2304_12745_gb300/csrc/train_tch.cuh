@@ -55,11 +55,14 @@ struct TrainTCH {
   static_assert(GROUP_STRIDE % 16 == 0, "alignment");
 
   // one forward layer l in scaled units: W'_l -> W'_{l+1}
+  // (r2: the column sums of the input W'_l, for a reverse step that needs them)
   __device__ __forceinline__ static void fwd_layer(const Lane& L, const Ctx& c, const TrainArgs& A,
                                                    const uint4* hh, const uint4* hl, const uint4* xf,
-                                                   float* nb, float* fb, int l, float beta, WT& w) {
+                                                   float* nb, float* fb, int l, float beta, WT& w,
+                                                   float2& r2) {
     float e[4];
-    S::shrink(L, fb, S::colsum(L, nb, w), fmaxf(__ldg(A.s.step + l), 0.f) * beta, w);
+    r2 = S::colsum(L, nb, w);
+    S::shrink(L, fb, r2, fmaxf(__ldg(A.s.step + l), 0.f) * beta, w);
     SH::residual_h(L, hh, hl, w, e);
     if (2 * L.q == L.g) e[0] -= c.tks[L.g];
     if (2 * L.q + 1 == L.g) e[1] -= c.tks[L.g];
@@ -210,7 +213,8 @@ struct TrainTCH {
 #pragma unroll 1
       for (int l = 0; l < T; ++l) {
         if (l % A.cp_every == 0) store_cp(l / A.cp_every);
-        fwd_layer(L, c, A, hh, hl, xf, nb, fb, l, beta, w);
+        float2 r2;
+        fwd_layer(L, c, A, hh, hl, xf, nb, fb, l, beta, w, r2);
       }
 
       // ---- loss and its gradient at W_T, in original units
@@ -271,19 +275,27 @@ struct TrainTCH {
 #pragma unroll
         for (int k = 0; k < 4; ++k) g[s][k] *= gs_;
 
-      // ---- reverse: layer l = T-1 .. 0, recomputing its input from a checkpoint
+      // ---- reverse: layer l = T-1 .. 0, recomputing its input from a checkpoint.  The
+      // last recomputed layer's input column sums (of W'_{l-1}) serve the next step,
+      // whose input that is (bitwise the same values, reloaded)
+      float2 r2c = make_float2(0.f, 0.f);
+      int r2l = -1;
 #pragma unroll 1
       for (int l = T - 1; l >= 0; --l) {
         const int k = l / A.cp_every;
         load_cp(k);
 #pragma unroll 1
-        for (int s = k * A.cp_every; s < l; ++s) fwd_layer(L, c, A, hh, hl, xf, nb, fb, s, beta, w);
+        for (int s = k * A.cp_every; s < l; ++s) {
+          fwd_layer(L, c, A, hh, hl, xf, nb, fb, s, beta, w, r2c);
+          r2l = s;
+        }
         // w = W'_l, the input of layer l
         float eg[4];
         SH::residual_h(L, hh, hl, g, eg);  // g' H'^T
         SH::update_h(L, xf, eg, g);        // g' - (g' H'^T) Q'
         const float mu_raw = __ldg(A.s.step + l);
-        const float dmu = TT::shrink_back(L, nb, fb, fb2, w, g, fmaxf(mu_raw, 0.f) * beta);
+        const float dmu = TT::shrink_back(L, nb, fb, fb2, w, g, fmaxf(mu_raw, 0.f) * beta,
+                                          r2l == l ? &r2c : nullptr);
         if (c.g == 0) part[1 + l] = mu_raw > 0.f ? dmu * igs : 0.f;
       }
       if (c.g == 0 && A.s.flags) A.s.flags[inst] = fl;
