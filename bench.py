@@ -221,6 +221,42 @@ def host_link_peak(torch, nbytes: int = 268 << 20, reps: int = 5) -> dict:
     return out
 
 
+def ring_link_rates(torch, ring_bytes: int = 4 << 30, chunk: int = 8 << 20, copies: int = 64,
+                    windows: int = 5) -> dict:
+    """Copy rates between the device and a page-locked buffer the size of the serving
+    load's output ring, as that load uses it: 8 MB copies at random 64 KB-aligned
+    offsets, `copies` per window, median over `windows` (CUDA events), taken with the
+    server idle.  Recorded beside the serving latencies as the state of the host link
+    they were measured under: the device->host rate into such a buffer has been seen
+    between ~23 and ~181 GB/s on boxes after sustained serving load, and at ~181 GB/s
+    on runs whose p99 was 12-22 ms, so it does not by itself explain the tail."""
+    host = torch.empty(ring_bytes, dtype=torch.uint8, pin_memory=True)
+    dev = torch.empty(chunk, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(3)
+    st = torch.cuda.current_stream()
+
+    def window(d2h: bool) -> float:
+        offs = rng.integers(0, (ring_bytes - chunk) // 65536, copies) * 65536
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for o in offs:
+            if d2h:
+                host[int(o):int(o) + chunk].copy_(dev, non_blocking=True)
+            else:
+                dev.copy_(host[int(o):int(o) + chunk], non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return copies * chunk / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    window(True)
+    d2h = [window(True) for _ in range(windows)]
+    h2d = [window(False) for _ in range(windows)]
+    del host, dev
+    return {"d2h_gbs": float(np.median(d2h)), "d2h_gbs_min": float(min(d2h)),
+            "h2d_gbs": float(np.median(h2d))}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -601,6 +637,8 @@ def bench_serve(capi, mu, duration_s: float = 2.0, n_runs: int = 3):
     for j in warm:
         j.wait()
     poisson_load(s, 500.0, 0.2, seed=11)
+    import torch
+    link_before = ring_link_rates(torch)
     runs = []
     for r in range(n_runs):  # independent Poisson runs back to back (seeds 12, 13, ...)
         s.reset_stats()
@@ -609,6 +647,7 @@ def bench_serve(capi, mu, duration_s: float = 2.0, n_runs: int = 3):
                      "max_ms": st["max_us"] / 1e3, "precoders_per_s": st["precoders_per_s"],
                      "jobs": st["jobs"], "achieved_jobs_per_s": st["achieved_rate_per_s"],
                      "launches": st["launches"]})
+    link_after = ring_link_rates(torch)
     s.close()
     med = lambda k: float(np.median([r[k] for r in runs]))  # noqa: E731
     return {"workload": "serve: Poisson 2,000 jobs/s, %d runs of %.1f s; M in {64,128,256}, "
@@ -618,6 +657,10 @@ def bench_serve(capi, mu, duration_s: float = 2.0, n_runs: int = 3):
             "p99_ms_per_run": [r["p99_ms"] for r in runs],
             "precoders_per_s": med("precoders_per_s"), "jobs": sum(r["jobs"] for r in runs),
             "achieved_jobs_per_s": med("achieved_jobs_per_s"), "runs": runs,
+            "ring_link": {"before_runs": link_before, "after_runs": link_after,
+                          "how": "8 MB copies at random offsets of a page-locked 4 GB buffer "
+                                 "(the output ring's size), median of 5 windows of 64, with "
+                                 "the server idle"},
             "note": "p50 / p99 / precoders per s: median over the runs; max: over all runs"}
 
 
