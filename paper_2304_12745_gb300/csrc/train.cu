@@ -2,6 +2,7 @@
 // then a deterministic FP64 batch mean of the per-instance loss and gradients.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <map>
@@ -27,21 +28,83 @@ const std::vector<TrainVariant>& train_variants() {
 
 namespace {
 
-// out[j] = scale * sum_b part[b][j] for j < P, summed in FP64 in a fixed order
-// (thread i takes rows i, i + blockDim, ...; then a fixed tree), one block per j.
-__global__ void batch_mean_kernel(const float* __restrict__ part, int64_t B, int P, double scale,
-                                  float* __restrict__ out) {
-  __shared__ double buf[256];
+// Batch means of the per-instance partials part[b][j] (j = 0: loss, 1..T: d step,
+// T+1..2T: d lam), in FP64 and in an order fixed by B and P alone, so a step gives the
+// same bits on every run.  Stage 1: block g sums rows [g R, (g+1) R) of every column;
+// for P <= 256 its threads read whole rows (coalesced), thread i taking column i % P of
+// every (256 / P)-th row, and the row phases are then added in order.  Stage 2: one
+// block per column adds the G block sums (strided, then a fixed tree) and scales.
+constexpr int kSumThreads = 256;
+
+struct BatchSumShape {
+  int64_t rows;  // R: rows per stage-1 block
+  int blocks;    // G = ceil(B / R) <= bound
+  int bound;     // non-decreasing in B: sizes the block-sum scratch for every B <= B_max
+};
+
+BatchSumShape batch_sum_shape(int64_t B, int P) {
+  int64_t g = (B + kSumThreads - 1) / kSumThreads;
+  g = std::min<int64_t>(g, 1024);
+  g = std::min<int64_t>(g, std::max<int64_t>(1, (int64_t(1) << 22) / P));
+  const int64_t rows = (B + g - 1) / g;
+  return {rows, (int)((B + rows - 1) / rows), (int)g};
+}
+
+__global__ void __launch_bounds__(kSumThreads)
+batch_sum_rows_kernel(const float* __restrict__ part, int64_t B, int P, int64_t rows,
+                      double* __restrict__ bsum) {
+  __shared__ double buf[kSumThreads];
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int64_t r1 = r0 + rows < B ? r0 + rows : B;
+  double* out = bsum + (int64_t)blockIdx.x * P;
+  const int i = threadIdx.x;
+  if (P <= kSumThreads) {
+    const int rpp = kSumThreads / P;
+    double s = 0.0;
+    if (i < rpp * P) {
+      const int j = i % P;
+#pragma unroll 4
+      for (int64_t r = r0 + i / P; r < r1; r += rpp) s += (double)part[r * P + j];
+    }
+    buf[i] = s;
+    __syncthreads();
+    if (i < P) {
+      double t = 0.0;
+      for (int q = 0; q < rpp; ++q) t += buf[q * P + i];
+      out[i] = t;
+    }
+  } else {
+    for (int j = i; j < P; j += kSumThreads) {
+      double s = 0.0;
+      for (int64_t r = r0; r < r1; ++r) s += (double)part[r * P + j];
+      out[j] = s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSumThreads)
+batch_sum_finish_kernel(const double* __restrict__ bsum, int G, int P, int T, double scale,
+                        float* __restrict__ loss, float* __restrict__ dstep,
+                        float* __restrict__ dlam) {
+  __shared__ double buf[kSumThreads];
   const int j = blockIdx.x;
   double s = 0.0;
-  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) s += (double)part[b * P + j];
+  for (int g = threadIdx.x; g < G; g += kSumThreads) s += bsum[(int64_t)g * P + j];
   buf[threadIdx.x] = s;
   __syncthreads();
-  for (int span = blockDim.x / 2; span > 0; span >>= 1) {
+  for (int span = kSumThreads / 2; span > 0; span >>= 1) {
     if ((int)threadIdx.x < span) buf[threadIdx.x] += buf[threadIdx.x + span];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[j] = (float)(buf[0] * scale);
+  if (threadIdx.x == 0) {
+    const float v = (float)(buf[0] * scale);
+    if (j == 0)
+      *loss = v;
+    else if (j <= T)
+      dstep[j - 1] = v;
+    else
+      dlam[j - 1 - T] = v;
+  }
 }
 
 
@@ -128,7 +191,11 @@ static precode_status_t train_step_impl(precode_plan_t p, int32_t M, int32_t K, 
   const bool cp_onchip = ncp <= v->cp_onchip;
   const size_t cp_need =
       cp_onchip ? 0 : (size_t)p->max_instances * ncp * v->KB * v->MB * sizeof(float2);
-  const size_t part_need = (size_t)p->max_instances * (1 + 2 * T) * sizeof(float);
+  // per-instance partials, then (8-byte aligned) the stage-1 block sums of the batch means
+  const int PW = 1 + 2 * T;
+  const size_t part_floats = ((size_t)p->max_instances * PW + 1) & ~(size_t)1;
+  const size_t part_need = part_floats * sizeof(float) +
+                           (size_t)batch_sum_shape(p->max_instances, PW).bound * PW * sizeof(double);
   if (cp_need > p->cp_bytes) {
     cudaFree(p->d_cp);
     p->d_cp = nullptr;
@@ -174,11 +241,12 @@ static precode_status_t train_step_impl(precode_plan_t p, int32_t M, int32_t K, 
   cudaError_t e = cudaLaunchKernel(v->fn, dim3((unsigned)grid), dim3(v->threads), args,
                                    (size_t)v->smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "precode_train_step: train kernel launch");
-  const int PW = 1 + 2 * T;
-  // loss (column 0) and d step (columns 1..T) into loss / dstep; d lam separately
-  batch_mean_kernel<<<1, 256, 0, s>>>(p->d_part, B, PW, 1.0 / (double)B, loss);
-  batch_mean_kernel<<<T, 256, 0, s>>>(p->d_part + 1, B, PW, 1.0 / (double)B, dstep);
-  if (dlam) batch_mean_kernel<<<T, 256, 0, s>>>(p->d_part + 1 + T, B, PW, 1.0 / (double)B, dlam);
+  // loss (column 0), d step (columns 1..T) and, where asked for, d lam (T+1..2T)
+  const BatchSumShape bs = batch_sum_shape(B, PW);
+  double* bsum = reinterpret_cast<double*>(p->d_part + part_floats);
+  batch_sum_rows_kernel<<<bs.blocks, kSumThreads, 0, s>>>(p->d_part, B, PW, bs.rows, bsum);
+  batch_sum_finish_kernel<<<dlam ? PW : 1 + T, kSumThreads, 0, s>>>(
+      bsum, bs.blocks, PW, T, 1.0 / (double)B, loss, dstep, dlam);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "precode_train_step: batch reduction launch");
   return PRECODE_OK;
