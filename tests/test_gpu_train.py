@@ -346,3 +346,33 @@ def test_supervised_training_lowers_the_mse(orc):
     assert last < 0.2 * first, (first, last)
     assert np.all(tr.step.detach().cpu().numpy() >= 0)  # the projection mu >= 0 held
     tr.plan.close()
+
+
+@pytest.mark.parametrize("K,M,tc", [(4, 32, False), (8, 64, True)])
+def test_batch_means_at_long_depth_equal_per_instance_means(K, M, tc):
+    """The batch loss and gradients are FP64 means of the per-instance values. At
+    T = 130 the per-instance record holds 1 + 2T = 261 scalars, more than one
+    reduction block has threads, and B = 300 leaves a ragged row chunk. The batch
+    results must equal the mean of the same instances solved one at a time (B = 1,
+    where the mean is the instance's own value), up to the final rounding to FP32.
+    Uses the paper layer, so d lam is reduced as well."""
+    from paper_2304_12745_gb300 import capi
+    from paper_2304_12745_gb300.precoder import Plan
+    T, B = 130, 300
+    H = ch.rayleigh(B, K, M, seed=90 + K)
+    t = np.full((B, K), math.sqrt(10.0), np.float32)
+    rs = np.random.default_rng(91)
+    eta = (ch.paper_eta(K, M) * rs.uniform(0.5, 1.0, T)).astype(np.float32).astype(np.float64)
+    lam = np.full(T, np.float32(1 / 15), np.float64)
+    a = 1 / 15
+    plan = Plan(capi.LAYER_PGD, T, [(M, K)], B, tensor_cores=tc)
+    loss, ge, gl = _train_step(plan, H, t, eta, lam, a)
+    one = [_train_step_one(plan, H[b], t[b], eta, lam, a) for b in range(B)]
+    plan.close()
+    per_loss = np.array([o[0] for o in one])
+    per_ge = np.array([o[1] for o in one])
+    per_gl = np.array([o[2] for o in one])
+    assert np.all(np.isfinite(per_ge)) and np.all(np.isfinite(per_gl))
+    assert loss == pytest.approx(per_loss.mean(), rel=1e-6)
+    for got, per in ((ge, per_ge), (gl, per_gl)):
+        assert np.allclose(got, per.mean(0), rtol=1e-6, atol=1e-9 * np.abs(per).max()), (got, per.mean(0))
