@@ -228,7 +228,7 @@ def ring_link_rates(torch, ring_bytes: int = 4 << 30, chunk: int = 8 << 20, copi
     offsets, `copies` per window, median over `windows` (CUDA events), taken with the
     server idle.  Recorded beside the serving latencies as the state of the host link
     they were measured under: the device->host rate into such a buffer has been seen
-    between ~23 and ~181 GB/s on boxes after sustained serving load, and at ~181 GB/s
+    between ~23 and ~181 GB/s on GB300 hosts after sustained serving load, and at ~181 GB/s
     on runs whose p99 was 12-22 ms, so it does not by itself explain the tail."""
     host = torch.empty(ring_bytes, dtype=torch.uint8, pin_memory=True)
     dev = torch.empty(chunk, dtype=torch.uint8, device="cuda")
