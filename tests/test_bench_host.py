@@ -33,6 +33,21 @@ def test_mma_counts():
     assert bench.mma_per_instance(10) == 96 * 10 + 192
 
 
+def test_tcgen05_counts():
+    # transposed tcgen05 kernel at 32 x 256: the Gram matrix and Q^T in the setup, 16
+    # M = N = 128 K = 16 products each; a layer: the residual (16 of them) and the
+    # update (8 at N = 128 for Q hi, 8 at N = 64 for Q lo x E hi); the final residual
+    # (16) only when the residual is asked for.  2 M N K flop per product.
+    big, small = 2 * 128 * 128 * 16, 2 * 128 * 64 * 16
+    f, slots = bench.tcgen05_flop_per_instance(10, False)
+    assert slots == 2 * 16 + 10 * (16 + 8 + 8) == 352
+    assert f == (2 * 16 + 10 * (16 + 8)) * big + 10 * 8 * small == 163_577_856
+    f_r, slots_r = bench.tcgen05_flop_per_instance(10, True)
+    assert slots_r - slots == 16 and f_r - f == 16 * big
+    f1, slots1 = bench.tcgen05_flop_per_instance(1, False)
+    assert slots1 == 64 and f1 == 56 * big + 8 * small
+
+
 def test_fp32_peak():
     assert bench.fp32_peak_tflops() == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
     bench.set_fp32_peak(148, 1965.0, "test")
